@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Throughput of the fused RR-MHD lattice Boltzmann step on GB300.
+
+Workload (default): the Orszag-Tang vortex on a 4096 x 4096 periodic lattice,
+u0 = b0 = 0.04, nu = eta = 2e-5 (tau = 0.50006), FP32 storage of the
+populations as deviations f_i - w_i rho0.  One bench step = one time step =
+one launch of the fused stream-and-collide kernel over all 16.8 M nodes
+(queued through mhd_advance, 64-step CUDA graphs).
+
+Prints ONE JSON line (rank 0):
+  value     MLUPS over all ranks (nodes x steps / max-over-ranks device time),
+            inputs resident in HBM, timed with CUDA events on the lattice stream;
+  e2e       the same metric through the C ABI with pinned HOST buffers:
+            mhd_set_fields (H2D) + mhd_advance + mhd_get_fields (D2H) +
+            mhd_get_totals inside the timed region;
+  roofline  achieved HBM GB/s of the step kernel (152 algorithmic bytes per
+            node for FP32: 19 values read + 19 written) vs the measured copy
+            bandwidth in MEASURED_PEAKS.json;
+  cpu_baseline  the FP64 oracle on the host cores, bounded sample.
+--impl reference times the oracle itself (the only reference this method
+has) on a bounded sample of the same workload.
+Multi-GPU (torchrun): every rank advances its own replica (weak scaling, no
+data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_NODE = {"fp64": 304, "fp32": 152, "fp16s": 76}
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16s": "f32 (f16 storage)"}
+METRIC = "MLUPS & % HBM roofline (4096² RR-MHD step); coarse+closure vs plain error"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16s"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--shape", default=None,
+                    help="fixed launch shape 'V,BY' (skips the autotuner; for profiling)")
+    return ap.parse_args()
+
+
+def workload(n, prec):
+    return {"workload": f"orszag_tang_{n}x{n}_{prec}", "nx": n, "ny": n, "u0": 0.04, "b0": 0.04,
+            "nu": 2e-5, "eta": 2e-5, "tau_f": 0.50006, "tau_m": 0.50006, "precision": prec,
+            "collision": "recursive_regularised", "eq_variant": "A"}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2602_14667_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(prec, n):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken
+    from the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"rr_step_{prec}_ncu.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line and line.startswith("- "):
+                k, v = line[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    try:
+        per_node = float(vals["dram_bytes_per_node"])
+    except (KeyError, ValueError):
+        return None
+    return per_node * n * n
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+                for name, v in zip(names, r[4:8]):
+                    if v.lower() in ("active", "1"):
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(n_sample=512, budget_s=12.0):
+    """The FP64 oracle, as it stands, on all host cores: an OT lattice of
+    n_sample^2 with the bench's physical parameters, as many steps as fit in
+    about budget_s seconds."""
+    import mhd_inputs
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    p = oracle.Params(n_sample, n_sample, 0.50006, 0.50006)
+    f, g = oracle.init(p, *mhd_inputs.orszag_tang(n_sample, 0.04, 0.04))
+    t0 = time.perf_counter()
+    f, g = oracle.run(p, f, g, 1)
+    t1 = time.perf_counter() - t0
+    steps = max(1, min(200, int(budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.run(p, f, g, steps)
+    dt = time.perf_counter() - t0
+    return {"value": n_sample * n_sample * steps / dt / 1e6, "unit": "MLUPS",
+            "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{n_sample}x{n_sample} Orszag-Tang, {steps} steps, FP64 oracle "
+                      f"(same u0, nu as the workload), {dt:.1f} s"}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """The oracle (the method's only reference implementation) timed on the
+    host cores on a bounded sample of the workload: each step is one oracle
+    step of an n_s x n_s Orszag-Tang lattice with the workload's physics,
+    n_s chosen so that warmup + steps end in about two minutes."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import mhd_inputs
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    total = args.warmup + args.steps
+    ns = 512
+    while True:
+        p = oracle.Params(ns, ns, 0.50006, 0.50006)
+        f, g = oracle.init(p, *mhd_inputs.orszag_tang(ns, 0.04, 0.04))
+        t0 = time.perf_counter()
+        f, g = oracle.run(p, f, g, 1)
+        t1 = time.perf_counter() - t0
+        if t1 * total <= 120.0 or ns <= 16:
+            break
+        ns //= 2
+    f, g = oracle.run(p, f, g, args.warmup)
+    t0 = time.perf_counter()
+    oracle.run(p, f, g, args.steps)
+    dt = time.perf_counter() - t0
+    v = ns * ns * args.steps / dt / 1e6
+    sample = f"{ns}x{ns} Orszag-Tang sub-lattice per step (u0=b0=0.04, nu=eta=2e-5), FP64 oracle"
+    out = {"metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference", "config": workload(args.n, args.precision),
+           "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    import mhd_inputs
+    from paper_2602_14667_gb300 import Lattice, MhdError
+
+    world, rank, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, prec = args.n, args.precision
+    tau = 0.50006
+    stream = torch.cuda.Stream(device=dev)
+    ux, uy, bx, by = mhd_inputs.orszag_tang(n, 0.04, 0.04)
+
+    lat = Lattice(n, n, tau, tau, precision=prec, stream=stream.cuda_stream)
+    lat.set_fields(ux, uy, bx, by)
+    if args.shape:
+        lat.kernel_config = tuple(int(v) for v in args.shape.split(","))
+        shape = lat.kernel_config
+    else:
+        shape = lat.autotune()
+    lat.advance(args.warmup)
+    stream.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        lat.advance(args.steps)
+        ev1.record(stream)
+        ev1.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    try:
+        tot = lat.get_totals()
+        stable = True
+    except MhdError:
+        tot, stable = None, False
+
+    nodes = n * n
+    value = world * nodes * args.steps / (ms_max * 1e-3) / 1e6
+    per_launch_s = ms * 1e-3 / args.steps
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_NODE[prec] * nodes / per_launch_s / 1e9
+    traffic = profiled_traffic(prec, n)
+
+    e2e = None
+    if not args.no_e2e:
+        pin = [torch.empty((n, n), dtype=torch.float64).pin_memory() for _ in range(9)]
+        for t_, a in zip(pin[:4], (ux, uy, bx, by)):
+            t_.numpy()[:] = a
+        h = [t_.numpy() for t_ in pin]
+        lat2 = Lattice(n, n, tau, tau, precision=prec, stream=stream.cuda_stream)
+        lat2.kernel_config = shape
+        lat2.set_fields(*h[:4])
+        lat2.advance(args.warmup)
+        stream.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        lat2.set_fields(*h[:4])                 # H2D of the initial fields
+        lat2.advance(args.steps)
+        lat2.get_fields(out=h[4:9])            # D2H of rho, u, b
+        lat2.get_totals()                      # D2H of the totals
+        t_e2e = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        lat2.close()
+        h2d = 4 * 8 * nodes / args.steps
+        d2h = (5 * 8 * nodes + 13 * 8) / args.steps
+        e2e = {"value": world * nodes * args.steps / t_e2e / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "note": "mhd_set_fields + mhd_advance(steps) + mhd_get_fields + mhd_get_totals "
+                       "from/to pinned host memory; bytes amortised over the steps"}
+    lat.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline()
+    cfg = workload(n, prec)
+    cfg.update({"kernel_config": list(shape), "graph_steps": 64,
+                "l2": "no flush: the 2 x 19-plane state (2.55 GB FP32) is far above the 129 MB L2",
+                "stable": stable, "replicas": world})
+    out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
+           "config": cfg,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "peak_source": peak_kind,
+                        "frac_of_nominal_8tbs": achieved / 8000.0,
+                        "bytes_per_node": BYTES_PER_NODE[prec],
+                        "traffic": traffic},
+           "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+           "clocks": clk.summary()}
+    if tot is not None:
+        out["totals"] = {k: tot[k] for k in ("mass", "e_kin", "e_mag", "jz_max", "divb_max")}
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

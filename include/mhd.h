@@ -1,0 +1,173 @@
+/*
+ * mhd.h -- C ABI of the GB300 (sm_103a) recursive regularised lattice
+ * Boltzmann solver for 2-D incompressible resistive MHD.
+ *
+ * Method: De Rosis, "Recursive regularised lattice Boltzmann method for
+ * magnetohydrodynamics".  Fluid: D2Q9 populations f_i, fourth-order Hermite
+ * equilibrium carrying the Maxwell stress (Eq. feq_4th), recursive regularised
+ * collision (Section "Recursive regularised lattice Boltzmann method", tasks
+ * 1-5 of "Algorithm of computation").  Magnetic field: D2Q5 vector populations
+ * g_j relaxed by BGK towards Dellar's induction equilibrium (Eq. collide_g).
+ *
+ * Conventions for every call:
+ *  - Lattice units.  Node n = y*nx + x, x fastest.  Host arrays are FP64,
+ *    caller-owned, read or written only during the call.
+ *  - nu = (tau_f - 1/2)/3 and eta = (tau_m - 1/2)/3 (cs^2 = 1/3 on both
+ *    lattices; the paper's transport relation prints the bracket without the
+ *    cs^2 factor).
+ *  - The library owns all device memory of a lattice.  No exception crosses
+ *    the ABI; every call returns an mhd_status and, on failure, leaves a
+ *    message for mhd_last_error() in the calling thread.  A lattice must not
+ *    be used from two host threads at once.
+ *  - Work is queued on the CUDA stream given at creation (NULL: the legacy
+ *    default stream).  mhd_advance returns without waiting; every mhd_get_*
+ *    call waits for the stream.
+ *  - The device buffer holds post-collision populations f*(t) (pull scheme:
+ *    one kernel per step gathers f*(t-1) from the neighbours, collides, and
+ *    writes f*(t)).  rho, rho u and b are collision invariants, so fields read
+ *    back are the moments of the state at time t.
+ */
+#ifndef MHD_LBM_H
+#define MHD_LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mhd_lattice mhd_lattice; /* opaque single lattice */
+
+typedef enum {
+    MHD_OK = 0,
+    MHD_EINVAL = 1,    /* bad argument (NULL pointer, size, tau <= 1/2, ...) */
+    MHD_ENOMEM = 2,    /* device or host allocation failed */
+    MHD_ECUDA = 3,     /* a CUDA runtime call failed; see mhd_last_error() */
+    MHD_EUNSTABLE = 4, /* a diagnostic came out non-finite (the run blew up) */
+    MHD_ESTATE = 5     /* call not valid in the current state (e.g. no fields set) */
+} mhd_status;
+
+typedef enum {
+    MHD_FP64 = 0,  /* populations stored as FP64 deviations, FP64 arithmetic */
+    MHD_FP32 = 1,  /* FP32 deviations f_i - w_i rho0 (g unshifted), FP32 arithmetic */
+    MHD_FP16S = 2  /* IEEE FP16 of 2^12 (f_i - w_i rho0) and 2^12 g, FP32 arithmetic */
+} mhd_precision;
+
+typedef enum { MHD_PERIODIC = 0, MHD_WALL = 1 } mhd_bc; /* per axis; walls: half-way bounce-back */
+
+typedef enum {
+    MHD_RR = 0, /* recursive regularised (the paper's scheme) */
+    MHD_BGK = 1 /* plain BGK fluid collision (Eq. collide_f), for comparison */
+} mhd_collision;
+
+typedef struct {
+    double rho0;    /* reference density, > 0 (shift of the stored populations) */
+    double tau_f;   /* fluid relaxation time, > 1/2 (omega = 1/tau_f) */
+    double tau_m;   /* magnetic relaxation time, > 1/2 (omega_m = 1/tau_m) */
+    int bc_x, bc_y; /* mhd_bc */
+    int precision;  /* mhd_precision */
+    int eq_variant; /* 0: Eq. feq_4th as printed (Maxwell stress at 2nd order
+                       only); 1: with the u (x) M terms of Eq. a0_4 at 3rd and
+                       4th order */
+    int collision;  /* mhd_collision */
+} mhd_params;
+
+/* Global diagnostics at the current time (mhd_get_totals).  Sums run over
+ * all nodes; means divide by nx*ny.  Gradients use the isotropic lattice
+ * stencil of the Orszag-Tang section; on a wall axis, nodes whose 3x3
+ * stencil leaves the lattice are left out of divb_*, omega_max. */
+typedef struct {
+    double mass;      /* sum rho */
+    double mom_x;     /* sum rho u_x */
+    double mom_y;     /* sum rho u_y */
+    double e_kin;     /* mean |u|^2 / 2  (E_k of the Orszag-Tang section) */
+    double e_mag;     /* mean |b|^2 / 2  (E_m) */
+    double cross_hel; /* mean u . b */
+    double bsum_x;    /* sum b_x */
+    double bsum_y;    /* sum b_y */
+    double divb_max;  /* max |div b| */
+    double divb_rms;  /* sqrt(mean (div b)^2) */
+    double jz_max;    /* max |j_z|, j_z from the populations by Eq. current */
+    double omega_max; /* max |d_x u_y - d_y u_x| */
+    long long step;   /* time steps taken since the fields were set */
+} mhd_totals;
+
+/* Kernel launch shape of the fused step (chosen by mhd_autotune or the
+ * built-in heuristic).  nodes_per_thread: consecutive x nodes one thread
+ * updates with vector loads and stores: 1, 2 or 4 (at most 2 for MHD_FP64);
+ * it must divide nx and must be 1 when the x axis has walls.
+ * rows_per_block: warps per block, one row of 32*nodes_per_thread nodes
+ * each: 1..16 (1..8 for MHD_FP64). */
+typedef struct {
+    int nodes_per_thread;
+    int rows_per_block;
+} mhd_kernel_config;
+
+/* Create an nx x ny lattice on the current CUDA device.  The populations are
+ * undefined until mhd_set_fields or mhd_set_populations.
+ * stream: a cudaStream_t (may be NULL).  *out receives the handle (NULL on
+ * failure).  MHD_EINVAL if nx or ny < 2, nx*ny > 2^31, tau_f or tau_m <= 1/2,
+ * rho0 <= 0, an unknown enum value, or NULL p / out; MHD_ENOMEM if the two
+ * population buffers (2 x 19 planes) do not fit in device memory. */
+mhd_status mhd_create(int nx, int ny, const mhd_params* p, void* stream, mhd_lattice** out);
+
+/* Set the initial state: f = f_eq(rho, u, b) (Eq. feq_4th), g = g_eq(u, b),
+ * i.e. zero non-equilibrium (a1^(2) = 0, so this is both the pre- and the
+ * post-collision state at t = 0).  ux, uy, bx, by: host arrays of nx*ny;
+ * rho may be NULL (rho = rho0).  Resets the step counter.  Non-finite input
+ * -> MHD_EINVAL. */
+mhd_status mhd_set_fields(mhd_lattice* l, const double* ux, const double* uy, const double* bx,
+                          const double* by, const double* rho);
+
+/* Queue nsteps fused stream-and-collide steps (tasks 1-6 of "Algorithm of
+ * computation") on the lattice's stream; runs of 64 steps go through a CUDA
+ * graph captured on first use.  nsteps >= 0. */
+mhd_status mhd_advance(mhd_lattice* l, long long nsteps);
+
+/* Read the fields of the current state into host arrays of nx*ny (any of
+ * them may be NULL).  Waits for the stream. */
+mhd_status mhd_get_fields(mhd_lattice* l, double* rho, double* ux, double* uy, double* bx,
+                          double* by);
+
+/* Global diagnostics of the current state (see mhd_totals), reduced on the
+ * GPU in FP64 with a fixed order (bitwise reproducible).  Waits for the
+ * stream.  MHD_EUNSTABLE (with *out filled) if any total is not finite.
+ * j_z needs the pre-collision magnetic populations: after a step they are
+ * gathered again from the buffer that step read; right after
+ * mhd_set_populations or mhd_autotune they are recovered from the stored
+ * post-collision ones as g - g_eq = (g* - g_eq)/(1 - omega_m) (jz_max = 0
+ * when tau_m = 1, where that inverse does not exist). */
+mhd_status mhd_get_totals(mhd_lattice* l, mhd_totals* out);
+
+/* Checkpoint: the stored post-collision populations as unshifted FP64 values.
+ * f: 9*nx*ny doubles, plane i at f + i*nx*ny (i in the paper's D2Q9 order);
+ * g: 10*nx*ny doubles, component a of g_j at g + (2*j + a)*nx*ny.
+ * Waits for the stream. */
+mhd_status mhd_get_populations(mhd_lattice* l, double* f, double* g);
+
+/* Restore populations written by mhd_get_populations (same layout; values are
+ * rounded to the storage precision).  The step counter is kept. */
+mhd_status mhd_set_populations(mhd_lattice* l, const double* f, const double* g);
+
+/* Current launch shape, or set one explicitly (MHD_EINVAL if the shape is not
+ * valid for this lattice). */
+mhd_status mhd_get_kernel_config(const mhd_lattice* l, mhd_kernel_config* out);
+mhd_status mhd_set_kernel_config(mhd_lattice* l, const mhd_kernel_config* cfg);
+
+/* Autotune the launch shape: time every valid (nodes_per_thread,
+ * rows_per_block) for this lattice with CUDA events and keep the fastest.
+ * The state is not advanced (candidates read the current buffer and write
+ * the spare one).  Results are cached per (GPU, precision, nx, ny, bc) in
+ * the JSON file named by $MHD_TUNE_CACHE (no caching when unset); a cached
+ * entry is reused without timing.  best (may be NULL) receives the choice. */
+mhd_status mhd_autotune(mhd_lattice* l, mhd_kernel_config* best);
+
+mhd_status mhd_destroy(mhd_lattice* l);
+
+/* Message of the last failed call in this thread ("" if none). */
+const char* mhd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MHD_LBM_H */

@@ -1,0 +1,199 @@
+"""ctypes binding of ``libmhdlbm.so`` (the C ABI in ``include/mhd.h``).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Loading fails loudly when the library has not been built --
+there is no CPU fallback.  Functions keep the C names (``mhd_create``, ...);
+``Lattice`` is a small owner object over them that converts numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmhdlbm.so")
+
+MHD_OK, MHD_EINVAL, MHD_ENOMEM, MHD_ECUDA, MHD_EUNSTABLE, MHD_ESTATE = range(6)
+MHD_FP64, MHD_FP32, MHD_FP16S = range(3)
+MHD_PERIODIC, MHD_WALL = range(2)
+MHD_RR, MHD_BGK = range(2)
+STATUS_NAMES = {0: "MHD_OK", 1: "MHD_EINVAL", 2: "MHD_ENOMEM", 3: "MHD_ECUDA", 4: "MHD_EUNSTABLE",
+                5: "MHD_ESTATE"}
+PRECISIONS = {"fp64": MHD_FP64, "fp32": MHD_FP32, "fp16s": MHD_FP16S}
+
+
+class mhd_params(ctypes.Structure):
+    _fields_ = [("rho0", ctypes.c_double), ("tau_f", ctypes.c_double), ("tau_m", ctypes.c_double),
+                ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int), ("precision", ctypes.c_int),
+                ("eq_variant", ctypes.c_int), ("collision", ctypes.c_int)]
+
+
+TOTAL_FIELDS = ("mass", "mom_x", "mom_y", "e_kin", "e_mag", "cross_hel", "bsum_x", "bsum_y",
+                "divb_max", "divb_rms", "jz_max", "omega_max")
+
+
+class mhd_totals(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in TOTAL_FIELDS] + [("step", ctypes.c_longlong)]
+
+
+class mhd_kernel_config(ctypes.Structure):
+    _fields_ = [("nodes_per_thread", ctypes.c_int), ("rows_per_block", ctypes.c_int)]
+
+
+class MhdError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+
+
+_lib = None
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+
+_SIGNATURES = {
+    "mhd_create": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(mhd_params), _P, ctypes.POINTER(_P)],
+    "mhd_set_fields": [_P, _D, _D, _D, _D, _D],
+    "mhd_advance": [_P, ctypes.c_longlong],
+    "mhd_get_fields": [_P, _D, _D, _D, _D, _D],
+    "mhd_get_totals": [_P, ctypes.POINTER(mhd_totals)],
+    "mhd_get_populations": [_P, _D, _D],
+    "mhd_set_populations": [_P, _D, _D],
+    "mhd_get_kernel_config": [_P, ctypes.POINTER(mhd_kernel_config)],
+    "mhd_set_kernel_config": [_P, ctypes.POINTER(mhd_kernel_config)],
+    "mhd_autotune": [_P, ctypes.POINTER(mhd_kernel_config)],
+    "mhd_destroy": [_P],
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load the library (raises if it was not built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        l = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGNATURES.items():
+            fn = getattr(l, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        l.mhd_last_error.argtypes = []
+        l.mhd_last_error.restype = ctypes.c_char_p
+        _lib = l
+    return _lib
+
+
+def check(status: int, where: str) -> None:
+    if status != MHD_OK:
+        raise MhdError(status, where, lib().mhd_last_error().decode())
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_D)
+
+
+def _in(a, n):
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    if arr.size != n:
+        raise ValueError(f"expected {n} values, got {arr.size}")
+    return arr
+
+
+class Lattice:
+    """One nx x ny lattice on the current CUDA device (owner of the C handle)."""
+
+    def __init__(self, nx: int, ny: int, tau_f: float, tau_m: float, precision="fp32",
+                 rho0: float = 1.0, wall_x: bool = False, wall_y: bool = False, eq_variant: int = 0,
+                 collision: int = MHD_RR, stream=None):
+        self.nx, self.ny = int(nx), int(ny)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.params = mhd_params(rho0, tau_f, tau_m, int(wall_x), int(wall_y), prec, eq_variant,
+                                 collision)
+        self._h = _P()
+        s = None if stream is None else _P(int(stream))
+        check(lib().mhd_create(self.nx, self.ny, ctypes.byref(self.params), s, ctypes.byref(self._h)),
+              "mhd_create")
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            check(lib().mhd_destroy(self._h), "mhd_destroy")
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_fields(self, ux, uy, bx, by, rho=None):
+        arrs = [_in(a, self.n) for a in (ux, uy, bx, by)]
+        r = None if rho is None else _in(rho, self.n)
+        check(lib().mhd_set_fields(self._h, *[_dptr(a) for a in arrs], _dptr(r)), "mhd_set_fields")
+
+    def advance(self, nsteps: int):
+        check(lib().mhd_advance(self._h, int(nsteps)), "mhd_advance")
+
+    def get_fields(self, out=None):
+        """rho, ux, uy, bx, by as a dict; `out` may give five C-contiguous
+        float64 arrays of nx*ny to fill instead (e.g. pinned host memory)."""
+        if out is None:
+            out = [np.empty((self.ny, self.nx)) for _ in range(5)]
+        for a in out:
+            if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or a.size != self.n:
+                raise ValueError("out arrays must be C-contiguous float64 of nx*ny")
+        check(lib().mhd_get_fields(self._h, *[_dptr(a) for a in out]), "mhd_get_fields")
+        return dict(zip(("rho", "ux", "uy", "bx", "by"), out))
+
+    def get_totals(self, check_stable: bool = True) -> dict:
+        t = mhd_totals()
+        st = lib().mhd_get_totals(self._h, ctypes.byref(t))
+        if st != MHD_EUNSTABLE or check_stable:
+            check(st, "mhd_get_totals")
+        d = {n: getattr(t, n) for n in TOTAL_FIELDS}
+        d["step"] = t.step
+        return d
+
+    def get_populations(self):
+        f = np.empty((9, self.ny, self.nx))
+        g = np.empty((5, 2, self.ny, self.nx))
+        check(lib().mhd_get_populations(self._h, _dptr(f), _dptr(g)), "mhd_get_populations")
+        return f, g
+
+    def set_populations(self, f, g):
+        fa = _in(f, 9 * self.n)
+        ga = _in(g, 10 * self.n)
+        check(lib().mhd_set_populations(self._h, _dptr(fa), _dptr(ga)), "mhd_set_populations")
+
+    @property
+    def kernel_config(self):
+        c = mhd_kernel_config()
+        check(lib().mhd_get_kernel_config(self._h, ctypes.byref(c)), "mhd_get_kernel_config")
+        return c.nodes_per_thread, c.rows_per_block
+
+    @kernel_config.setter
+    def kernel_config(self, v):
+        c = mhd_kernel_config(int(v[0]), int(v[1]))
+        check(lib().mhd_set_kernel_config(self._h, ctypes.byref(c)), "mhd_set_kernel_config")
+
+    def autotune(self):
+        c = mhd_kernel_config()
+        check(lib().mhd_autotune(self._h, ctypes.byref(c)), "mhd_autotune")
+        return c.nodes_per_thread, c.rows_per_block

@@ -1,0 +1,497 @@
+// api.cu -- C ABI of the single-lattice RR-MHD solver (declared in
+// include/mhd.h): argument checking, device buffers, CUDA-graph capture of
+// the step loop, diagnostics, checkpointing and the launch-shape autotuner.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/mhd.h"
+#include "internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+mhd_status fail(mhd_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+mhd_status cuda_fail(cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(e == cudaErrorMemoryAllocation ? MHD_ENOMEM : MHD_ECUDA, m);
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+constexpr int kGraphSteps = 64;  // steps per captured graph (even: ends on the same buffer)
+
+bool finite_array(const double* a, long long n) {
+    for (long long k = 0; k < n; ++k)
+        if (!std::isfinite(a[k])) return false;
+    return true;
+}
+
+}  // namespace
+
+struct mhd_lattice {
+    int nx = 0, ny = 0;
+    mhd_params p{};
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;
+    mhd::Layout L{};
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    bool fields_set = false;
+    bool prev_valid = false;  // buf[cur^1] holds the state the last step read
+    bool state_is_eq = false; // current state has zero non-equilibrium
+    long long step = 0;
+    double* io = nullptr;     // 5*n doubles, lazily allocated
+    double* partials = nullptr;
+    double* totals_d = nullptr;
+    double* totals_h = nullptr;  // pinned
+    mhd_kernel_config cfg{1, 8};
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+
+    long long n() const { return (long long)nx * ny; }
+    size_t buf_bytes() const { return (size_t)mhd::kStatePlanes * L.plane * L.esize; }
+};
+
+namespace {
+
+mhd::StepLaunch step_launch(const mhd_lattice* l, int from) {
+    mhd::StepLaunch s;
+    s.L = l->L;
+    s.prec = l->p.precision;
+    s.src = l->buf[from];
+    s.dst = l->buf[from ^ 1];
+    s.omega = 1.0 / l->p.tau_f;
+    s.omega_m = 1.0 / l->p.tau_m;
+    s.rho0 = l->p.rho0;
+    s.variant = l->p.eq_variant;
+    s.collision = l->p.collision;
+    s.wall_x = l->p.bc_x == MHD_WALL;
+    s.wall_y = l->p.bc_y == MHD_WALL;
+    s.V = l->cfg.nodes_per_thread;
+    s.BY = l->cfg.rows_per_block;
+    return s;
+}
+
+void drop_graphs(mhd_lattice* l) {
+    for (auto& g : l->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+mhd_kernel_config default_config(const mhd::Layout& L, int prec, int wall_x) {
+    mhd_kernel_config c;
+    int V = prec == 0 ? 2 : 4;
+    while (V > 1 && !mhd::step_shape_ok(L, prec, wall_x, V, 4)) V >>= 1;
+    c.nodes_per_thread = V;
+    c.rows_per_block = V == 1 ? 8 : 4;
+    return c;
+}
+
+bool config_ok(const mhd_lattice* l, const mhd_kernel_config& c) {
+    if (l->p.precision == 0 && c.rows_per_block > 8) return false;
+    return mhd::step_shape_ok(l->L, l->p.precision, l->p.bc_x == MHD_WALL, c.nodes_per_thread,
+                              c.rows_per_block);
+}
+
+mhd_status ensure_io(mhd_lattice* l) {
+    if (l->io) return MHD_OK;
+    CK(cudaMalloc(&l->io, sizeof(double) * 5 * (size_t)l->n()), "cudaMalloc(io)");
+    return MHD_OK;
+}
+
+// ---- tune cache: one JSON object, one "key": [V, BY] entry per line ----
+std::string cache_key(const mhd_lattice* l) {
+    cudaDeviceProp prop;
+    std::string name = "gpu";
+    if (cudaGetDeviceProperties(&prop, l->dev) == cudaSuccess) name = prop.name;
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s|p%d|%dx%d|bc%d%d", name.c_str(), l->p.precision, l->nx, l->ny,
+             l->p.bc_x, l->p.bc_y);
+    return buf;
+}
+
+std::map<std::string, std::pair<int, int>> read_cache(const char* path) {
+    std::map<std::string, std::pair<int, int>> m;
+    FILE* fp = fopen(path, "r");
+    if (!fp) return m;
+    char line[512];
+    while (fgets(line, sizeof line, fp)) {
+        char* q1 = strchr(line, '"');
+        if (!q1) continue;
+        char* q2 = strchr(q1 + 1, '"');
+        if (!q2) continue;
+        int v = 0, by = 0;
+        if (sscanf(q2 + 1, " : [%d , %d]", &v, &by) == 2) m[std::string(q1 + 1, q2)] = {v, by};
+    }
+    fclose(fp);
+    return m;
+}
+
+void write_cache(const char* path, const std::map<std::string, std::pair<int, int>>& m) {
+    std::string tmp = std::string(path) + ".tmp";
+    FILE* fp = fopen(tmp.c_str(), "w");
+    if (!fp) return;
+    fprintf(fp, "{\n");
+    size_t i = 0;
+    for (auto& kv : m)
+        fprintf(fp, "  \"%s\": [%d, %d]%s\n", kv.first.c_str(), kv.second.first, kv.second.second,
+                ++i < m.size() ? "," : "");
+    fprintf(fp, "}\n");
+    fclose(fp);
+    rename(tmp.c_str(), path);
+}
+
+mhd_status check_params(const mhd_params* p) {
+    if (!p) return fail(MHD_EINVAL, "params is NULL");
+    if (!(std::isfinite(p->tau_f) && p->tau_f > 0.5)) return fail(MHD_EINVAL, "tau_f must be > 1/2");
+    if (!(std::isfinite(p->tau_m) && p->tau_m > 0.5)) return fail(MHD_EINVAL, "tau_m must be > 1/2");
+    if (!(std::isfinite(p->rho0) && p->rho0 > 0)) return fail(MHD_EINVAL, "rho0 must be > 0");
+    if ((p->bc_x != MHD_PERIODIC && p->bc_x != MHD_WALL) || (p->bc_y != MHD_PERIODIC && p->bc_y != MHD_WALL))
+        return fail(MHD_EINVAL, "bc_x / bc_y must be MHD_PERIODIC or MHD_WALL");
+    if (p->precision < MHD_FP64 || p->precision > MHD_FP16S)
+        return fail(MHD_EINVAL, "unknown precision");
+    if (p->eq_variant != 0 && p->eq_variant != 1) return fail(MHD_EINVAL, "eq_variant must be 0 or 1");
+    if (p->collision != MHD_RR && p->collision != MHD_BGK) return fail(MHD_EINVAL, "unknown collision");
+    return MHD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mhd_last_error(void) { return g_err.c_str(); }
+
+mhd_status mhd_create(int nx, int ny, const mhd_params* p, void* stream, mhd_lattice** out) {
+    if (!out) return fail(MHD_EINVAL, "out is NULL");
+    *out = nullptr;
+    mhd_status s = check_params(p);
+    if (s != MHD_OK) return s;
+    if (nx < 2 || ny < 2) return fail(MHD_EINVAL, "nx and ny must be >= 2");
+    if ((long long)nx * ny > (1LL << 31)) return fail(MHD_EINVAL, "nx*ny must be <= 2^31");
+    auto* l = new (std::nothrow) mhd_lattice();
+    if (!l) return fail(MHD_ENOMEM, "host allocation failed");
+    l->nx = nx;
+    l->ny = ny;
+    l->p = *p;
+    l->stream = static_cast<cudaStream_t>(stream);
+    l->L = mhd::make_layout(nx, ny, p->precision);
+    cudaError_t e = cudaGetDevice(&l->dev);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&l->cap, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&l->buf[b], l->buf_bytes());
+    if (e == cudaSuccess)
+        e = cudaMalloc(&l->partials, sizeof(double) * mhd::kDiagSlots * mhd::diag_blocks(l->L));
+    if (e == cudaSuccess) e = cudaMalloc(&l->totals_d, sizeof(double) * mhd::kDiagSlots);
+    if (e == cudaSuccess) e = cudaMallocHost(&l->totals_h, sizeof(double) * mhd::kDiagSlots);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        mhd_destroy(l);
+        return cuda_fail(e, "mhd_create");
+    }
+    l->cfg = default_config(l->L, p->precision, p->bc_x == MHD_WALL);
+    if (const char* path = getenv("MHD_TUNE_CACHE")) {
+        auto m = read_cache(path);
+        auto it = m.find(cache_key(l));
+        if (it != m.end()) {
+            mhd_kernel_config c{it->second.first, it->second.second};
+            if (config_ok(l, c)) l->cfg = c;
+        }
+    }
+    *out = l;
+    return MHD_OK;
+}
+
+mhd_status mhd_destroy(mhd_lattice* l) {
+    if (!l) return fail(MHD_EINVAL, "lattice is NULL");
+    cudaSetDevice(l->dev);
+    if (l->stream || l->buf[0]) cudaStreamSynchronize(l->stream);
+    drop_graphs(l);
+    for (auto& b : l->buf)
+        if (b) cudaFree(b);
+    if (l->io) cudaFree(l->io);
+    if (l->partials) cudaFree(l->partials);
+    if (l->totals_d) cudaFree(l->totals_d);
+    if (l->totals_h) cudaFreeHost(l->totals_h);
+    if (l->cap) cudaStreamDestroy(l->cap);
+    delete l;
+    return MHD_OK;
+}
+
+mhd_status mhd_set_fields(mhd_lattice* l, const double* ux, const double* uy, const double* bx,
+                          const double* by, const double* rho) {
+    if (!l || !ux || !uy || !bx || !by) return fail(MHD_EINVAL, "NULL argument");
+    const long long n = l->n();
+    for (const double* a : {ux, uy, bx, by, rho})
+        if (a && !finite_array(a, n)) return fail(MHD_EINVAL, "non-finite input field");
+    if (rho)
+        for (long long k = 0; k < n; ++k)
+            if (!(rho[k] > 0)) return fail(MHD_EINVAL, "rho must be > 0");
+    CK(cudaSetDevice(l->dev), "cudaSetDevice");
+    mhd_status s = ensure_io(l);
+    if (s != MHD_OK) return s;
+    const size_t bytes = sizeof(double) * n;
+    double* d[5] = {l->io, l->io + n, l->io + 2 * n, l->io + 3 * n, l->io + 4 * n};
+    const double* h[5] = {ux, uy, bx, by, rho};
+    for (int q = 0; q < 5; ++q)
+        if (h[q]) CK(cudaMemcpyAsync(d[q], h[q], bytes, cudaMemcpyHostToDevice, l->stream), "H2D fields");
+    CK(mhd::launch_init(l->L, l->p.precision, l->buf[l->cur], rho ? d[4] : nullptr, d[0], d[1], d[2],
+                        d[3], l->p.rho0, l->p.eq_variant, l->stream),
+       "init kernel");
+    CK(cudaStreamSynchronize(l->stream), "mhd_set_fields");
+    l->step = 0;
+    l->fields_set = true;
+    l->prev_valid = false;
+    l->state_is_eq = true;
+    return MHD_OK;
+}
+
+static mhd_status capture_graph(mhd_lattice* l, int from) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(l->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    int c = from;
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k) {
+        le = mhd::launch_step(step_launch(l, c), l->cap);
+        c ^= 1;
+    }
+    cudaError_t ee = cudaStreamEndCapture(l->cap, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(le, "step launch during capture");
+    }
+    if (ee != cudaSuccess) return cuda_fail(ee, "end capture");
+    cudaError_t ie = cudaGraphInstantiate(&l->graph[from], g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return cuda_fail(ie, "graph instantiate");
+    return MHD_OK;
+}
+
+mhd_status mhd_advance(mhd_lattice* l, long long nsteps) {
+    if (!l) return fail(MHD_EINVAL, "lattice is NULL");
+    if (nsteps < 0) return fail(MHD_EINVAL, "nsteps must be >= 0");
+    if (!l->fields_set) return fail(MHD_ESTATE, "set fields or populations first");
+    if (nsteps == 0) return MHD_OK;
+    CK(cudaSetDevice(l->dev), "cudaSetDevice");
+    while (nsteps >= kGraphSteps) {
+        if (!l->graph[l->cur]) {
+            mhd_status s = capture_graph(l, l->cur);
+            if (s != MHD_OK) return s;
+        }
+        CK(cudaGraphLaunch(l->graph[l->cur], l->stream), "graph launch");
+        nsteps -= kGraphSteps;
+        l->step += kGraphSteps;
+    }
+    while (nsteps > 0) {
+        CK(mhd::launch_step(step_launch(l, l->cur), l->stream), "step launch");
+        l->cur ^= 1;
+        --nsteps;
+        ++l->step;
+    }
+    l->prev_valid = true;
+    l->state_is_eq = false;
+    return MHD_OK;
+}
+
+mhd_status mhd_get_fields(mhd_lattice* l, double* rho, double* ux, double* uy, double* bx, double* by) {
+    if (!l) return fail(MHD_EINVAL, "lattice is NULL");
+    if (!l->fields_set) return fail(MHD_ESTATE, "set fields or populations first");
+    CK(cudaSetDevice(l->dev), "cudaSetDevice");
+    mhd_status s = ensure_io(l);
+    if (s != MHD_OK) return s;
+    const long long n = l->n();
+    double* d[5] = {l->io, l->io + n, l->io + 2 * n, l->io + 3 * n, l->io + 4 * n};
+    double* h[5] = {rho, ux, uy, bx, by};
+    CK(mhd::launch_fields(l->L, l->p.precision, l->buf[l->cur], l->p.rho0, h[0] ? d[0] : nullptr,
+                          h[1] ? d[1] : nullptr, h[2] ? d[2] : nullptr, h[3] ? d[3] : nullptr,
+                          h[4] ? d[4] : nullptr, l->stream),
+       "fields kernel");
+    for (int q = 0; q < 5; ++q)
+        if (h[q])
+            CK(cudaMemcpyAsync(h[q], d[q], sizeof(double) * n, cudaMemcpyDeviceToHost, l->stream),
+               "D2H fields");
+    CK(cudaStreamSynchronize(l->stream), "mhd_get_fields");
+    return MHD_OK;
+}
+
+mhd_status mhd_get_totals(mhd_lattice* l, mhd_totals* out) {
+    if (!l || !out) return fail(MHD_EINVAL, "NULL argument");
+    if (!l->fields_set) return fail(MHD_ESTATE, "set fields or populations first");
+    CK(cudaSetDevice(l->dev), "cudaSetDevice");
+    mhd::DiagLaunch d;
+    d.L = l->L;
+    d.prec = l->p.precision;
+    d.prev = l->buf[l->cur ^ 1];
+    d.cur = l->buf[l->cur];
+    d.mode = l->prev_valid ? 0 : 1;
+    d.omega_m = 1.0 / l->p.tau_m;
+    d.rho0 = l->p.rho0;
+    const double om1 = 1.0 - d.omega_m;
+    d.neq_scale = (l->state_is_eq || std::fabs(om1) < 1e-12) ? 0.0 : 1.0 / om1;
+    d.wall_x = l->p.bc_x == MHD_WALL;
+    d.wall_y = l->p.bc_y == MHD_WALL;
+    CK(mhd::launch_diag(d, l->partials, l->totals_d, l->stream), "diagnostics kernel");
+    CK(cudaMemcpyAsync(l->totals_h, l->totals_d, sizeof(double) * mhd::kDiagSlots,
+                       cudaMemcpyDeviceToHost, l->stream),
+       "D2H totals");
+    CK(cudaStreamSynchronize(l->stream), "mhd_get_totals");
+    const double* t = l->totals_h;
+    const double n = (double)l->n();
+    out->mass = t[0];
+    out->mom_x = t[1];
+    out->mom_y = t[2];
+    out->e_kin = t[3] / n;
+    out->e_mag = t[4] / n;
+    out->cross_hel = t[5] / n;
+    out->bsum_x = t[6];
+    out->bsum_y = t[7];
+    out->divb_rms = t[9] > 0 ? std::sqrt(t[8] / t[9]) : 0.0;
+    out->divb_max = t[10];
+    out->jz_max = t[11];
+    out->omega_max = t[12];
+    out->step = l->step;
+    for (int s = 0; s < mhd::kDiagSlots; ++s)
+        if (!std::isfinite(t[s])) return fail(MHD_EUNSTABLE, "non-finite diagnostics: the run blew up");
+    return MHD_OK;
+}
+
+mhd_status mhd_get_populations(mhd_lattice* l, double* f, double* g) {
+    if (!l || !f || !g) return fail(MHD_EINVAL, "NULL argument");
+    if (!l->fields_set) return fail(MHD_ESTATE, "set fields or populations first");
+    CK(cudaSetDevice(l->dev), "cudaSetDevice");
+    mhd_status s = ensure_io(l);
+    if (s != MHD_OK) return s;
+    const long long n = l->n();
+    for (int p = 0; p < mhd::kStatePlanes; ++p) {
+        double* host = p < 9 ? f + (long long)p * n : g + (long long)(p - 9) * n;
+        CK(mhd::launch_plane_out(l->L, l->p.precision, l->buf[l->cur], p, l->p.rho0, l->io, l->stream),
+           "plane out kernel");
+        CK(cudaMemcpyAsync(host, l->io, sizeof(double) * n, cudaMemcpyDeviceToHost, l->stream),
+           "D2H populations");
+        CK(cudaStreamSynchronize(l->stream), "mhd_get_populations");
+    }
+    return MHD_OK;
+}
+
+mhd_status mhd_set_populations(mhd_lattice* l, const double* f, const double* g) {
+    if (!l || !f || !g) return fail(MHD_EINVAL, "NULL argument");
+    const long long n = l->n();
+    if (!finite_array(f, 9 * n) || !finite_array(g, 10 * n))
+        return fail(MHD_EINVAL, "non-finite populations");
+    CK(cudaSetDevice(l->dev), "cudaSetDevice");
+    mhd_status s = ensure_io(l);
+    if (s != MHD_OK) return s;
+    for (int p = 0; p < mhd::kStatePlanes; ++p) {
+        const double* host = p < 9 ? f + (long long)p * n : g + (long long)(p - 9) * n;
+        CK(cudaMemcpyAsync(l->io, host, sizeof(double) * n, cudaMemcpyHostToDevice, l->stream),
+           "H2D populations");
+        CK(mhd::launch_plane_in(l->L, l->p.precision, l->buf[l->cur], p, l->p.rho0, l->io, l->stream),
+           "plane in kernel");
+        CK(cudaStreamSynchronize(l->stream), "mhd_set_populations");
+    }
+    l->fields_set = true;
+    l->prev_valid = false;
+    l->state_is_eq = false;
+    return MHD_OK;
+}
+
+mhd_status mhd_get_kernel_config(const mhd_lattice* l, mhd_kernel_config* out) {
+    if (!l || !out) return fail(MHD_EINVAL, "NULL argument");
+    *out = l->cfg;
+    return MHD_OK;
+}
+
+mhd_status mhd_set_kernel_config(mhd_lattice* l, const mhd_kernel_config* cfg) {
+    if (!l || !cfg) return fail(MHD_EINVAL, "NULL argument");
+    if (!config_ok(l, *cfg)) return fail(MHD_EINVAL, "launch shape not valid for this lattice");
+    if (cfg->nodes_per_thread != l->cfg.nodes_per_thread || cfg->rows_per_block != l->cfg.rows_per_block) {
+        CK(cudaStreamSynchronize(l->stream), "mhd_set_kernel_config");
+        drop_graphs(l);
+        l->cfg = *cfg;
+    }
+    return MHD_OK;
+}
+
+mhd_status mhd_autotune(mhd_lattice* l, mhd_kernel_config* best) {
+    if (!l) return fail(MHD_EINVAL, "lattice is NULL");
+    CK(cudaSetDevice(l->dev), "cudaSetDevice");
+    const char* path = getenv("MHD_TUNE_CACHE");
+    const std::string key = cache_key(l);
+    if (path) {
+        auto m = read_cache(path);
+        auto it = m.find(key);
+        if (it != m.end()) {
+            mhd_kernel_config c{it->second.first, it->second.second};
+            if (config_ok(l, c)) {
+                mhd_status s = mhd_set_kernel_config(l, &c);
+                if (best) *best = l->cfg;
+                return s;
+            }
+        }
+    }
+    CK(cudaStreamSynchronize(l->stream), "mhd_autotune");
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    mhd_kernel_config chosen = l->cfg;
+    float best_ms = 1e30f;
+    const mhd_kernel_config saved = l->cfg;
+    const int iters = 20;
+    for (int V : {1, 2, 4}) {
+        for (int BY : {1, 2, 4, 8, 16}) {
+            mhd_kernel_config c{V, BY};
+            if (!config_ok(l, c)) continue;
+            l->cfg = c;
+            mhd::StepLaunch s = step_launch(l, l->cur);  // reads cur, writes the spare buffer
+            cudaError_t err = cudaSuccess;
+            for (int k = 0; k < 3 && err == cudaSuccess; ++k) err = mhd::launch_step(s, l->stream);
+            if (err == cudaSuccess) err = cudaEventRecord(e0, l->stream);
+            for (int k = 0; k < iters && err == cudaSuccess; ++k) err = mhd::launch_step(s, l->stream);
+            if (err == cudaSuccess) err = cudaEventRecord(e1, l->stream);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            if (err != cudaSuccess) {
+                l->cfg = saved;
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return cuda_fail(err, "autotune candidate");
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                chosen = c;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    l->cfg = saved;
+    l->prev_valid = false;  // the spare buffer was overwritten
+    mhd_status s = mhd_set_kernel_config(l, &chosen);
+    if (s != MHD_OK) return s;
+    if (path) {
+        auto m = read_cache(path);
+        m[key] = {chosen.nodes_per_thread, chosen.rows_per_block};
+        write_cache(path, m);
+    }
+    if (best) *best = l->cfg;
+    return MHD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,71 @@
+// internal.h -- host-side declarations shared by the library's translation
+// units (kernel launchers and layout).  Not part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace mhd {
+
+constexpr int kStatePlanes = 19;  // 9 f_i + 5 x 2 g_{j,a} per buffer
+
+// Geometry of one population buffer: 19 planes of ny rows x pitch elements.
+struct Layout {
+    int nx, ny;
+    long long pitch;  // elements per row (multiple of 128 bytes)
+    long long plane;  // elements per plane (ny * pitch rounded to 256 bytes)
+    int esize;        // bytes per stored element (8, 4, 2)
+};
+
+// Everything a step launch needs.  Doubles are converted to the compute
+// type inside the launcher.
+struct StepLaunch {
+    Layout L;
+    int prec;  // 0 fp64, 1 fp32, 2 fp16s
+    const void* src;
+    void* dst;
+    double omega, omega_m, rho0;
+    int variant, collision, wall_x, wall_y;
+    int V;   // nodes per thread along x
+    int BY;  // warps (rows) per block
+};
+
+// fused stream + collide (one time step)
+cudaError_t launch_step(const StepLaunch& s, cudaStream_t st);
+// is (V, BY) a legal launch shape for this lattice?
+bool step_shape_ok(const Layout& L, int prec, int wall_x, int V, int BY);
+
+// f = f_eq(rho, u, b), g = g_eq(u, b) from device FP64 fields (rho may be null)
+cudaError_t launch_init(const Layout& L, int prec, void* buf, const double* rho, const double* ux,
+                        const double* uy, const double* bx, const double* by, double rho0,
+                        int variant, cudaStream_t st);
+// rho, u, b (FP64, nx*ny each, any may be null) of the stored state
+cudaError_t launch_fields(const Layout& L, int prec, const void* buf, double rho0, double* rho,
+                          double* ux, double* uy, double* bx, double* by, cudaStream_t st);
+// one plane <-> unshifted FP64 array of nx*ny (population p = 0..18)
+cudaError_t launch_plane_out(const Layout& L, int prec, const void* buf, int p, double rho0,
+                             double* out, cudaStream_t st);
+cudaError_t launch_plane_in(const Layout& L, int prec, void* buf, int p, double rho0,
+                            const double* in, cudaStream_t st);
+
+// Diagnostics.  mode 0: gather the pre-collision state from `prev` (the
+// buffer the last step read); mode 1: use `cur` in place, with the
+// magnetic non-equilibrium scaled by neq_scale.  Writes kDiagSlots doubles
+// per block into `partials`, then reduces them in a fixed order into
+// `totals` (kDiagSlots doubles).
+constexpr int kDiagSlots = 13;
+struct DiagLaunch {
+    Layout L;
+    int prec;
+    const void* prev;
+    const void* cur;
+    int mode;
+    double omega_m, rho0, neq_scale;
+    int wall_x, wall_y;
+};
+int diag_blocks(const Layout& L);
+cudaError_t launch_diag(const DiagLaunch& d, double* partials, double* totals, cudaStream_t st);
+
+Layout make_layout(int nx, int ny, int prec);
+
+}  // namespace mhd

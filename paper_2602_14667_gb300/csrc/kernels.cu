@@ -1,0 +1,546 @@
+// kernels.cu -- sm_103a kernels of the fused RR-MHD lattice Boltzmann step
+// and their launchers.
+//
+// One kernel launch per time step (pull scheme): each thread gathers the
+// post-collision populations f*_i(x - c_i, t-1), g*_j(x - e_j, t-1) of the
+// previous step (task 6, streaming, read in pull form), runs tasks 1-5 of
+// the paper's "Algorithm of computation" in registers, and writes f*(x, t),
+// g*(x, t) to the other buffer.  Half-way bounce-back on wall axes:
+// a population whose source node lies outside the lattice is the node's own
+// post-collision population of the opposite direction.
+//
+// step_vec: periodic x axis, V consecutive x nodes per thread, one warp per
+// row segment of 32*V nodes.  Every plane is read with aligned V-wide
+// vector loads; the +-1 x shift of the moving populations is done with a
+// warp shuffle (lane l takes the neighbour lane's edge element), and only
+// the lanes at a warp or lattice edge issue one extra scalar load.  Stores
+// are aligned V-wide vectors.  HBM traffic is one read and one write of
+// the 19 planes.
+// step_gen: any boundary (x walls too), one node per thread, scalar loads
+// (the nodes_per_thread = 1 shape).
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "lbm_device.cuh"
+
+namespace mhd {
+
+template <typename C> struct StepArgs {
+    const void* src;
+    void* dst;
+    int nx, ny;
+    long long pitch, plane;
+    NodeParams<C> np;
+    int wall_x, wall_y;
+};
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int PREC, int V>
+__global__ void __launch_bounds__(512) step_vec(const StepArgs<typename Prec<PREC>::C> a) {
+    using S = typename Prec<PREC>::S;
+    using C = typename Prec<PREC>::C;
+    const int lane = threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (y >= a.ny) return;  // whole warp (one row per warp)
+    const int nx = a.nx, ny = a.ny;
+    const int x0 = (blockIdx.x * 32 + lane) * V;
+    const bool active = x0 < nx;
+    const S* __restrict__ src = static_cast<const S*>(a.src);
+    S* __restrict__ dst = static_cast<S*>(a.dst);
+
+    int ym = y - 1, yp = y + 1;
+    bool bm = false, bp = false;
+    if (a.wall_y) {
+        bm = ym < 0;
+        bp = yp >= ny;
+    } else {
+        if (ym < 0) ym += ny;
+        if (yp >= ny) yp -= ny;
+    }
+    const int xl = (x0 == 0) ? nx - 1 : x0 - 1;          // source column for c_x = +1 at x0
+    const int xr = (x0 + V >= nx) ? x0 + V - nx : x0 + V;  // source column for c_x = -1 at x0+V-1
+    const bool right_by_shfl = (lane < 31) && (x0 + V < nx);
+    const long long rowy = (long long)y * a.pitch;
+
+    C v[kPlanes][V];
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        const int cx = pcx(p), cy = pcy(p);
+        const bool bounce = cy > 0 ? bm : (cy < 0 ? bp : false);  // uniform over the warp
+        if (bounce) {
+            S r[V];
+            if (active) VecIO<S, V>::load(src + (long long)popp(p) * a.plane + rowy + x0, r);
+#pragma unroll
+            for (int k = 0; k < V; ++k) v[p][k] = active ? decode(r[k]) : C(0);
+            continue;
+        }
+        const int sy = cy > 0 ? ym : (cy < 0 ? yp : y);
+        const S* row = src + (long long)p * a.plane + (long long)sy * a.pitch;
+        S r[V];
+        C c[V];
+        if (active) VecIO<S, V>::load(row + x0, r);
+#pragma unroll
+        for (int k = 0; k < V; ++k) c[k] = active ? decode(r[k]) : C(0);
+        if (cx == 0) {
+#pragma unroll
+            for (int k = 0; k < V; ++k) v[p][k] = c[k];
+        } else if (cx > 0) {  // source x - 1
+            C left = __shfl_up_sync(kFull, c[V - 1], 1);
+            if (lane == 0 && active) left = decode(row[xl]);
+            v[p][0] = left;
+#pragma unroll
+            for (int k = 1; k < V; ++k) v[p][k] = c[k - 1];
+        } else {  // source x + 1
+            C right = __shfl_down_sync(kFull, c[0], 1);
+            if (!right_by_shfl && active) right = decode(row[xr]);
+#pragma unroll
+            for (int k = 0; k < V - 1; ++k) v[p][k] = c[k + 1];
+            v[p][V - 1] = right;
+        }
+    }
+    if (!active) return;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        C f[9], g[10];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = v[i][k];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) g[q] = v[9 + q][k];
+        collide(f, g, a.np);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) v[i][k] = f[i];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) v[9 + q][k] = g[q];
+    }
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        S r[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) encode(v[p][k], r[k]);
+        VecIO<S, V>::store(dst + (long long)p * a.plane + rowy + x0, r);
+    }
+}
+
+// Pre-collision populations of node (x, y) gathered from a post-collision
+// buffer (pull streaming with half-way bounce-back on wall axes).
+template <typename S, typename C>
+__device__ __forceinline__ void gather_node(const S* __restrict__ src, int x, int y, int nx, int ny,
+                                            long long pitch, long long plane, int wall_x,
+                                            int wall_y, C (&f)[9], C (&g)[10]) {
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        int sx = x - pcx(p), sy = y - pcy(p);
+        const bool out = (wall_x && (sx < 0 || sx >= nx)) || (wall_y && (sy < 0 || sy >= ny));
+        long long off;
+        if (out) {
+            off = (long long)popp(p) * plane + (long long)y * pitch + x;
+        } else {
+            sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+            sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+            off = (long long)p * plane + (long long)sy * pitch + sx;
+        }
+        const C val = decode(src[off]);
+        if (p < 9) f[p] = val; else g[p - 9] = val;
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(512) step_gen(const StepArgs<typename Prec<PREC>::C> a) {
+    using S = typename Prec<PREC>::S;
+    using C = typename Prec<PREC>::C;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.nx || y >= a.ny) return;
+    C f[9], g[10];
+    gather_node(static_cast<const S*>(a.src), x, y, a.nx, a.ny, a.pitch, a.plane, a.wall_x, a.wall_y,
+                f, g);
+    collide(f, g, a.np);
+    S* dst = static_cast<S*>(a.dst);
+    const long long o = (long long)y * a.pitch + x;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) encode(f[i], dst[(long long)i * a.plane + o]);
+#pragma unroll
+    for (int q = 0; q < 10; ++q) encode(g[q], dst[(long long)(9 + q) * a.plane + o]);
+}
+
+template <int PREC>
+static cudaError_t launch_step_t(const StepLaunch& s, cudaStream_t st) {
+    using C = typename Prec<PREC>::C;
+    StepArgs<C> a;
+    a.src = s.src;
+    a.dst = s.dst;
+    a.nx = s.L.nx;
+    a.ny = s.L.ny;
+    a.pitch = s.L.pitch;
+    a.plane = s.L.plane;
+    a.np.omega = C(s.omega);
+    a.np.omega_m = C(s.omega_m);
+    a.np.rho0 = C(s.rho0);
+    a.np.variant = s.variant;
+    a.np.collision = s.collision;
+    a.wall_x = s.wall_x;
+    a.wall_y = s.wall_y;
+    dim3 block(32, s.BY);
+    const int cols = 32 * s.V;
+    dim3 grid((s.L.nx + cols - 1) / cols, (s.L.ny + s.BY - 1) / s.BY);
+    switch (s.V) {
+    case 1: step_gen<PREC><<<grid, block, 0, st>>>(a); break;
+    case 2: step_vec<PREC, 2><<<grid, block, 0, st>>>(a); break;
+    case 4:
+        if constexpr (PREC != 0) {
+            step_vec<PREC, 4><<<grid, block, 0, st>>>(a);
+            break;
+        }
+        return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+bool step_shape_ok(const Layout& L, int prec, int wall_x, int V, int BY) {
+    if (BY < 1 || BY > 16) return false;
+    if (V != 1 && V != 2 && V != 4) return false;
+    if (prec == 0 && V > 2) return false;
+    if (wall_x && V != 1) return false;
+    if (L.nx % V) return false;
+    return true;
+}
+
+cudaError_t launch_step(const StepLaunch& s, cudaStream_t st) {
+    if (!step_shape_ok(s.L, s.prec, s.wall_x, s.V, s.BY)) return cudaErrorInvalidValue;
+    switch (s.prec) {
+    case 0: return launch_step_t<0>(s, st);
+    case 1: return launch_step_t<1>(s, st);
+    case 2: return launch_step_t<2>(s, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ---- state conversion kernels ------------------------------------------
+
+__device__ __forceinline__ void encode_d(double v, double& s) { s = v; }
+__device__ __forceinline__ void encode_d(double v, float& s) { s = __double2float_rn(v); }
+__device__ __forceinline__ void encode_d(double v, __half& s) { s = __double2half(v * 4096.0); }
+
+template <int PREC>
+__global__ void init_kernel(Layout L, void* buf, const double* rho, const double* ux,
+                            const double* uy, const double* bx, const double* by, double rho0,
+                            int variant) {
+    using S = typename Prec<PREC>::S;
+    const long long n = (long long)L.nx * L.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / L.nx), x = (int)(k % L.nx);
+        double f[9], g[10];
+        equilibrium<double>(rho ? rho[k] : rho0, ux[k], uy[k], bx[k], by[k], rho0, variant, f, g);
+        S* b = static_cast<S*>(buf);
+        const long long o = (long long)y * L.pitch + x;
+        for (int i = 0; i < 9; ++i) encode_d(f[i], b[(long long)i * L.plane + o]);
+        for (int q = 0; q < 10; ++q) encode_d(g[q], b[(long long)(9 + q) * L.plane + o]);
+    }
+}
+
+template <int PREC>
+__global__ void fields_kernel(Layout L, const void* buf, double rho0, double* rho, double* ux,
+                              double* uy, double* bx, double* by) {
+    using S = typename Prec<PREC>::S;
+    const long long n = (long long)L.nx * L.ny;
+    const S* b = static_cast<const S*>(buf);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / L.nx), x = (int)(k % L.nx);
+        const long long o = (long long)y * L.pitch + x;
+        double f[9], g[10];
+        for (int i = 0; i < 9; ++i) f[i] = (double)decode(b[(long long)i * L.plane + o]);
+        for (int q = 0; q < 10; ++q) g[q] = (double)decode(b[(long long)(9 + q) * L.plane + o]);
+        const Moments<double> m = moments<double>(f, g, rho0);
+        if (rho) rho[k] = m.rho;
+        if (ux) ux[k] = m.ux;
+        if (uy) uy[k] = m.uy;
+        if (bx) bx[k] = m.bx;
+        if (by) by[k] = m.by;
+    }
+}
+
+template <int PREC>
+__global__ void plane_out_kernel(Layout L, const void* buf, int p, double shift, double* out) {
+    using S = typename Prec<PREC>::S;
+    const long long n = (long long)L.nx * L.ny;
+    const S* b = static_cast<const S*>(buf) + (long long)p * L.plane;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / L.nx), x = (int)(k % L.nx);
+        out[k] = (double)decode(b[(long long)y * L.pitch + x]) + shift;
+    }
+}
+
+template <int PREC>
+__global__ void plane_in_kernel(Layout L, void* buf, int p, double shift, const double* in) {
+    using S = typename Prec<PREC>::S;
+    const long long n = (long long)L.nx * L.ny;
+    S* b = static_cast<S*>(buf) + (long long)p * L.plane;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / L.nx), x = (int)(k % L.nx);
+        encode_d(in[k] - shift, b[(long long)y * L.pitch + x]);
+    }
+}
+
+static dim3 flat_grid(long long n) {
+    long long b = (n + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < 1) b = 1;
+    return dim3((unsigned)b);
+}
+
+#define MHD_DISPATCH(prec, KERNEL, grid, block, st, ...)                  \
+    do {                                                                  \
+        switch (prec) {                                                   \
+        case 0: KERNEL<0><<<grid, block, 0, st>>>(__VA_ARGS__); break;    \
+        case 1: KERNEL<1><<<grid, block, 0, st>>>(__VA_ARGS__); break;    \
+        case 2: KERNEL<2><<<grid, block, 0, st>>>(__VA_ARGS__); break;    \
+        default: return cudaErrorInvalidValue;                            \
+        }                                                                 \
+    } while (0)
+
+cudaError_t launch_init(const Layout& L, int prec, void* buf, const double* rho, const double* ux,
+                        const double* uy, const double* bx, const double* by, double rho0,
+                        int variant, cudaStream_t st) {
+    MHD_DISPATCH(prec, init_kernel, flat_grid((long long)L.nx * L.ny), 256, st, L, buf, rho, ux, uy,
+                 bx, by, rho0, variant);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fields(const Layout& L, int prec, const void* buf, double rho0, double* rho,
+                          double* ux, double* uy, double* bx, double* by, cudaStream_t st) {
+    MHD_DISPATCH(prec, fields_kernel, flat_grid((long long)L.nx * L.ny), 256, st, L, buf, rho0, rho,
+                 ux, uy, bx, by);
+    return cudaGetLastError();
+}
+
+static double plane_shift(int p, double rho0) { return p < 9 ? w_of(p) * rho0 : 0.0; }
+
+cudaError_t launch_plane_out(const Layout& L, int prec, const void* buf, int p, double rho0,
+                             double* out, cudaStream_t st) {
+    MHD_DISPATCH(prec, plane_out_kernel, flat_grid((long long)L.nx * L.ny), 256, st, L, buf, p,
+                 plane_shift(p, rho0), out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plane_in(const Layout& L, int prec, void* buf, int p, double rho0,
+                            const double* in, cudaStream_t st) {
+    MHD_DISPATCH(prec, plane_in_kernel, flat_grid((long long)L.nx * L.ny), 256, st, L, buf, p,
+                 plane_shift(p, rho0), in);
+    return cudaGetLastError();
+}
+
+// ---- diagnostics ----------------------------------------------------------
+// Block tile of 32 x 8 nodes; the moments of the tile plus a one-node halo
+// are staged in shared memory for the isotropic gradient stencil.  Per-node
+// contributions are accumulated in FP64, reduced with warp shuffles, then
+// across warps in shared memory, into kDiagSlots partials per block:
+//   0 mass, 1 mom_x, 2 mom_y, 3 sum |u|^2/2, 4 sum |b|^2/2, 5 sum u.b,
+//   6 sum b_x, 7 sum b_y, 8 sum (div b)^2, 9 #gradient nodes,
+//   10 max |div b|, 11 max |j_z|, 12 max |omega_z|.
+constexpr int kDTX = 32, kDTY = 8, kDHX = kDTX + 2, kDHY = kDTY + 2;
+
+template <typename C> struct DiagArgs {
+    const void* prev;
+    const void* cur;
+    int nx, ny;
+    long long pitch, plane;
+    C omega_m, rho0, neq_scale;
+    int wall_x, wall_y;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(kFull, v, o));
+    return v;
+}
+
+template <int PREC, int MODE>
+__global__ void __launch_bounds__(256) diag_kernel(const DiagArgs<typename Prec<PREC>::C> a,
+                                                   double* __restrict__ partials) {
+    using S = typename Prec<PREC>::S;
+    using C = typename Prec<PREC>::C;
+    __shared__ C sm[4][kDHY][kDHX];  // ux, uy, bx, by
+    __shared__ double red[8][kDiagSlots];
+    const int tid = threadIdx.y * kDTX + threadIdx.x;
+    const int tx0 = blockIdx.x * kDTX, ty0 = blockIdx.y * kDTY;
+    double acc[kDiagSlots];
+#pragma unroll
+    for (int s = 0; s < kDiagSlots; ++s) acc[s] = 0.0;
+
+    for (int r = tid; r < kDHX * kDHY; r += kDTX * kDTY) {
+        const int hx = r % kDHX, hy = r / kDHX;
+        int gx = tx0 - 1 + hx, gy = ty0 - 1 + hy;
+        const bool interior = hx >= 1 && hx <= kDTX && hy >= 1 && hy <= kDTY && gx < a.nx && gy < a.ny;
+        bool have = true;
+        if (a.wall_x) have = have && gx >= 0 && gx < a.nx;
+        else gx = ((gx % a.nx) + a.nx) % a.nx;
+        if (a.wall_y) have = have && gy >= 0 && gy < a.ny;
+        else gy = ((gy % a.ny) + a.ny) % a.ny;
+        C ux = 0, uy = 0, bx = 0, by = 0;
+        if (have) {
+            C f[9], g[10];
+            if (MODE == 0) {
+                gather_node(static_cast<const S*>(a.prev), gx, gy, a.nx, a.ny, a.pitch, a.plane,
+                            a.wall_x, a.wall_y, f, g);
+            } else {
+                const S* b = static_cast<const S*>(a.cur);
+                const long long o = (long long)gy * a.pitch + gx;
+#pragma unroll
+                for (int p = 0; p < kPlanes; ++p) {
+                    const C val = decode(b[(long long)p * a.plane + o]);
+                    if (p < 9) f[p] = val; else g[p - 9] = val;
+                }
+            }
+            const Moments<C> m = moments(f, g, a.rho0);
+            ux = m.ux; uy = m.uy; bx = m.bx; by = m.by;
+            if (interior) {
+                const double rho = (double)m.rho, dux = (double)ux, duy = (double)uy;
+                const double dbx = (double)bx, dby = (double)by;
+                acc[0] += rho;
+                acc[1] += rho * dux;
+                acc[2] += rho * duy;
+                acc[3] += 0.5 * (dux * dux + duy * duy);
+                acc[4] += 0.5 * (dbx * dbx + dby * dby);
+                acc[5] += dux * dbx + duy * dby;
+                acc[6] += dbx;
+                acc[7] += dby;
+                const C jz = current_density(g, ux, uy, bx, by, a.omega_m, a.neq_scale);
+                acc[11] = fmax(acc[11], fabs((double)jz));
+            }
+        }
+        sm[0][hy][hx] = ux; sm[1][hy][hx] = uy; sm[2][hy][hx] = bx; sm[3][hy][hx] = by;
+    }
+    __syncthreads();
+    {
+        const int lx = threadIdx.x, ly = threadIdx.y;
+        const int x = tx0 + lx, y = ty0 + ly;
+        bool ok = x < a.nx && y < a.ny;
+        if (a.wall_x) ok = ok && x >= 1 && x <= a.nx - 2;
+        if (a.wall_y) ok = ok && y >= 1 && y <= a.ny - 2;
+        if (ok) {
+            // d_a phi = 3 sum_i w_i phi(x + c_i) c_ia
+            auto dx = [&](int q) {
+                const C e = sm[q][ly + 1][lx + 2] - sm[q][ly + 1][lx];
+                const C d = (sm[q][ly + 2][lx + 2] - sm[q][ly + 2][lx]) + (sm[q][ly][lx + 2] - sm[q][ly][lx]);
+                return (double)(C(1.0 / 3.0) * e + C(1.0 / 12.0) * d);
+            };
+            auto dy = [&](int q) {
+                const C e = sm[q][ly + 2][lx + 1] - sm[q][ly][lx + 1];
+                const C d = (sm[q][ly + 2][lx + 2] - sm[q][ly][lx + 2]) + (sm[q][ly + 2][lx] - sm[q][ly][lx]);
+                return (double)(C(1.0 / 3.0) * e + C(1.0 / 12.0) * d);
+            };
+            const double div = dx(2) + dy(3);
+            const double vort = dx(1) - dy(0);
+            acc[8] += div * div;
+            acc[9] += 1.0;
+            acc[10] = fmax(acc[10], fabs(div));
+            acc[12] = fmax(acc[12], fabs(vort));
+        }
+    }
+    const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+    for (int s = 0; s < kDiagSlots; ++s) {
+        const double v = s < 10 ? warp_sum(acc[s]) : warp_max(acc[s]);
+        if (lane == 0) red[warp][s] = v;
+    }
+    __syncthreads();
+    if (tid < kDiagSlots) {
+        double v = red[0][tid];
+        for (int w = 1; w < 8; ++w) v = tid < 10 ? v + red[w][tid] : fmax(v, red[w][tid]);
+        partials[(long long)(blockIdx.y * gridDim.x + blockIdx.x) * kDiagSlots + tid] = v;
+    }
+}
+
+// Fixed-order final reduction of the per-block partials (one block).
+__global__ void __launch_bounds__(256) diag_final(const double* __restrict__ partials, int nblocks,
+                                                  double* __restrict__ totals) {
+    __shared__ double red[8][kDiagSlots];
+    double acc[kDiagSlots];
+#pragma unroll
+    for (int s = 0; s < kDiagSlots; ++s) acc[s] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+#pragma unroll
+        for (int s = 0; s < kDiagSlots; ++s) {
+            const double v = partials[(long long)b * kDiagSlots + s];
+            acc[s] = s < 10 ? acc[s] + v : fmax(acc[s], v);
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int s = 0; s < kDiagSlots; ++s) {
+        const double v = s < 10 ? warp_sum(acc[s]) : warp_max(acc[s]);
+        if (lane == 0) red[warp][s] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kDiagSlots) {
+        const int s = threadIdx.x;
+        double v = red[0][s];
+        for (int w = 1; w < 8; ++w) v = s < 10 ? v + red[w][s] : fmax(v, red[w][s]);
+        totals[s] = v;
+    }
+}
+
+int diag_blocks(const Layout& L) {
+    return ((L.nx + kDTX - 1) / kDTX) * ((L.ny + kDTY - 1) / kDTY);
+}
+
+template <int PREC>
+static cudaError_t launch_diag_t(const DiagLaunch& d, double* partials, cudaStream_t st) {
+    using C = typename Prec<PREC>::C;
+    DiagArgs<C> a;
+    a.prev = d.prev;
+    a.cur = d.cur;
+    a.nx = d.L.nx;
+    a.ny = d.L.ny;
+    a.pitch = d.L.pitch;
+    a.plane = d.L.plane;
+    a.omega_m = C(d.omega_m);
+    a.rho0 = C(d.rho0);
+    a.neq_scale = C(d.neq_scale);
+    a.wall_x = d.wall_x;
+    a.wall_y = d.wall_y;
+    dim3 block(kDTX, kDTY);
+    dim3 grid((d.L.nx + kDTX - 1) / kDTX, (d.L.ny + kDTY - 1) / kDTY);
+    if (d.mode == 0) diag_kernel<PREC, 0><<<grid, block, 0, st>>>(a, partials);
+    else diag_kernel<PREC, 1><<<grid, block, 0, st>>>(a, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diag(const DiagLaunch& d, double* partials, double* totals, cudaStream_t st) {
+    cudaError_t e;
+    switch (d.prec) {
+    case 0: e = launch_diag_t<0>(d, partials, st); break;
+    case 1: e = launch_diag_t<1>(d, partials, st); break;
+    case 2: e = launch_diag_t<2>(d, partials, st); break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    diag_final<<<1, 256, 0, st>>>(partials, diag_blocks(d.L), totals);
+    return cudaGetLastError();
+}
+
+Layout make_layout(int nx, int ny, int prec) {
+    Layout L;
+    L.nx = nx;
+    L.ny = ny;
+    L.esize = prec == 0 ? 8 : (prec == 1 ? 4 : 2);
+    const long long row_align = 128 / L.esize;
+    L.pitch = (nx + row_align - 1) / row_align * row_align;
+    const long long pl_align = 256 / L.esize;
+    L.plane = ((long long)ny * L.pitch + pl_align - 1) / pl_align * pl_align;
+    return L;
+}
+
+}  // namespace mhd

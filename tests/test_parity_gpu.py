@@ -1,0 +1,309 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (fixed for the method's configurations):
+  * FP64 storage: fields within 1e-12 relative L2 after 100 steps of the
+    64^2 Orszag-Tang vortex (nu = eta = 0.01); populations element-wise.
+  * FP32 storage: populations within 2e-6 max-abs after one step from an
+    identical state; rho, u, b within 1e-4 relative L2 after 1000 steps.
+  * FP16S storage: one step within the half rounding bound (see
+    test_fp16s_one_step); field error after 1000 steps reported and bounded.
+Sizes span several thread blocks with ragged tails; every launch shape is
+exercised; walls and both equilibrium variants and the BGK switch are
+covered.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+OT_TAU = 0.53  # nu = eta = 0.01
+
+
+def _lat(nx, ny, prec, tau_f=OT_TAU, tau_m=OT_TAU, **kw):
+    from paper_2602_14667_gb300 import Lattice
+    return Lattice(nx, ny, tau_f, tau_m, precision=prec, **kw)
+
+
+def _ot(nx, ny=None, amp=0.05):
+    import mhd_inputs
+    return mhd_inputs.orszag_tang(nx, amp, amp, ny)
+
+
+def _rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _oracle_state(orc, p, fields, steps):
+    f, g = orc.init(p, *fields)
+    return orc.run(p, f, g, steps)
+
+
+def _pert_state(orc, p, seed):
+    """A random non-equilibrium pre-collision state of the oracle."""
+    rng = np.random.default_rng(seed)
+    ny, nx = p.ny, p.nx
+    ux, uy, bx, by = (rng.uniform(-0.06, 0.06, (ny, nx)) for _ in range(4))
+    f, g = orc.init(p, ux, uy, bx, by, rho=rng.uniform(0.95, 1.05, (ny, nx)))
+    f = f + rng.normal(0, 3e-4, f.shape) * np.array([4 / 9] + [1 / 36, 1 / 9] * 4)[:, None, None]
+    g = g + rng.normal(0, 3e-4, g.shape)
+    return f, g
+
+
+def _gpu_one_step(lat, orc, p, f_pre, g_pre):
+    """Load the post-collision state P = collide(pre) into the GPU, run one
+    step, return (gpu, oracle) post-collision states of the next step."""
+    fs, gs = orc.collide(p, f_pre, g_pre)
+    lat.set_populations(fs, gs)
+    lat.advance(1)
+    fg, gg = lat.get_populations()
+    f1, g1 = orc.stream(p, fs, gs)
+    fo, go = orc.collide(p, f1, g1)
+    return (fg, gg), (fo, go)
+
+
+# ---------------------------------------------------------------- FP64 -----
+
+@pytest.mark.parametrize("steps,tol", [(100, 1e-12), (1000, 1e-12)])
+def test_fp64_orszag_tang_64(orc, steps, tol):
+    n = 64
+    fields = _ot(n)
+    p = orc.Params(n, n, OT_TAU, OT_TAU)
+    ref = orc.fields(p, *_oracle_state(orc, p, fields, steps))
+    with _lat(n, n, "fp64") as lat:
+        lat.set_fields(*fields)
+        lat.advance(steps)
+        got = lat.get_fields()
+    for name, r in zip(("rho", "ux", "uy", "bx", "by"), ref):
+        assert _rel_l2(got[name], r) < tol, (name, _rel_l2(got[name], r))
+
+
+@pytest.mark.parametrize("nx,ny,wx,wy,variant,collision", [
+    (64, 64, False, False, 1, 0),
+    (37, 29, False, False, 0, 0),    # ragged: V = 1 path, odd sizes
+    (96, 40, False, True, 0, 0),     # y walls, vector path
+    (30, 34, True, True, 1, 0),      # walls on both axes
+    (66, 18, False, False, 0, 1),    # BGK fluid collision
+    (2, 2, False, False, 0, 0),      # smallest lattice
+])
+def test_fp64_populations_elementwise(orc, nx, ny, wx, wy, variant, collision):
+    steps = 50
+    p = orc.Params(nx, ny, 0.56, 0.71, wall_x=wx, wall_y=wy, eq_variant=variant, collision=collision)
+    fields = _ot(nx, ny)
+    f, g = _oracle_state(orc, p, fields, steps)
+    fo, go = orc.collide(p, f, g)  # GPU buffer holds post-collision populations
+    with _lat(nx, ny, "fp64", 0.56, 0.71, wall_x=wx, wall_y=wy, eq_variant=variant,
+              collision=collision) as lat:
+        lat.set_fields(*fields)
+        lat.advance(steps)
+        fg, gg = lat.get_populations()
+    np.testing.assert_allclose(fg, fo, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(gg, go, rtol=0, atol=1e-14)
+
+
+def test_fp64_totals_match_oracle(orc):
+    n = 64
+    fields = _ot(n)
+    p = orc.Params(n, n, OT_TAU, OT_TAU)
+    f, g = _oracle_state(orc, p, fields, 200)
+    ref = orc.totals(p, f, g)
+    with _lat(n, n, "fp64") as lat:
+        lat.set_fields(*fields)
+        t0 = lat.get_totals()
+        lat.advance(200)
+        got = lat.get_totals()
+    assert got["step"] == 200 and t0["jz_max"] == 0.0
+    for k, v in ref.items():
+        assert abs(got[k] - v) <= 1e-11 * max(abs(v), 1e-3), (k, got[k], v)
+
+
+def test_fp64_totals_with_walls(orc):
+    nx, ny = 40, 24
+    p = orc.Params(nx, ny, 0.6, 0.8, wall_y=True)
+    fields = _ot(nx, ny)
+    f, g = _oracle_state(orc, p, fields, 30)
+    ref = orc.totals(p, f, g)
+    with _lat(nx, ny, "fp64", 0.6, 0.8, wall_y=True) as lat:
+        lat.set_fields(*fields)
+        lat.advance(30)
+        got = lat.get_totals()
+    for k, v in ref.items():
+        assert abs(got[k] - v) <= 1e-11 * max(abs(v), 1e-3), (k, got[k], v)
+
+
+# ---------------------------------------------------------------- FP32 -----
+
+SHAPES_FP32 = [(1, 1), (1, 8), (2, 2), (2, 16), (4, 1), (4, 4), (4, 16)]
+
+
+@pytest.mark.parametrize("shape", SHAPES_FP32)
+@pytest.mark.parametrize("nx,ny,wy", [(256, 24, False), (136, 20, True), (4, 6, False)])
+def test_fp32_one_step_populations(orc, shape, nx, ny, wy):
+    V, BY = shape
+    if nx % V:
+        pytest.skip("nodes_per_thread must divide nx")
+    p = orc.Params(nx, ny, 0.5 + 3e-4, 0.51, wall_y=wy)
+    f_pre, g_pre = _pert_state(orc, p, seed=nx + ny)
+    with _lat(nx, ny, "fp32", 0.5 + 3e-4, 0.51, wall_y=wy) as lat:
+        lat.kernel_config = (V, BY)
+        (fg, gg), (fo, go) = _gpu_one_step(lat, orc, p, f_pre, g_pre)
+    assert np.abs(fg - fo).max() < 2e-6
+    assert np.abs(gg - go).max() < 2e-6
+
+
+def test_fp32_orszag_tang_1000_steps(orc):
+    n = 64
+    fields = _ot(n)
+    p = orc.Params(n, n, OT_TAU, OT_TAU)
+    ref = orc.fields(p, *_oracle_state(orc, p, fields, 1000))
+    with _lat(n, n, "fp32") as lat:
+        lat.set_fields(*fields)
+        lat.advance(1000)
+        got = lat.get_fields()
+    for name, r in zip(("rho", "ux", "uy", "bx", "by"), ref):
+        assert _rel_l2(got[name], r) < 1e-4, (name, _rel_l2(got[name], r))
+
+
+def test_fp32_walls_x_and_y_one_step(orc):
+    nx, ny = 33, 17
+    p = orc.Params(nx, ny, 0.7, 0.9, wall_x=True, wall_y=True, eq_variant=1)
+    f_pre, g_pre = _pert_state(orc, p, seed=5)
+    with _lat(nx, ny, "fp32", 0.7, 0.9, wall_x=True, wall_y=True, eq_variant=1) as lat:
+        (fg, gg), (fo, go) = _gpu_one_step(lat, orc, p, f_pre, g_pre)
+    assert np.abs(fg - fo).max() < 2e-6 and np.abs(gg - go).max() < 2e-6
+
+
+# --------------------------------------------------------------- FP16S -----
+
+def test_fp16s_one_step(orc):
+    """Stored values are 2^12 x (deviation) rounded to IEEE half: relative
+    error <= 2^-11 each.  One step reads rounded inputs (the collision is a
+    contraction with |1 - omega| <= 1 on the non-equilibrium part and
+    reproduces the equilibrium part to first order) and rounds its output
+    once more, so each output lies within a few half ulps of the largest
+    deviation: bound 4 x 2^-11 x max|deviation|."""
+    nx, ny = 128, 16
+    p = orc.Params(nx, ny, 0.5 + 3e-4, 0.51)
+    f_pre, g_pre = _pert_state(orc, p, seed=9)
+    w = np.array([4 / 9] + [1 / 36, 1 / 9] * 4)[:, None, None]
+    with _lat(nx, ny, "fp16s", 0.5 + 3e-4, 0.51) as lat:
+        (fg, gg), (fo, go) = _gpu_one_step(lat, orc, p, f_pre, g_pre)
+    dmax = max(np.abs(fo - w).max(), np.abs(go).max())
+    bound = 4 * 2.0 ** -11 * dmax
+    assert np.abs(fg - fo).max() < bound and np.abs(gg - go).max() < bound
+
+
+def test_fp16s_orszag_tang_field_error(orc):
+    n = 64
+    fields = _ot(n)
+    p = orc.Params(n, n, OT_TAU, OT_TAU)
+    ref = orc.fields(p, *_oracle_state(orc, p, fields, 1000))
+    with _lat(n, n, "fp16s") as lat:
+        lat.set_fields(*fields)
+        lat.advance(1000)
+        got = lat.get_fields()
+    errs = {name: _rel_l2(got[name], r) for name, r in zip(("ux", "uy", "bx", "by"), ref[1:])}
+    print("fp16s 64^2 OT rel L2 after 1000 steps:", errs)
+    assert max(errs.values()) < 2e-2
+
+
+# -------------------------------------------------- state handling / API -----
+
+def test_graph_and_single_launches_agree():
+    n = 96
+    fields = _ot(n)
+    with _lat(n, n, "fp32") as a, _lat(n, n, "fp32") as b:
+        a.set_fields(*fields); b.set_fields(*fields)
+        a.advance(128)          # two captured 64-step graphs
+        for _ in range(128):
+            b.advance(1)        # single launches
+        fa, ga = a.get_populations(); fb, gb = b.get_populations()
+    np.testing.assert_array_equal(fa, fb)
+    np.testing.assert_array_equal(ga, gb)
+
+
+def test_checkpoint_restart_is_bitwise():
+    n = 64
+    fields = _ot(n)
+    for prec in ("fp32", "fp16s", "fp64"):
+        with _lat(n, n, prec) as a, _lat(n, n, prec) as b:
+            a.set_fields(*fields)
+            a.advance(37)
+            f, g = a.get_populations()
+            b.set_populations(f, g)
+            a.advance(70); b.advance(70)
+            fa, ga = a.get_populations(); fb, gb = b.get_populations()
+        np.testing.assert_array_equal(fa, fb)
+        np.testing.assert_array_equal(ga, gb)
+
+
+def test_autotune_keeps_state_and_returns_valid_shape(tmp_path, monkeypatch):
+    monkeypatch.setenv("MHD_TUNE_CACHE", str(tmp_path / "tune.json"))
+    n = 128
+    fields = _ot(n)
+    with _lat(n, n, "fp32") as a:
+        a.set_fields(*fields)
+        a.advance(10)
+        before = a.get_populations()
+        shape = a.autotune()
+        assert shape in [(v, by) for v in (1, 2, 4) for by in (1, 2, 4, 8, 16)]
+        after = a.get_populations()
+        np.testing.assert_array_equal(before[0], after[0])
+        assert a.kernel_config == shape
+    assert (tmp_path / "tune.json").exists()
+    with _lat(n, n, "fp32") as b:       # a new lattice picks the cached shape
+        assert b.kernel_config == shape
+
+
+def test_conservation_over_many_steps():
+    n = 256
+    fields = _ot(n, amp=0.04)
+    with _lat(n, n, "fp32", 0.50006, 0.50006) as lat:
+        lat.set_fields(*fields)
+        t0 = lat.get_totals()
+        lat.advance(500)
+        t1 = lat.get_totals()
+    assert abs(t1["mass"] - t0["mass"]) < 1e-6 * t0["mass"]
+    assert abs(t1["mom_x"] - t0["mom_x"]) < 1e-6 * t0["mass"]
+    assert abs(t1["bsum_x"] - t0["bsum_x"]) < 1e-6 * n * n * 0.04
+    assert abs(t1["e_kin"] + t1["e_mag"] - t0["e_kin"] - t0["e_mag"]) < 0.01 * (t0["e_kin"] + t0["e_mag"])
+
+
+def test_errors_are_reported():
+    from paper_2602_14667_gb300 import Lattice, MhdError, _abi
+    with pytest.raises(MhdError, match="EINVAL"):
+        Lattice(16, 16, 0.5, 0.6)
+    with pytest.raises(MhdError, match="EINVAL"):
+        Lattice(1, 16, 0.6, 0.6)
+    with pytest.raises(MhdError, match="EINVAL"):
+        Lattice(65536, 65536, 0.6, 0.6)                # nx*ny > 2^31
+    with pytest.raises(MhdError, match="ENOMEM"):
+        Lattice(46000, 46000, 0.6, 0.6, precision="fp64")  # ~640 GB: refused by cudaMalloc
+    with _lat(8, 8, "fp32") as lat:
+        with pytest.raises(MhdError, match="ESTATE"):
+            lat.advance(1)
+        z = np.zeros((8, 8))
+        bad = z.copy(); bad[2, 3] = np.nan
+        with pytest.raises(MhdError, match="EINVAL"):
+            lat.set_fields(bad, z, z, z)
+        with pytest.raises(MhdError, match="EINVAL"):
+            lat.kernel_config = (3, 4)
+        with pytest.raises(MhdError, match="EINVAL"):
+            lat.advance(-1)
+
+
+def test_blow_up_is_reported_as_unstable():
+    """A vacuum node (all populations zero) gives u = 0/0 on the GPU; the
+    NaN spreads and the totals report MHD_EUNSTABLE (no device fault)."""
+    from paper_2602_14667_gb300 import MhdError
+    n = 16
+    w = np.array([4 / 9] + [1 / 36, 1 / 9] * 4)
+    f = np.tile(w[:, None, None], (1, n, n))
+    f[:, 5, 7] = 0.0
+    g = np.zeros((5, 2, n, n))
+    with _lat(n, n, "fp32") as lat:
+        lat.set_populations(f, g)
+        lat.advance(3)
+        with pytest.raises(MhdError, match="EUNSTABLE"):
+            lat.get_totals()
