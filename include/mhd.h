@@ -146,8 +146,22 @@ mhd_status mhd_get_totals(mhd_lattice* l, mhd_totals* out);
 mhd_status mhd_get_populations(mhd_lattice* l, double* f, double* g);
 
 /* Restore populations written by mhd_get_populations (same layout; values are
- * rounded to the storage precision).  The step counter is kept. */
+ * rounded to the storage precision).  The step counter is kept.  The FP64
+ * view round-trips exactly for MHD_FP32 and MHD_FP16S storage; for MHD_FP64
+ * storage to within one ulp (the shift w_i rho0 is added and removed in
+ * FP64) -- use mhd_get_state / mhd_set_state for a bitwise checkpoint. */
 mhd_status mhd_set_populations(mhd_lattice* l, const double* f, const double* g);
+
+/* Bitwise checkpoint of the stored state: the 19 planes exactly as stored
+ * (storage precision, FP32/FP16S/FP64 deviations f_i - w_i rho0 and g_{j,a},
+ * FP16S scaled by 2^12), plane after plane, each nx*ny elements without row
+ * padding.  *bytes = 19 * nx * ny * element size.  mhd_get_state waits for
+ * the stream; mhd_set_state makes the restored state current (resuming
+ * from it is bitwise identical to the run it was saved from).  host must
+ * hold exactly mhd_state_bytes bytes (MHD_EINVAL otherwise). */
+mhd_status mhd_state_bytes(const mhd_lattice* l, size_t* bytes);
+mhd_status mhd_get_state(mhd_lattice* l, void* host, size_t bytes);
+mhd_status mhd_set_state(mhd_lattice* l, const void* host, size_t bytes);
 
 /* Current launch shape, or set one explicitly (MHD_EINVAL if the shape is not
  * valid for this lattice). */

@@ -64,6 +64,9 @@ _SIGNATURES = {
     "mhd_set_kernel_config": [_P, ctypes.POINTER(mhd_kernel_config)],
     "mhd_autotune": [_P, ctypes.POINTER(mhd_kernel_config)],
     "mhd_destroy": [_P],
+    "mhd_state_bytes": [_P, ctypes.POINTER(ctypes.c_size_t)],
+    "mhd_get_state": [_P, _P, ctypes.c_size_t],
+    "mhd_set_state": [_P, _P, ctypes.c_size_t],
 }
 
 
@@ -181,6 +184,18 @@ class Lattice:
         fa = _in(f, 9 * self.n)
         ga = _in(g, 10 * self.n)
         check(lib().mhd_set_populations(self._h, _dptr(fa), _dptr(ga)), "mhd_set_populations")
+
+    def get_state(self) -> np.ndarray:
+        """Bitwise checkpoint of the stored planes (raw bytes, uint8)."""
+        nb = ctypes.c_size_t()
+        check(lib().mhd_state_bytes(self._h, ctypes.byref(nb)), "mhd_state_bytes")
+        buf = np.empty(nb.value, dtype=np.uint8)
+        check(lib().mhd_get_state(self._h, buf.ctypes.data_as(_P), nb.value), "mhd_get_state")
+        return buf
+
+    def set_state(self, buf: np.ndarray):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        check(lib().mhd_set_state(self._h, buf.ctypes.data_as(_P), buf.size), "mhd_set_state")
 
     @property
     def kernel_config(self):

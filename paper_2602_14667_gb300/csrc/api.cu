@@ -411,6 +411,50 @@ mhd_status mhd_set_populations(mhd_lattice* l, const double* f, const double* g)
     return MHD_OK;
 }
 
+mhd_status mhd_state_bytes(const mhd_lattice* l, size_t* bytes) {
+    if (!l || !bytes) return fail(MHD_EINVAL, "NULL argument");
+    *bytes = (size_t)mhd::kStatePlanes * (size_t)l->n() * (size_t)l->L.esize;
+    return MHD_OK;
+}
+
+mhd_status mhd_get_state(mhd_lattice* l, void* host, size_t bytes) {
+    size_t need = 0;
+    if (!host || mhd_state_bytes(l, &need) != MHD_OK) return fail(MHD_EINVAL, "NULL argument");
+    if (bytes != need) return fail(MHD_EINVAL, "state buffer has the wrong size");
+    if (!l->fields_set) return fail(MHD_ESTATE, "set fields or populations first");
+    CK(cudaSetDevice(l->dev), "cudaSetDevice");
+    const size_t es = l->L.esize, row = (size_t)l->nx * es;
+    for (int p = 0; p < mhd::kStatePlanes; ++p) {
+        char* dst = static_cast<char*>(host) + (size_t)p * l->n() * es;
+        const char* src = static_cast<const char*>(l->buf[l->cur]) + (size_t)p * l->L.plane * es;
+        CK(cudaMemcpy2DAsync(dst, row, src, (size_t)l->L.pitch * es, row, l->ny,
+                             cudaMemcpyDeviceToHost, l->stream),
+           "D2H state");
+    }
+    CK(cudaStreamSynchronize(l->stream), "mhd_get_state");
+    return MHD_OK;
+}
+
+mhd_status mhd_set_state(mhd_lattice* l, const void* host, size_t bytes) {
+    size_t need = 0;
+    if (!host || mhd_state_bytes(l, &need) != MHD_OK) return fail(MHD_EINVAL, "NULL argument");
+    if (bytes != need) return fail(MHD_EINVAL, "state buffer has the wrong size");
+    CK(cudaSetDevice(l->dev), "cudaSetDevice");
+    const size_t es = l->L.esize, row = (size_t)l->nx * es;
+    for (int p = 0; p < mhd::kStatePlanes; ++p) {
+        const char* src = static_cast<const char*>(host) + (size_t)p * l->n() * es;
+        char* dst = static_cast<char*>(l->buf[l->cur]) + (size_t)p * l->L.plane * es;
+        CK(cudaMemcpy2DAsync(dst, (size_t)l->L.pitch * es, src, row, row, l->ny,
+                             cudaMemcpyHostToDevice, l->stream),
+           "H2D state");
+    }
+    CK(cudaStreamSynchronize(l->stream), "mhd_set_state");
+    l->fields_set = true;
+    l->prev_valid = false;
+    l->state_is_eq = false;
+    return MHD_OK;
+}
+
 mhd_status mhd_get_kernel_config(const mhd_lattice* l, mhd_kernel_config* out) {
     if (!l || !out) return fail(MHD_EINVAL, "NULL argument");
     *out = l->cfg;

@@ -199,14 +199,25 @@ __device__ __forceinline__ void collide(C (&f)[9], C (&g)[10], const NodeParams<
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = feq[i] + om1 * (f[i] - feq[i]);
     }
+    // Mass and momentum are collision invariants (a1^(0) = a1^(1) = 0).  The
+    // weights 1/9, 1/36 are not representable, so the evaluated populations
+    // carry a systematic relative bias of ~1e-8 (FP32) in their mass and
+    // momentum; left alone it accumulates step after step.  Fold the
+    // (algebraically zero) residuals back: x / y momentum into the axis pairs
+    // (2, 6) / (4, 8), mass into the rest population.
+    const C rx = m.mx - ((f[5] + f[6] + f[7]) - (f[1] + f[2] + f[3]));
+    f[6] += C(0.5) * rx;
+    f[2] -= C(0.5) * rx;
+    const C ry = m.my - ((f[1] + f[7] + f[8]) - (f[3] + f[4] + f[5]));
+    f[8] += C(0.5) * ry;
+    f[4] -= C(0.5) * ry;
+    f[0] = m.drho - (((f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8])));
     // magnetic BGK (Eq. collide_g): g* = omega_m g_eq + (1 - omega_m) g,
     // g_eq_{j,a} = psi_j [b_a + 3 e_{j,c} (u_c b_a - u_a b_c)], E = ux by - uy bx
     const C E3 = C(3) * (ux * by - uy * bx);
     const C om = p.omega_m, omm1 = C(1) - p.omega_m;
-    const C q0 = C(1.0 / 3.0), q1 = C(1.0 / 6.0);
+    const C q1 = C(1.0 / 6.0);
     const C gbx = q1 * bx, gby = q1 * by;
-    g[0] = om * (q0 * bx) + omm1 * g[0];
-    g[1] = om * (q0 * by) + omm1 * g[1];
     g[2] = om * gbx + omm1 * g[2];               // j=1 (-1,0): x
     g[3] = om * (q1 * (by - E3)) + omm1 * g[3];  // j=1: y
     g[4] = om * (q1 * (bx + E3)) + omm1 * g[4];  // j=2 (0,-1): x
@@ -215,6 +226,10 @@ __device__ __forceinline__ void collide(C (&f)[9], C (&g)[10], const NodeParams<
     g[7] = om * (q1 * (by + E3)) + omm1 * g[7];  // j=3: y
     g[8] = om * (q1 * (bx - E3)) + omm1 * g[8];  // j=4 (0,+1): x
     g[9] = om * gby + omm1 * g[9];               // j=4: y
+    // rest population by difference: sum_j g*_j = b exactly (psi_0 + 4 psi_1
+    // = 1 + 6e-8 in FP32 would otherwise grow b by ~1e-7 per step)
+    g[0] = bx - ((g[2] + g[4]) + (g[6] + g[8]));
+    g[1] = by - ((g[3] + g[5]) + (g[7] + g[9]));
 }
 
 // Equilibrium deviations for given fields (initial state; a1 = 0).
