@@ -37,6 +37,7 @@ extern "C" {
 #endif
 
 typedef struct mhd_lattice mhd_lattice; /* opaque single lattice */
+typedef struct mhd_batch mhd_batch;     /* opaque ensemble of independent lattices */
 
 typedef enum {
     MHD_OK = 0,
@@ -173,13 +174,42 @@ mhd_status mhd_set_kernel_config(mhd_lattice* l, const mhd_kernel_config* cfg);
  * The state is not advanced (candidates read the current buffer and write
  * the spare one).  Results are cached per (GPU, precision, nx, ny, bc) in
  * the JSON file named by $MHD_TUNE_CACHE (no caching when unset); a cached
- * entry is reused without timing.  best (may be NULL) receives the choice. */
+ * entry is reused without timing.  best (may be NULL) receives the choice.
+ * With $MHD_TUNE_VERBOSE set, every candidate's time is printed to stderr. */
 mhd_status mhd_autotune(mhd_lattice* l, mhd_kernel_config* best);
 
 mhd_status mhd_destroy(mhd_lattice* l);
 
 /* Message of the last failed call in this thread ("" if none). */
 const char* mhd_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Batched ensemble: many independent periodic lattices of uneven sizes and
+ * relaxation times advanced by ONE persistent kernel launch per time step
+ * (a tile work-list over all lattices, as many blocks as fit on the GPU),
+ * the step loop captured in CUDA graphs of 64 steps.  Storage is FP32; each
+ * lattice i has its own params[i] (precision must be MHD_FP32 and both axes
+ * MHD_PERIODIC).  A lattice advanced in a batch is bitwise identical to the
+ * same lattice advanced alone with the same launch shape.  Same conventions
+ * as the single-lattice calls; index selects a lattice (0..count-1).
+ * ------------------------------------------------------------------------- */
+mhd_status mhd_batch_create(int count, const int* nx, const int* ny, const mhd_params* params,
+                            void* stream, mhd_batch** out);
+mhd_status mhd_batch_set_fields(mhd_batch* b, int index, const double* ux, const double* uy,
+                                const double* bx, const double* by, const double* rho);
+/* every lattice must have its fields set (MHD_ESTATE otherwise) */
+mhd_status mhd_batch_advance(mhd_batch* b, long long nsteps);
+mhd_status mhd_batch_get_fields(mhd_batch* b, int index, double* rho, double* ux, double* uy,
+                                double* bx, double* by);
+mhd_status mhd_batch_get_totals(mhd_batch* b, int index, mhd_totals* out);
+/* total number of nodes over all lattices */
+mhd_status mhd_batch_nodes(const mhd_batch* b, long long* nodes);
+/* launch shape (nodes_per_thread must divide every nx); autotune times every
+ * valid shape over the whole ensemble without advancing it */
+mhd_status mhd_batch_get_kernel_config(const mhd_batch* b, mhd_kernel_config* out);
+mhd_status mhd_batch_set_kernel_config(mhd_batch* b, const mhd_kernel_config* cfg);
+mhd_status mhd_batch_autotune(mhd_batch* b, mhd_kernel_config* best);
+mhd_status mhd_batch_destroy(mhd_batch* b);
 
 #ifdef __cplusplus
 }

@@ -77,17 +77,21 @@ def _spectral_modes(kmax: int):
 
 
 def _solenoidal(nx: int, ny: int, rng: SplitMix64, kmax: int, rms: float):
-    X, Y = grid(nx, ny)
-    vx = np.zeros((ny, nx))
-    vy = np.zeros((ny, nx))
+    """u = (d_y psi, -d_x psi) for psi = sum_k A(|k|) cos(k.x + phi_k), evaluated
+    on the grid as the inverse DFT of its sparse spectrum (the same values as
+    the direct sum of cosines, up to rounding)."""
+    cx = np.zeros((ny, nx), dtype=np.complex128)
+    cy = np.zeros((ny, nx), dtype=np.complex128)
     for kx, ky in _spectral_modes(kmax):
         kk = math.hypot(kx, ky)
         amp = kk ** (-7.0 / 3.0)
         phase = 2.0 * math.pi * rng.uniform()
-        s = np.sin(kx * X + ky * Y + phase)
-        # psi = amp cos(k.x + phase): d_y psi = -amp ky sin(.), -d_x psi = amp kx sin(.)
-        vx += -amp * ky * s
-        vy += amp * kx * s
+        c = amp * complex(math.cos(phase), math.sin(phase))
+        # d_y cos(k.x + phi) = Re(i ky e^{i(k.x + phi)}); -d_x likewise with -i kx
+        cx[ky % ny, kx % nx] += 1j * ky * c
+        cy[ky % ny, kx % nx] += -1j * kx * c
+    vx = np.real(np.fft.ifft2(cx)) * (nx * ny)
+    vy = np.real(np.fft.ifft2(cy)) * (nx * ny)
     cur = math.sqrt(float(np.mean(vx * vx + vy * vy)))
     scale = rms / cur if cur > 0 else 0.0
     return vx * scale, vy * scale

@@ -65,6 +65,17 @@ _SIGNATURES = {
     "mhd_autotune": [_P, ctypes.POINTER(mhd_kernel_config)],
     "mhd_destroy": [_P],
     "mhd_state_bytes": [_P, ctypes.POINTER(ctypes.c_size_t)],
+    "mhd_batch_create": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                         ctypes.POINTER(mhd_params), _P, ctypes.POINTER(_P)],
+    "mhd_batch_set_fields": [_P, ctypes.c_int, _D, _D, _D, _D, _D],
+    "mhd_batch_advance": [_P, ctypes.c_longlong],
+    "mhd_batch_get_fields": [_P, ctypes.c_int, _D, _D, _D, _D, _D],
+    "mhd_batch_get_totals": [_P, ctypes.c_int, ctypes.POINTER(mhd_totals)],
+    "mhd_batch_nodes": [_P, ctypes.POINTER(ctypes.c_longlong)],
+    "mhd_batch_get_kernel_config": [_P, ctypes.POINTER(mhd_kernel_config)],
+    "mhd_batch_set_kernel_config": [_P, ctypes.POINTER(mhd_kernel_config)],
+    "mhd_batch_autotune": [_P, ctypes.POINTER(mhd_kernel_config)],
+    "mhd_batch_destroy": [_P],
     "mhd_get_state": [_P, _P, ctypes.c_size_t],
     "mhd_set_state": [_P, _P, ctypes.c_size_t],
 }
@@ -211,4 +222,97 @@ class Lattice:
     def autotune(self):
         c = mhd_kernel_config()
         check(lib().mhd_autotune(self._h, ctypes.byref(c)), "mhd_autotune")
+        return c.nodes_per_thread, c.rows_per_block
+
+
+def _totals_dict(t: "mhd_totals") -> dict:
+    d = {n: getattr(t, n) for n in TOTAL_FIELDS}
+    d["step"] = t.step
+    return d
+
+
+class Batch:
+    """Ensemble of independent periodic FP32 lattices advanced by one
+    persistent kernel launch per step (owner of the C handle).
+    sizes: list of (nx, ny); taus: list of (tau_f, tau_m)."""
+
+    def __init__(self, sizes, taus, rho0: float = 1.0, eq_variant: int = 0, collision: int = MHD_RR,
+                 stream=None):
+        self.sizes = [(int(a), int(b)) for a, b in sizes]
+        n = len(self.sizes)
+        if len(taus) != n:
+            raise ValueError("one (tau_f, tau_m) per lattice")
+        nx = (ctypes.c_int * n)(*[s[0] for s in self.sizes])
+        ny = (ctypes.c_int * n)(*[s[1] for s in self.sizes])
+        ps = (mhd_params * n)(*[mhd_params(rho0, tf, tm, MHD_PERIODIC, MHD_PERIODIC, MHD_FP32, eq_variant,
+                                           collision) for tf, tm in taus])
+        self._h = _P()
+        s = None if stream is None else _P(int(stream))
+        check(lib().mhd_batch_create(n, nx, ny, ps, s, ctypes.byref(self._h)), "mhd_batch_create")
+
+    def __len__(self):
+        return len(self.sizes)
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def nodes(self) -> int:
+        v = ctypes.c_longlong()
+        check(lib().mhd_batch_nodes(self._h, ctypes.byref(v)), "mhd_batch_nodes")
+        return v.value
+
+    def close(self):
+        if self._h:
+            check(lib().mhd_batch_destroy(self._h), "mhd_batch_destroy")
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_fields(self, i, ux, uy, bx, by, rho=None):
+        nx, ny = self.sizes[i]
+        arrs = [_in(a, nx * ny) for a in (ux, uy, bx, by)]
+        r = None if rho is None else _in(rho, nx * ny)
+        check(lib().mhd_batch_set_fields(self._h, int(i), *[_dptr(a) for a in arrs], _dptr(r)),
+              "mhd_batch_set_fields")
+
+    def advance(self, nsteps: int):
+        check(lib().mhd_batch_advance(self._h, int(nsteps)), "mhd_batch_advance")
+
+    def get_fields(self, i):
+        nx, ny = self.sizes[i]
+        out = [np.empty((ny, nx)) for _ in range(5)]
+        check(lib().mhd_batch_get_fields(self._h, int(i), *[_dptr(a) for a in out]), "mhd_batch_get_fields")
+        return dict(zip(("rho", "ux", "uy", "bx", "by"), out))
+
+    def get_totals(self, i) -> dict:
+        t = mhd_totals()
+        check(lib().mhd_batch_get_totals(self._h, int(i), ctypes.byref(t)), "mhd_batch_get_totals")
+        return _totals_dict(t)
+
+    @property
+    def kernel_config(self):
+        c = mhd_kernel_config()
+        check(lib().mhd_batch_get_kernel_config(self._h, ctypes.byref(c)), "mhd_batch_get_kernel_config")
+        return c.nodes_per_thread, c.rows_per_block
+
+    @kernel_config.setter
+    def kernel_config(self, v):
+        c = mhd_kernel_config(int(v[0]), int(v[1]))
+        check(lib().mhd_batch_set_kernel_config(self._h, ctypes.byref(c)), "mhd_batch_set_kernel_config")
+
+    def autotune(self):
+        c = mhd_kernel_config()
+        check(lib().mhd_batch_autotune(self._h, ctypes.byref(c)), "mhd_batch_autotune")
         return c.nodes_per_thread, c.rows_per_block

@@ -44,6 +44,8 @@ bool finite_array(const double* a, long long n) {
 
 }  // namespace
 
+void mhd::set_last_error(const std::string& msg) { g_err = msg; }
+
 struct mhd_lattice {
     int nx = 0, ny = 0;
     mhd_params p{};
@@ -343,7 +345,9 @@ mhd_status mhd_get_totals(mhd_lattice* l, mhd_totals* out) {
     d.omega_m = 1.0 / l->p.tau_m;
     d.rho0 = l->p.rho0;
     const double om1 = 1.0 - d.omega_m;
-    d.neq_scale = (l->state_is_eq || std::fabs(om1) < 1e-12) ? 0.0 : 1.0 / om1;
+    // gather mode reads the pre-collision g itself; the stored-state mode
+    // recovers g - g_eq = (g* - g_eq) / (1 - omega_m)
+    d.neq_scale = d.mode == 0 ? 1.0 : ((l->state_is_eq || std::fabs(om1) < 1e-12) ? 0.0 : 1.0 / om1);
     d.wall_x = l->p.bc_x == MHD_WALL;
     d.wall_y = l->p.bc_y == MHD_WALL;
     CK(mhd::launch_diag(d, l->partials, l->totals_d, l->stream), "diagnostics kernel");
@@ -517,6 +521,9 @@ mhd_status mhd_autotune(mhd_lattice* l, mhd_kernel_config* best) {
                 cudaEventDestroy(e1);
                 return cuda_fail(err, "autotune candidate");
             }
+            if (getenv("MHD_TUNE_VERBOSE"))
+                fprintf(stderr, "mhd_autotune %dx%d p%d V=%d BY=%d: %.4f ms/step\n", l->nx, l->ny,
+                        l->p.precision, V, BY, ms / iters);
             if (ms < best_ms) {
                 best_ms = ms;
                 chosen = c;

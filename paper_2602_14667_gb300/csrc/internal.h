@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <string>
+
 namespace mhd {
 
 constexpr int kStatePlanes = 19;  // 9 f_i + 5 x 2 g_{j,a} per buffer
@@ -67,5 +69,8 @@ int diag_blocks(const Layout& L);
 cudaError_t launch_diag(const DiagLaunch& d, double* partials, double* totals, cudaStream_t st);
 
 Layout make_layout(int nx, int ny, int prec);
+
+// message returned by mhd_last_error() in the calling thread
+void set_last_error(const std::string& msg);
 
 }  // namespace mhd

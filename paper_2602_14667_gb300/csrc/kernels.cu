@@ -10,140 +10,25 @@
 // post-collision population of the opposite direction.
 //
 // step_vec: periodic x axis, V consecutive x nodes per thread, one warp per
-// row segment of 32*V nodes.  Every plane is read with aligned V-wide
-// vector loads; the +-1 x shift of the moving populations is done with a
-// warp shuffle (lane l takes the neighbour lane's edge element), and only
-// the lanes at a warp or lattice edge issue one extra scalar load.  Stores
-// are aligned V-wide vectors.  HBM traffic is one read and one write of
-// the 19 planes.
-// step_gen: any boundary (x walls too), one node per thread, scalar loads
-// (the nodes_per_thread = 1 shape).
+// row segment of 32*V nodes (step_row.cuh).  HBM traffic is one read and
+// one write of the 19 planes.
+// step_gen: x walls (any boundary), one node per thread, scalar loads.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "internal.h"
 #include "lbm_device.cuh"
+#include "step_row.cuh"
 
 namespace mhd {
-
-template <typename C> struct StepArgs {
-    const void* src;
-    void* dst;
-    int nx, ny;
-    long long pitch, plane;
-    NodeParams<C> np;
-    int wall_x, wall_y;
-};
-
-constexpr unsigned kFull = 0xffffffffu;
 
 template <int PREC, int V>
 __global__ void __launch_bounds__(512) step_vec(const StepArgs<typename Prec<PREC>::C> a) {
     using S = typename Prec<PREC>::S;
-    using C = typename Prec<PREC>::C;
-    const int lane = threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (y >= a.ny) return;  // whole warp (one row per warp)
-    const int nx = a.nx, ny = a.ny;
-    const int x0 = (blockIdx.x * 32 + lane) * V;
-    const bool active = x0 < nx;
-    const S* __restrict__ src = static_cast<const S*>(a.src);
-    S* __restrict__ dst = static_cast<S*>(a.dst);
-
-    int ym = y - 1, yp = y + 1;
-    bool bm = false, bp = false;
-    if (a.wall_y) {
-        bm = ym < 0;
-        bp = yp >= ny;
-    } else {
-        if (ym < 0) ym += ny;
-        if (yp >= ny) yp -= ny;
-    }
-    const int xl = (x0 == 0) ? nx - 1 : x0 - 1;          // source column for c_x = +1 at x0
-    const int xr = (x0 + V >= nx) ? x0 + V - nx : x0 + V;  // source column for c_x = -1 at x0+V-1
-    const bool right_by_shfl = (lane < 31) && (x0 + V < nx);
-    const long long rowy = (long long)y * a.pitch;
-
-    C v[kPlanes][V];
-#pragma unroll
-    for (int p = 0; p < kPlanes; ++p) {
-        const int cx = pcx(p), cy = pcy(p);
-        const bool bounce = cy > 0 ? bm : (cy < 0 ? bp : false);  // uniform over the warp
-        if (bounce) {
-            S r[V];
-            if (active) VecIO<S, V>::load(src + (long long)popp(p) * a.plane + rowy + x0, r);
-#pragma unroll
-            for (int k = 0; k < V; ++k) v[p][k] = active ? decode(r[k]) : C(0);
-            continue;
-        }
-        const int sy = cy > 0 ? ym : (cy < 0 ? yp : y);
-        const S* row = src + (long long)p * a.plane + (long long)sy * a.pitch;
-        S r[V];
-        C c[V];
-        if (active) VecIO<S, V>::load(row + x0, r);
-#pragma unroll
-        for (int k = 0; k < V; ++k) c[k] = active ? decode(r[k]) : C(0);
-        if (cx == 0) {
-#pragma unroll
-            for (int k = 0; k < V; ++k) v[p][k] = c[k];
-        } else if (cx > 0) {  // source x - 1
-            C left = __shfl_up_sync(kFull, c[V - 1], 1);
-            if (lane == 0 && active) left = decode(row[xl]);
-            v[p][0] = left;
-#pragma unroll
-            for (int k = 1; k < V; ++k) v[p][k] = c[k - 1];
-        } else {  // source x + 1
-            C right = __shfl_down_sync(kFull, c[0], 1);
-            if (!right_by_shfl && active) right = decode(row[xr]);
-#pragma unroll
-            for (int k = 0; k < V - 1; ++k) v[p][k] = c[k + 1];
-            v[p][V - 1] = right;
-        }
-    }
-    if (!active) return;
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-        C f[9], g[10];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = v[i][k];
-#pragma unroll
-        for (int q = 0; q < 10; ++q) g[q] = v[9 + q][k];
-        collide(f, g, a.np);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) v[i][k] = f[i];
-#pragma unroll
-        for (int q = 0; q < 10; ++q) v[9 + q][k] = g[q];
-    }
-#pragma unroll
-    for (int p = 0; p < kPlanes; ++p) {
-        S r[V];
-#pragma unroll
-        for (int k = 0; k < V; ++k) encode(v[p][k], r[k]);
-        VecIO<S, V>::store(dst + (long long)p * a.plane + rowy + x0, r);
-    }
-}
-
-// Pre-collision populations of node (x, y) gathered from a post-collision
-// buffer (pull streaming with half-way bounce-back on wall axes).
-template <typename S, typename C>
-__device__ __forceinline__ void gather_node(const S* __restrict__ src, int x, int y, int nx, int ny,
-                                            long long pitch, long long plane, int wall_x,
-                                            int wall_y, C (&f)[9], C (&g)[10]) {
-#pragma unroll
-    for (int p = 0; p < kPlanes; ++p) {
-        int sx = x - pcx(p), sy = y - pcy(p);
-        const bool out = (wall_x && (sx < 0 || sx >= nx)) || (wall_y && (sy < 0 || sy >= ny));
-        long long off;
-        if (out) {
-            off = (long long)popp(p) * plane + (long long)y * pitch + x;
-        } else {
-            sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
-            sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
-            off = (long long)p * plane + (long long)sy * pitch + sx;
-        }
-        const C val = decode(src[off]);
-        if (p < 9) f[p] = val; else g[p - 9] = val;
-    }
+    step_row<PREC, V>(static_cast<const S*>(a.src), static_cast<S*>(a.dst), a.nx, a.ny, a.pitch,
+                      a.plane, a.np, a.wall_y, blockIdx.x, y, threadIdx.x);
 }
 
 template <int PREC>
@@ -186,7 +71,10 @@ static cudaError_t launch_step_t(const StepLaunch& s, cudaStream_t st) {
     const int cols = 32 * s.V;
     dim3 grid((s.L.nx + cols - 1) / cols, (s.L.ny + s.BY - 1) / s.BY);
     switch (s.V) {
-    case 1: step_gen<PREC><<<grid, block, 0, st>>>(a); break;
+    case 1:
+        if (s.wall_x) step_gen<PREC><<<grid, block, 0, st>>>(a);
+        else step_vec<PREC, 1><<<grid, block, 0, st>>>(a);
+        break;
     case 2: step_vec<PREC, 2><<<grid, block, 0, st>>>(a); break;
     case 4:
         if constexpr (PREC != 0) {

@@ -1,0 +1,135 @@
+// step_row.cuh -- the per-row body of the fused pull-scheme step, shared by
+// the single-lattice kernel and the batched persistent kernel.
+//
+// One warp updates 32*V consecutive x nodes of row y: every plane is read
+// with aligned V-wide vector loads; the +-1 x shift of the moving
+// populations is done with warp shuffles (lane l takes the neighbour lane's
+// edge element) and only the lanes at a warp or lattice edge issue one extra
+// scalar load.  Pull streaming with half-way bounce-back on y walls; the x
+// axis is periodic.  Stores are aligned V-wide vectors.
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace mhd {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename C> struct StepArgs {
+    const void* src;
+    void* dst;
+    int nx, ny;
+    long long pitch, plane;
+    NodeParams<C> np;
+    int wall_x, wall_y;
+};
+
+// Requires nx % V == 0, all 32 lanes of the warp present, y < ny.
+template <int PREC, int V>
+__device__ __forceinline__ void step_row(const typename Prec<PREC>::S* __restrict__ src,
+                                         typename Prec<PREC>::S* __restrict__ dst, int nx, int ny,
+                                         long long pitch, long long plane,
+                                         const NodeParams<typename Prec<PREC>::C>& np, int wall_y,
+                                         int xblock, int y, int lane) {
+    using S = typename Prec<PREC>::S;
+    using C = typename Prec<PREC>::C;
+    const int x0 = (xblock * 32 + lane) * V;
+    const bool active = x0 < nx;
+
+    int ym = y - 1, yp = y + 1;
+    bool bm = false, bp = false;
+    if (wall_y) {
+        bm = ym < 0;
+        bp = yp >= ny;
+    } else {
+        if (ym < 0) ym += ny;
+        if (yp >= ny) yp -= ny;
+    }
+    const int xl = (x0 == 0) ? nx - 1 : x0 - 1;          // source column for c_x = +1 at x0
+    const int xr = (x0 + V >= nx) ? x0 + V - nx : x0 + V;  // source column for c_x = -1 at x0+V-1
+    const bool right_by_shfl = (lane < 31) && (x0 + V < nx);
+    const long long rowy = (long long)y * pitch;
+
+    C v[kPlanes][V];
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        const int cx = pcx(p), cy = pcy(p);
+        const bool bounce = cy > 0 ? bm : (cy < 0 ? bp : false);  // uniform over the warp
+        if (bounce) {
+            S r[V];
+            if (active) VecIO<S, V>::load(src + (long long)popp(p) * plane + rowy + x0, r);
+#pragma unroll
+            for (int k = 0; k < V; ++k) v[p][k] = active ? decode(r[k]) : C(0);
+            continue;
+        }
+        const int sy = cy > 0 ? ym : (cy < 0 ? yp : y);
+        const S* row = src + (long long)p * plane + (long long)sy * pitch;
+        S r[V];
+        C c[V];
+        if (active) VecIO<S, V>::load(row + x0, r);
+#pragma unroll
+        for (int k = 0; k < V; ++k) c[k] = active ? decode(r[k]) : C(0);
+        if (cx == 0) {
+#pragma unroll
+            for (int k = 0; k < V; ++k) v[p][k] = c[k];
+        } else if (cx > 0) {  // source x - 1
+            C left = __shfl_up_sync(kFull, c[V - 1], 1);
+            if (lane == 0 && active) left = decode(row[xl]);
+            v[p][0] = left;
+#pragma unroll
+            for (int k = 1; k < V; ++k) v[p][k] = c[k - 1];
+        } else {  // source x + 1
+            C right = __shfl_down_sync(kFull, c[0], 1);
+            if (!right_by_shfl && active) right = decode(row[xr]);
+#pragma unroll
+            for (int k = 0; k < V - 1; ++k) v[p][k] = c[k + 1];
+            v[p][V - 1] = right;
+        }
+    }
+    if (!active) return;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        C f[9], g[10];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = v[i][k];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) g[q] = v[9 + q][k];
+        collide(f, g, np);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) v[i][k] = f[i];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) v[9 + q][k] = g[q];
+    }
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        S r[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) encode(v[p][k], r[k]);
+        VecIO<S, V>::store(dst + (long long)p * plane + rowy + x0, r);
+    }
+}
+
+// Pre-collision populations of node (x, y) gathered from a post-collision
+// buffer (pull streaming with half-way bounce-back on wall axes).
+template <typename S, typename C>
+__device__ __forceinline__ void gather_node(const S* __restrict__ src, int x, int y, int nx, int ny,
+                                            long long pitch, long long plane, int wall_x,
+                                            int wall_y, C (&f)[9], C (&g)[10]) {
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        int sx = x - pcx(p), sy = y - pcy(p);
+        const bool out = (wall_x && (sx < 0 || sx >= nx)) || (wall_y && (sy < 0 || sy >= ny));
+        long long off;
+        if (out) {
+            off = (long long)popp(p) * plane + (long long)y * pitch + x;
+        } else {
+            sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+            sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+            off = (long long)p * plane + (long long)sy * pitch + sx;
+        }
+        const C val = decode(src[off]);
+        if (p < 9) f[p] = val; else g[p - 9] = val;
+    }
+}
+
+}  // namespace mhd

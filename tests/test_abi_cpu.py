@@ -104,6 +104,23 @@ def test_random_spectrum_is_solenoidal_band_limited_and_scaled():
     assert np.abs(other[0] - ux).max() > 1e-3
 
 
+def test_random_spectrum_equals_direct_sum_of_modes():
+    import mhd_inputs
+    nx, ny, kmax = 24, 20, 5
+    ux, uy, bx, by = mhd_inputs.random_spectrum(nx, ny, seed=77, rms_u=1.0, rms_b=1.0, kmax=kmax)
+    rng = mhd_inputs.SplitMix64(77)
+    X, Y = mhd_inputs.grid(nx, ny)
+    vx = np.zeros((ny, nx)); vy = np.zeros((ny, nx))
+    for kx, ky in mhd_inputs._spectral_modes(kmax):
+        a = math.hypot(kx, ky) ** (-7.0 / 3.0)
+        s = np.sin(kx * X + ky * Y + 2 * math.pi * rng.uniform())
+        vx += -a * ky * s
+        vy += a * kx * s
+    scale = 1.0 / math.sqrt(np.mean(vx ** 2 + vy ** 2))
+    np.testing.assert_allclose(ux, vx * scale, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(uy, vy * scale, rtol=0, atol=1e-12)
+
+
 def test_ensemble_draws():
     import mhd_inputs
     e = mhd_inputs.ensemble(512)

@@ -1,0 +1,92 @@
+"""GPU parity of the batched persistent ensemble kernel.
+
+Each lattice of a batch must be bitwise identical to the same lattice
+advanced alone through the single-lattice path with the same launch shape
+(the per-node arithmetic is shared), and within the FP32 tolerance of the
+FP64 oracle.  Sizes are uneven (several tiles, partial warps for widths
+below 32 x nodes_per_thread) and each lattice has its own nu and eta.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(64, 64), (96, 32), (32, 40), (128, 96), (64, 128)]
+TAUS = [(0.53, 0.56), (0.6, 0.52), (0.51, 0.7), (0.55, 0.55), (0.8, 0.9)]
+
+
+def _fields(i, nx, ny):
+    import mhd_inputs
+    return mhd_inputs.random_spectrum(nx, ny, seed=1000 + i, rms_u=0.02, rms_b=0.02)
+
+
+@pytest.mark.parametrize("shape", [(1, 4), (2, 8), (4, 2), (4, 16)])
+def test_batch_equals_single_lattices_bitwise(shape):
+    from paper_2602_14667_gb300 import Batch, Lattice
+    steps = 150
+    with Batch(SIZES, TAUS) as b:
+        b.kernel_config = shape
+        for i, (nx, ny) in enumerate(SIZES):
+            b.set_fields(i, *_fields(i, nx, ny))
+        b.advance(steps)
+        got = [b.get_fields(i) for i in range(len(SIZES))]
+    for i, (nx, ny) in enumerate(SIZES):
+        with Lattice(nx, ny, *TAUS[i], precision="fp32") as lat:
+            lat.kernel_config = shape
+            lat.set_fields(*_fields(i, nx, ny))
+            lat.advance(steps)
+            ref = lat.get_fields()
+        for k in ("rho", "ux", "uy", "bx", "by"):
+            np.testing.assert_array_equal(got[i][k], ref[k], err_msg=f"lattice {i} {k}")
+
+
+def test_batch_matches_oracle(orc):
+    from paper_2602_14667_gb300 import Batch
+    steps = 200
+    with Batch(SIZES, TAUS) as b:
+        for i, (nx, ny) in enumerate(SIZES):
+            b.set_fields(i, *_fields(i, nx, ny))
+        b.advance(steps)
+        for i, (nx, ny) in enumerate(SIZES):
+            p = orc.Params(nx, ny, *TAUS[i])
+            f, g = orc.run(p, *orc.init(p, *_fields(i, nx, ny)), steps)
+            ref = orc.fields(p, f, g)
+            got = b.get_fields(i)
+            for k, r in zip(("ux", "uy", "bx", "by"), ref[1:]):
+                err = np.linalg.norm(got[k] - r) / np.linalg.norm(r)
+                assert err < 1e-4, (i, k, err)
+            tot = b.get_totals(i)
+            otot = orc.totals(p, f, g)
+            assert abs(tot["mass"] - otot["mass"]) < 1e-5 * nx * ny
+            assert abs(tot["e_kin"] - otot["e_kin"]) < 1e-4 * otot["e_kin"]
+            assert abs(tot["jz_max"] - otot["jz_max"]) < 1e-3 * otot["jz_max"]
+
+
+def test_batch_autotune_keeps_state():
+    from paper_2602_14667_gb300 import Batch
+    with Batch(SIZES, TAUS) as b:
+        for i, (nx, ny) in enumerate(SIZES):
+            b.set_fields(i, *_fields(i, nx, ny))
+        b.advance(10)
+        before = [b.get_fields(i)["ux"] for i in range(len(SIZES))]
+        shape = b.autotune()
+        assert shape == b.kernel_config
+        after = [b.get_fields(i)["ux"] for i in range(len(SIZES))]
+        for x, y in zip(before, after):
+            np.testing.assert_array_equal(x, y)
+        assert b.nodes == sum(nx * ny for nx, ny in SIZES)
+
+
+def test_batch_errors():
+    from paper_2602_14667_gb300 import Batch, MhdError
+    with pytest.raises(MhdError, match="EINVAL"):
+        Batch([(64, 64)], [(0.5, 0.6)])
+    with Batch([(64, 64), (32, 32)], [(0.6, 0.6), (0.6, 0.6)]) as b:
+        z = np.zeros((64, 64))
+        b.set_fields(0, z, z, z, z)
+        with pytest.raises(MhdError, match="ESTATE"):
+            b.advance(1)            # lattice 1 has no fields yet
+        with pytest.raises(MhdError, match="EINVAL"):
+            b.get_fields(2)
+        with pytest.raises(MhdError, match="EINVAL"):
+            b.kernel_config = (3, 4)
