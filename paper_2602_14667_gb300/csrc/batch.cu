@@ -46,8 +46,8 @@ __global__ void __launch_bounds__(512) batch_step(const BatchLattice* __restrict
         const BatchLattice L = lats[tile.lat];
         const int y = tile.y0 + threadIdx.y;
         if (y < L.ny)  // uniform over the warp
-            step_row<1, V>(src + L.offset, dst + L.offset, L.nx, L.ny, L.pitch, L.plane, L.np, 0,
-                           tile.xblock, y, threadIdx.x);
+            step_row<1, V, false>(src + L.offset, dst + L.offset, L.nx, L.ny, L.pitch, L.plane,
+                                  L.np, tile.xblock, y, threadIdx.x);
     }
 }
 

@@ -16,19 +16,28 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 #include "lbm_device.cuh"
 #include "step_row.cuh"
 
 namespace mhd {
 
-template <int PREC, int V>
-__global__ void __launch_bounds__(512) step_vec(const StepArgs<typename Prec<PREC>::C> a) {
+// Persistent: the grid holds as many blocks as are resident on the GPU at
+// once and each block walks the tiles (rows_per_block rows x 32*V columns)
+// with a fixed stride, so warps of one SM drift apart and the loads of one
+// tile overlap the arithmetic of another.
+template <int PREC, int V, bool WALLY>
+__global__ void __launch_bounds__(512) step_vec(const StepArgs<typename Prec<PREC>::C> a, int nxb,
+                                                int ntiles) {
     using S = typename Prec<PREC>::S;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (y >= a.ny) return;  // whole warp (one row per warp)
-    step_row<PREC, V>(static_cast<const S*>(a.src), static_cast<S*>(a.dst), a.nx, a.ny, a.pitch,
-                      a.plane, a.np, a.wall_y, blockIdx.x, y, threadIdx.x);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int y = (t / nxb) * blockDim.y + threadIdx.y;
+        if (y < a.ny)  // whole warp (one row per warp)
+            step_row<PREC, V, WALLY>(static_cast<const S*>(a.src), static_cast<S*>(a.dst), a.nx,
+                                     a.ny, a.pitch, a.plane, a.np, t % nxb, y, threadIdx.x);
+    }
 }
 
 template <int PREC>
@@ -70,21 +79,29 @@ static cudaError_t launch_step_t(const StepLaunch& s, cudaStream_t st) {
     dim3 block(32, s.BY);
     const int cols = 32 * s.V;
     dim3 grid((s.L.nx + cols - 1) / cols, (s.L.ny + s.BY - 1) / s.BY);
-    switch (s.V) {
-    case 1:
-        if (s.wall_x) step_gen<PREC><<<grid, block, 0, st>>>(a);
-        else step_vec<PREC, 1><<<grid, block, 0, st>>>(a);
-        break;
-    case 2: step_vec<PREC, 2><<<grid, block, 0, st>>>(a); break;
-    case 4:
-        if constexpr (PREC != 0) {
-            step_vec<PREC, 4><<<grid, block, 0, st>>>(a);
-            break;
-        }
-        return cudaErrorInvalidValue;
-    default: return cudaErrorInvalidValue;
+    if (s.V == 1 && s.wall_x) {
+        step_gen<PREC><<<grid, block, 0, st>>>(a);
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
+    const int nxb = grid.x, ntiles = grid.x * grid.y;
+    auto go = [&](auto kernel) -> cudaError_t {
+        int per_sm = 0, sms = 0, dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * s.BY, 0);
+        if (e != cudaSuccess) return e;
+        const int blocks = std::max(1, std::min(ntiles, std::max(1, per_sm) * sms));
+        kernel<<<blocks, block, 0, st>>>(a, nxb, ntiles);
+        return cudaGetLastError();
+    };
+    switch (s.V) {
+    case 1: return s.wall_y ? go(step_vec<PREC, 1, true>) : go(step_vec<PREC, 1, false>);
+    case 2: return s.wall_y ? go(step_vec<PREC, 2, true>) : go(step_vec<PREC, 2, false>);
+    case 4:
+        if constexpr (PREC != 0) return s.wall_y ? go(step_vec<PREC, 4, true>) : go(step_vec<PREC, 4, false>);
+        return cudaErrorInvalidValue;
+    }
+    return cudaErrorInvalidValue;
 }
 
 bool step_shape_ok(const Layout& L, int prec, int wall_x, int V, int BY) {

@@ -2,10 +2,10 @@
 // the single-lattice kernel and the batched persistent kernel.
 //
 // One warp updates 32*V consecutive x nodes of row y: every plane is read
-// with aligned V-wide vector loads; the +-1 x shift of the moving
-// populations is done with warp shuffles (lane l takes the neighbour lane's
-// edge element) and only the lanes at a warp or lattice edge issue one extra
-// scalar load.  Pull streaming with half-way bounce-back on y walls; the x
+// with aligned V-wide vector loads, all issued before the first shuffle;
+// the +-1 x shift of the moving populations is then done with warp shuffles
+// (lane l takes the neighbour lane's edge element) and only the lanes at a
+// warp or lattice edge issue one extra scalar load.  Pull streaming with half-way bounce-back on y walls; the x
 // axis is periodic.  Stores are aligned V-wide vectors.
 #pragma once
 
@@ -24,13 +24,15 @@ template <typename C> struct StepArgs {
     int wall_x, wall_y;
 };
 
-// Requires nx % V == 0, all 32 lanes of the warp present, y < ny.
-template <int PREC, int V>
+// Requires nx % V == 0, all 32 lanes of the warp present, y < ny.  WALLY:
+// half-way bounce-back walls below row 0 and above row ny-1 (compile-time,
+// so that the periodic kernel has no branch between its 19 plane loads).
+template <int PREC, int V, bool WALLY>
 __device__ __forceinline__ void step_row(const typename Prec<PREC>::S* __restrict__ src,
                                          typename Prec<PREC>::S* __restrict__ dst, int nx, int ny,
                                          long long pitch, long long plane,
-                                         const NodeParams<typename Prec<PREC>::C>& np, int wall_y,
-                                         int xblock, int y, int lane) {
+                                         const NodeParams<typename Prec<PREC>::C>& np, int xblock,
+                                         int y, int lane) {
     using S = typename Prec<PREC>::S;
     using C = typename Prec<PREC>::C;
     const int x0 = (xblock * 32 + lane) * V;
@@ -38,7 +40,7 @@ __device__ __forceinline__ void step_row(const typename Prec<PREC>::S* __restric
 
     int ym = y - 1, yp = y + 1;
     bool bm = false, bp = false;
-    if (wall_y) {
+    if (WALLY) {
         bm = ym < 0;
         bp = yp >= ny;
     } else {
@@ -50,37 +52,46 @@ __device__ __forceinline__ void step_row(const typename Prec<PREC>::S* __restric
     const bool right_by_shfl = (lane < 31) && (x0 + V < nx);
     const long long rowy = (long long)y * pitch;
 
+    // Phase 1: issue every load of the 19 planes (aligned vectors, plus the
+    // edge element for the lanes at a warp / lattice edge) before any
+    // shuffle, so that all of them are in flight together.
+    S r[kPlanes][V];
+    S edge[kPlanes];
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        const int cx = pcx(p), cy = pcy(p);
+        const bool bounce = WALLY && (cy > 0 ? bm : (cy < 0 ? bp : false));  // warp-uniform
+        const int sy = cy > 0 ? ym : (cy < 0 ? yp : y);
+        const S* row = bounce ? src + (long long)popp(p) * plane + rowy
+                              : src + (long long)p * plane + (long long)sy * pitch;
+#pragma unroll
+        for (int k = 0; k < V; ++k) r[p][k] = S(0);
+        edge[p] = S(0);
+        if (active) VecIO<S, V>::load(row + x0, r[p]);
+        if (cx > 0 && !bounce && lane == 0 && active) edge[p] = row[xl];
+        if (cx < 0 && !bounce && !right_by_shfl && active) edge[p] = row[xr];
+    }
+    // Phase 2: decode and apply the +-1 x shift of the moving populations.
     C v[kPlanes][V];
 #pragma unroll
     for (int p = 0; p < kPlanes; ++p) {
         const int cx = pcx(p), cy = pcy(p);
-        const bool bounce = cy > 0 ? bm : (cy < 0 ? bp : false);  // uniform over the warp
-        if (bounce) {
-            S r[V];
-            if (active) VecIO<S, V>::load(src + (long long)popp(p) * plane + rowy + x0, r);
-#pragma unroll
-            for (int k = 0; k < V; ++k) v[p][k] = active ? decode(r[k]) : C(0);
-            continue;
-        }
-        const int sy = cy > 0 ? ym : (cy < 0 ? yp : y);
-        const S* row = src + (long long)p * plane + (long long)sy * pitch;
-        S r[V];
+        const bool bounce = WALLY && (cy > 0 ? bm : (cy < 0 ? bp : false));
         C c[V];
-        if (active) VecIO<S, V>::load(row + x0, r);
 #pragma unroll
-        for (int k = 0; k < V; ++k) c[k] = active ? decode(r[k]) : C(0);
-        if (cx == 0) {
+        for (int k = 0; k < V; ++k) c[k] = decode(r[p][k]);
+        if (cx == 0 || bounce) {
 #pragma unroll
             for (int k = 0; k < V; ++k) v[p][k] = c[k];
         } else if (cx > 0) {  // source x - 1
             C left = __shfl_up_sync(kFull, c[V - 1], 1);
-            if (lane == 0 && active) left = decode(row[xl]);
+            if (lane == 0) left = decode(edge[p]);
             v[p][0] = left;
 #pragma unroll
             for (int k = 1; k < V; ++k) v[p][k] = c[k - 1];
         } else {  // source x + 1
             C right = __shfl_down_sync(kFull, c[0], 1);
-            if (!right_by_shfl && active) right = decode(row[xr]);
+            if (!right_by_shfl) right = decode(edge[p]);
 #pragma unroll
             for (int k = 0; k < V - 1; ++k) v[p][k] = c[k + 1];
             v[p][V - 1] = right;
