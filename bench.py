@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--workload", default="ot4096", choices=["ot4096", "ensemble"],
                     help="ot4096: the headline single lattice; ensemble: 512 random-spectrum "
                          "lattices in one persistent launch per step")
+    ap.add_argument("--retune", action="store_true",
+                    help="time every launch shape instead of using the autotuner's cache")
     ap.add_argument("--shape", default=None,
                     help="fixed launch shape 'V,BY' (skips the autotuner; for profiling)")
     return ap.parse_args()
@@ -86,9 +88,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(prec, n):
+def profiled_traffic(prec, n, shape):
     """DRAM bytes per launch from a committed ncu summary, if it was taken
-    from the current kernel sources (else None)."""
+    from the current kernel sources with the same launch shape (else None)."""
     path = os.path.join(ROOT, "profiles", f"rr_step_{prec}_ncu.md")
     if not os.path.exists(path):
         return None
@@ -99,6 +101,8 @@ def profiled_traffic(prec, n):
                 k, v = line[2:].split(":", 1)
                 vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    if vals.get("shape") != f"{shape[0]},{shape[1]}":
         return None
     try:
         per_node = float(vals["dram_bytes_per_node"])
@@ -232,9 +236,17 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+TUNE_CACHE = os.path.join(ROOT, "paper_2602_14667_gb300", "tune_cache.json")
+
+
 def run_gb300(args):
     import numpy as np
     import torch
+
+    if not args.retune and "MHD_TUNE_CACHE" not in os.environ:
+        # the autotuner's results for this GPU (measured with --retune); a
+        # lattice without an entry is timed on the spot
+        os.environ["MHD_TUNE_CACHE"] = TUNE_CACHE
 
     import mhd_inputs
     from paper_2602_14667_gb300 import Lattice, MhdError
@@ -292,7 +304,7 @@ def run_gb300(args):
     per_launch_s = ms * 1e-3 / args.steps
     peak, peak_kind = measured_peaks()
     achieved = BYTES_PER_NODE[prec] * nodes / per_launch_s / 1e9
-    traffic = profiled_traffic(prec, n)
+    traffic = profiled_traffic(prec, n, shape)
 
     e2e = None
     if not args.no_e2e:
