@@ -164,6 +164,38 @@ mhd_status mhd_state_bytes(const mhd_lattice* l, size_t* bytes);
 mhd_status mhd_get_state(mhd_lattice* l, void* host, size_t bytes);
 mhd_status mhd_set_state(mhd_lattice* l, const void* host, size_t bytes);
 
+/* Allocation-free global diagnostics (the paper has no counterpart to this
+ * call; it is a service for callers that cannot allocate device memory
+ * when they need the totals -- e.g. a host framework that has reserved the
+ * whole GPU for its own memory pool and lends out only pointers it owns, or
+ * a latency-critical loop that must not call cudaMalloc, which synchronises
+ * the device).  It computes what mhd_get_totals computes, without a lattice
+ * handle and without allocating: no cudaMalloc, cudaFree or other allocating
+ * routine is called.
+ *   state       device pointer to a state in the packed layout of
+ *               mhd_get_state (19 planes of nx*ny elements of the storage
+ *               type of p->precision), caller-owned, read only;
+ *   prev_state  device pointer to the state the last step read (same
+ *               layout), or NULL: then the pre-collision magnetic
+ *               populations are recovered from `state` as
+ *               g - g_eq = (g* - g_eq)/(1 - omega_m) (jz_max = 0 for
+ *               tau_m = 1);
+ *   p           rho0, tau_m, bc_x, bc_y and precision are used;
+ *   stream      cudaStream_t (may be NULL); the call waits for it;
+ *   out         caller-owned host struct (out->step is set to 0).
+ * The per-block partial sums go to one fixed scratch array of about 1.7 MB
+ * that is compiled into the library: every GPU that loads the library holds
+ * it until the process exits.  Its device address is looked up on the first
+ * call made on each device (with that device current).  Every call uses the
+ * same array and each call overwrites what it reads, so calls whose work
+ * overlaps on a GPU (different streams or host threads at the same time)
+ * race and must be serialised by the caller.  Lattices with
+ * ceil(nx/32)*ceil(ny/8) > 16384 (about 4.2 M nodes, e.g. more than
+ * 2048 x 2048) are rejected with MHD_EINVAL.  Non-finite totals ->
+ * MHD_EUNSTABLE (with *out filled). */
+mhd_status mhd_totals_noalloc(const void* state, const void* prev_state, int nx, int ny,
+                              const mhd_params* p, void* stream, mhd_totals* out);
+
 /* Current launch shape, or set one explicitly (MHD_EINVAL if the shape is not
  * valid for this lattice). */
 mhd_status mhd_get_kernel_config(const mhd_lattice* l, mhd_kernel_config* out);

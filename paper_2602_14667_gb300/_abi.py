@@ -65,6 +65,8 @@ _SIGNATURES = {
     "mhd_autotune": [_P, ctypes.POINTER(mhd_kernel_config)],
     "mhd_destroy": [_P],
     "mhd_state_bytes": [_P, ctypes.POINTER(ctypes.c_size_t)],
+    "mhd_totals_noalloc": [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(mhd_params), _P,
+                           ctypes.POINTER(mhd_totals)],
     "mhd_batch_create": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                          ctypes.POINTER(mhd_params), _P, ctypes.POINTER(_P)],
     "mhd_batch_set_fields": [_P, ctypes.c_int, _D, _D, _D, _D, _D],
@@ -223,6 +225,18 @@ class Lattice:
         c = mhd_kernel_config()
         check(lib().mhd_autotune(self._h, ctypes.byref(c)), "mhd_autotune")
         return c.nodes_per_thread, c.rows_per_block
+
+
+def totals_noalloc(state_ptr: int, nx: int, ny: int, params: "mhd_params", prev_ptr=None,
+                   stream=None) -> dict:
+    """mhd_totals_noalloc on caller-owned device memory (integer device
+    pointers, e.g. ``tensor.data_ptr()``); allocates nothing."""
+    t = mhd_totals()
+    check(lib().mhd_totals_noalloc(_P(int(state_ptr)), None if prev_ptr is None else _P(int(prev_ptr)),
+                                   int(nx), int(ny), ctypes.byref(params),
+                                   None if stream is None else _P(int(stream)), ctypes.byref(t)),
+          "mhd_totals_noalloc")
+    return _totals_dict(t)
 
 
 def _totals_dict(t: "mhd_totals") -> dict:
