@@ -189,6 +189,22 @@ def cpu_baseline(n_sample=512, budget_s=12.0):
                       f"(same u0, nu as the workload), {dt:.1f} s"}
 
 
+def partition(items, rank, world):
+    """The share of an ensemble that one rank advances (replicas: no data
+    exchange between ranks)."""
+    return items[rank::world]
+
+
+def reduce_max(value, dist, device="cpu"):
+    """Max of a per-rank float over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -288,11 +304,7 @@ def run_gb300(args):
         ev1.synchronize()
     barrier()
     ms = ev0.elapsed_time(ev1)
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = reduce_max(ms, dist, dev)
     try:
         tot = lat.get_totals()
         stable = True
@@ -323,11 +335,7 @@ def run_gb300(args):
         lat2.advance(args.steps)
         lat2.get_fields(out=h[4:9])            # D2H of rho, u, b
         lat2.get_totals(check_stable=False)    # D2H of the totals
-        t_e2e = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = reduce_max(time.perf_counter() - t0, dist, dev)
         lat2.close()
         h2d = 4 * 8 * nodes / args.steps
         d2h = (5 * 8 * nodes + 13 * 8) / args.steps
@@ -377,9 +385,13 @@ def run_ensemble(args):
     from paper_2602_14667_gb300 import Batch, MhdError
 
     world, rank, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     draws = mhd_inputs.ensemble(512)
-    mine = draws[rank::world]                      # replicas: lattices split over ranks
+    mine = partition(draws, rank, world)           # replicas: lattices split over ranks
     stream = torch.cuda.Stream()
     sizes = [(d["n"], d["n"]) for d in mine]
     taus = [(0.5 + 3 * d["nu"], 0.5 + 3 * d["eta"]) for d in mine]
@@ -394,12 +406,16 @@ def run_ensemble(args):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     with ClockSampler(local) as clk:
         ev0.record(stream)
         b.advance(args.steps)
         ev1.record(stream)
         ev1.synchronize()
-    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        dist.barrier()
+    ms = reduce_max(ev0.elapsed_time(ev1), dist, torch.device("cuda", local))
     finite = 0
     for i in range(len(mine)):
         try:
@@ -408,6 +424,10 @@ def run_ensemble(args):
         except MhdError:
             pass
     nodes = b.nodes
+    if dist is not None:
+        t = torch.tensor([nodes], dtype=torch.float64, device=torch.device("cuda", local))
+        dist.all_reduce(t)
+        nodes = int(t.item())
     b.close()
     peak, peak_kind = measured_peaks()
     achieved = 152 * nodes / (ms * 1e-3 / args.steps) / 1e9
@@ -423,6 +443,8 @@ def run_ensemble(args):
            "gpu_launches": args.steps, "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def main():
