@@ -155,6 +155,26 @@ def collide(p: Params, f: np.ndarray, g: np.ndarray):
     return fs, gs
 
 
+def collide_da(p: Params, f: np.ndarray, g: np.ndarray, da):
+    """Collision with a per-node correction da (shape (ny, nx, 3): xx, xy, yy)
+    added to a1^(2) before the recursion; da=None is the plain collision."""
+    fs = np.zeros_like(f); gs = np.zeros_like(g)
+    pc = p.c()
+    d = None if da is None else np.ascontiguousarray(da, dtype=np.float64).reshape(-1)
+    lib().orc_collide_da(ctypes.byref(pc), _p(f), _p(g), _p(d) if d is not None else None,
+                         _p(fs), _p(gs))
+    return fs, gs
+
+
+def node_info(p: Params, f: np.ndarray, g: np.ndarray) -> np.ndarray:
+    """Per-node (ny, nx, 20): rho, ux, uy, bx, by, a2 (xx, xy, yy), a3 (xxy, xyy),
+    a4_xxyy, fneq_reg[9] of the pre-collision state (f, g)."""
+    out = np.zeros((p.ny, p.nx, 20))
+    pc = p.c()
+    lib().orc_node_info(ctypes.byref(pc), _p(f), _p(g), _p(out))
+    return out
+
+
 def stream(p: Params, fs: np.ndarray, gs: np.ndarray):
     f = np.zeros_like(fs); g = np.zeros_like(gs)
     pc = p.c()

@@ -233,11 +233,22 @@ void orc_moments(const double* f, const double* g, double* out5) {
     out5[0] = rho; out5[1] = mx / rho; out5[2] = my / rho; out5[3] = bx; out5[4] = by;
 }
 
-/* Tasks 1-5 at one node.  info (may be NULL) receives
+/* Tasks 1-5 at one node.  da (may be NULL) is a learned correction
+ * (xx, xy, yy) added to the projected a1^(2) before the recursion (the
+ * closure; only the second- and higher-order non-equilibrium content changes,
+ * so mass and momentum stay exact).  info (may be NULL) receives
  * [rho, ux, uy, bx, by, a2_xx, a2_xy, a2_yy, a3_xxy, a3_xyy, a4_xxyy,
- *  fneq_reg[0..8]] -- 20 doubles. */
+ *  fneq_reg[0..8]] -- 20 doubles, with a2 before the correction. */
+void orc_collide_node_da(const orc_params* p, const double* f, const double* g, const double* da,
+                         double* fs, double* gs, double* info);
+
 void orc_collide_node(const orc_params* p, const double* f, const double* g, double* fs,
                       double* gs, double* info) {
+    orc_collide_node_da(p, f, g, NULL, fs, gs, info);
+}
+
+void orc_collide_node_da(const orc_params* p, const double* f, const double* g, const double* da,
+                         double* fs, double* gs, double* info) {
     ensure_tables();
     double mom[5];
     orc_moments(f, g, mom);
@@ -255,6 +266,13 @@ void orc_collide_node(const orc_params* p, const double* f, const double* g, dou
             for (int i = 0; i < 9; ++i) s += HT[2][id[0] | (id[1] << 1)][i] * (f[i] - feq[i]);
             a2[a][c] = s;
         }
+    double a2_proj[3] = {a2[0][0], a2[0][1], a2[1][1]};
+    if (da) {
+        a2[0][0] += da[0];
+        a2[0][1] += da[1];
+        a2[1][0] += da[1];
+        a2[1][1] += da[2];
+    }
     /* recursion, third order: a3_abg = u_a a2_bg + u_b a2_ag + u_g a2_ab */
     for (int a = 0; a < 2; ++a)
         for (int c = 0; c < 2; ++c)
@@ -306,7 +324,7 @@ void orc_collide_node(const orc_params* p, const double* f, const double* g, dou
 
     if (info) {
         info[0] = rho; info[1] = u[0]; info[2] = u[1]; info[3] = b[0]; info[4] = b[1];
-        info[5] = a2[0][0]; info[6] = a2[0][1]; info[7] = a2[1][1];
+        info[5] = a2_proj[0]; info[6] = a2_proj[1]; info[7] = a2_proj[2];
         info[8] = a3[0][0][1]; info[9] = a3[0][1][1]; info[10] = a4[0][0][1][1];
         for (int i = 0; i < 9; ++i) info[11 + i] = fneq[i];
     }
@@ -328,6 +346,34 @@ void orc_collide(const orc_params* p, const double* f, const double* g, double* 
         orc_collide_node(p, fl, gl, fo, go, NULL);
         for (int i = 0; i < 9; ++i) fs[i * n + k] = fo[i];
         for (int q = 0; q < 10; ++q) gs[q * n + k] = go[q];
+    }
+}
+
+/* Task 5 over the lattice with a per-node correction da[3*k + (xx, xy, yy)]
+ * of a1^(2) (NULL: none). */
+void orc_collide_da(const orc_params* p, const double* f, const double* g, const double* da,
+                    double* fs, double* gs) {
+    ensure_tables();
+    long n = (long)p->nx * p->ny;
+#pragma omp parallel for schedule(static)
+    for (long k = 0; k < n; ++k) {
+        double fl[9], gl[10], fo[9], go[10];
+        gather_node(n, k, f, g, fl, gl);
+        orc_collide_node_da(p, fl, gl, da ? da + 3 * k : NULL, fo, go, NULL);
+        for (int i = 0; i < 9; ++i) fs[i * n + k] = fo[i];
+        for (int q = 0; q < 10; ++q) gs[q * n + k] = go[q];
+    }
+}
+
+/* Per-node info of orc_collide_node for the whole lattice: info[20*k + .]. */
+void orc_node_info(const orc_params* p, const double* f, const double* g, double* info) {
+    ensure_tables();
+    long n = (long)p->nx * p->ny;
+#pragma omp parallel for schedule(static)
+    for (long k = 0; k < n; ++k) {
+        double fl[9], gl[10], fo[9], go[10];
+        gather_node(n, k, f, g, fl, gl);
+        orc_collide_node(p, fl, gl, fo, go, info + 20 * k);
     }
 }
 

@@ -1,0 +1,131 @@
+"""Pins of the closure oracle (oracle/closure.py) against the mathematics:
+finite-difference gradients of the MLP, Adam's first step, the filter's
+conservation, closed forms of the stencils, and the target formula (zero
+on a plain coarse trajectory, and exactly the applied correction when the
+next state was produced by a corrected collision)."""
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def clo(orc):
+    from oracle import closure
+    return closure
+
+
+def test_mlp_gradients_match_finite_differences(clo):
+    rng = np.random.default_rng(0)
+    X = rng.normal(size=(40, clo.N_IN))
+    T = rng.normal(size=(40, clo.N_OUT))
+    net = clo.MLP(seed=3)
+    net.p["mean"] = rng.normal(size=clo.N_IN) * 0.1
+    net.p["scale"] = rng.uniform(0.5, 2.0, clo.N_IN)
+    net.p["out_scale"] = rng.uniform(0.5, 2.0, clo.N_OUT)
+    net.p["b1"] = rng.normal(size=clo.N_HID) * 0.1
+    loss, grads = net.loss_and_grads(X, T)
+    h = 1e-6
+    for name in clo.TRAINABLE:
+        flat = net.p[name].reshape(-1)
+        for idx in rng.choice(flat.size, size=min(12, flat.size), replace=False):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp, _ = net.loss_and_grads(X, T)
+            flat[idx] = old - h
+            lm, _ = net.loss_and_grads(X, T)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - grads[name].reshape(-1)[idx]) < 1e-6 * max(1.0, abs(fd)), (name, idx)
+
+
+def test_adam_first_step_is_lr_times_sign(clo):
+    params = {"w": np.array([1.0, -2.0, 0.5])}
+    g = {"w": np.array([0.3, -1e-3, 4.0])}
+    Adam = clo.Adam(lr=0.01, eps=1e-12)
+    Adam.step(params, g)
+    np.testing.assert_allclose(params["w"], [1.0 - 0.01, -2.0 + 0.01, 0.5 - 0.01], rtol=0, atol=1e-9)
+
+
+def test_bf16_rounding(clo):
+    x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 2 ** -7, 1.0 + 3 * 2 ** -8, -3.14159265, 1e-3])
+    r = clo.bf16(x)
+    assert r[0] == 1.0 and r[1] == 1.0            # tie to even
+    assert r[2] == 1.0 + 2 ** -7
+    assert r[3] == 1.0 + 2 ** -6                  # tie to even (upwards)
+    assert abs(r[4] / x[4] - 1) < 2 ** -8 and abs(r[5] / x[5] - 1) < 2 ** -8
+
+
+def test_filter_conserves_and_averages(orc, clo):
+    rng = np.random.default_rng(1)
+    f = rng.normal(size=(9, 16, 24))
+    g = rng.normal(size=(5, 2, 16, 24))
+    fc, gc = clo.box_filter(f, g, 4)
+    assert fc.shape == (9, 4, 6) and gc.shape == (5, 2, 4, 6)
+    np.testing.assert_allclose(fc.sum(axis=(1, 2)) * 16, f.sum(axis=(1, 2)), rtol=1e-13)
+    np.testing.assert_allclose(gc.sum(axis=(2, 3)) * 16, g.sum(axis=(2, 3)), rtol=1e-13)
+    assert abs(fc[3, 1, 2] - f[3, 4:8, 8:12].mean()) < 1e-15
+
+
+def test_stencil_closed_forms(clo):
+    nx, ny = 16, 12
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    k, q = 2 * np.pi * 3 / nx, 2 * np.pi * 2 / ny
+    th = k * X + q * Y
+    s = np.sin(th)
+    lap = (8 * (np.cos(k) + np.cos(q)) + 4 * np.cos(k) * np.cos(q) - 20) / 6 * s
+    np.testing.assert_allclose(clo.lap9(s), lap, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(clo.dxy(s), -np.sin(k) * np.sin(q) * s, rtol=0, atol=1e-14)
+
+
+def test_feature_columns(orc, clo):
+    import mhd_inputs
+    n = 16
+    p = orc.Params(n, n, 0.6, 0.7)
+    ux, uy, bx, by = mhd_inputs.orszag_tang(n, 0.05, 0.03)
+    f, g = orc.init(p, ux, uy, bx, by)
+    X, a2 = clo.features(p, f, g)
+    assert X.shape == (n * n, 24)
+    np.testing.assert_allclose(X[:, 1], ux.reshape(-1), atol=1e-15)
+    np.testing.assert_allclose(X[:, 4], by.reshape(-1), atol=1e-15)
+    np.testing.assert_allclose(X[:, 5:8], 0, atol=1e-16)        # equilibrium: no non-equilibrium
+    dx, dy, _ = orc.gradient(p, uy)
+    np.testing.assert_allclose(X[:, 12], dx.reshape(-1), atol=1e-16)  # d_x u_y
+    np.testing.assert_allclose(X[:, 14], clo.lap9(uy).reshape(-1), atol=1e-16)
+
+
+def _state(orc, n, seed):
+    import mhd_inputs
+    p = orc.Params(n, n, 0.53, 0.56)
+    f, g = orc.init(p, *mhd_inputs.random_spectrum(n, n, seed, 0.03, 0.03, kmax=3))
+    return p, *orc.run(p, f, g, 7)
+
+
+def test_target_is_zero_on_a_plain_coarse_step(orc, clo):
+    p, f, g = _state(orc, 16, 5)
+    f1, g1 = clo.closure_step(p, f, g, None)
+    assert np.abs(clo.targets(p, f, g, f1, g1)).max() < 1e-14
+
+
+def test_target_recovers_an_applied_correction(orc, clo):
+    p, f, g = _state(orc, 16, 6)
+    rng = np.random.default_rng(2)
+    da = rng.normal(0, 1e-4, (16, 16, 3))
+    fs, gs = orc.collide_da(p, f, g, da)
+    f1, g1 = orc.stream(p, fs, gs)
+    np.testing.assert_allclose(clo.targets(p, f, g, f1, g1), da.reshape(-1, 3), rtol=0, atol=1e-13)
+
+
+def test_closure_keeps_mass_and_momentum_and_zero_net_is_plain(orc, clo):
+    p, f, g = _state(orc, 16, 7)
+    net = clo.MLP(seed=1)
+    net.p["out_scale"][:] = 1e-4
+    f1, g1 = clo.closure_step(p, f, g, net)
+    cx, cy, *_ = orc.lattice()
+    assert abs(f1.sum() - f.sum()) < 1e-12
+    assert abs((f1 * cx[:, None, None]).sum() - (f * cx[:, None, None]).sum()) < 1e-13
+    zero = clo.MLP(seed=1)
+    for k in clo.TRAINABLE:
+        zero.p[k][:] = 0
+    fz, gz = clo.closure_step(p, f, g, zero)
+    fp, gp = clo.closure_step(p, f, g, None)
+    np.testing.assert_array_equal(fz, fp)
+    assert np.abs(f1 - fp).max() > 1e-8
