@@ -243,6 +243,90 @@ mhd_status mhd_batch_set_kernel_config(mhd_batch* b, const mhd_kernel_config* cf
 mhd_status mhd_batch_autotune(mhd_batch* b, mhd_kernel_config* best);
 mhd_status mhd_batch_destroy(mhd_batch* b);
 
+/* ---------------------------------------------------------------------------
+ * Learned sub-grid closure (an extension; the paper has no closure).  A
+ * per-node MLP predicts a correction dA = (xx, xy, yy) of the projected
+ * non-equilibrium coefficient a1^(2) (task 3 of "Algorithm of computation")
+ * on a coarse lattice; dA is added before the recursion, so mass and
+ * momentum stay exact.  The MLP is 24 -> 64 -> 64 -> 3 with ReLU:
+ *   y = out_scale * (W3^T h2 + b3), h2 = relu(W2^T h1 + b2),
+ *   h1 = relu(W1^T xn + b1), xn = (x - mean) * scale,
+ * evaluated and trained on BF16 tensor cores (mma.sync m16n8k16) with FP32
+ * accumulation; the master weights are FP32.
+ * Features x (24 per node, of the pre-collision state): rho - rho0, u_x,
+ * u_y, b_x, b_y, a1^(2)_xx, a1^(2)_xy, a1^(2)_yy, then for each of u_x, u_y,
+ * b_x, b_y: d_x, d_y (isotropic lattice gradient), the 9-point lattice
+ * Laplacian (4 sum_axes + sum_diagonals - 20 q)/6, and
+ * d_xy = (q_NE - q_NW - q_SE + q_SW)/4.
+ * Parameter blob (MHD_MLP_PARAMS floats, in order): mean[24], scale[24],
+ * out_scale[3], W1[24][64], b1[64], W2[64][64], b2[64], W3[64][3], b3[3]
+ * (weights input-major, W[in][out]).
+ * Device pointers below are caller-owned CUDA memory; the calls wait for
+ * their stream (the MLP's, or the one passed) before returning.
+ * ------------------------------------------------------------------------- */
+#define MHD_MLP_PARAMS 6006
+typedef struct mhd_mlp mhd_mlp;
+
+/* He-normal weights from SplitMix64(seed), zero biases, identity
+ * normalisation.  max_batch: the largest number of samples one training
+ * batch or gradient call holds (16 .. 2^24). */
+mhd_status mhd_mlp_create(unsigned long long seed, int max_batch, void* stream, mhd_mlp** out);
+mhd_status mhd_mlp_destroy(mhd_mlp* m);
+/* host copy of the FP32 parameter blob (count must be MHD_MLP_PARAMS);
+ * set_params also resets the Adam state */
+mhd_status mhd_mlp_get_params(const mhd_mlp* m, float* host, size_t count);
+mhd_status mhd_mlp_set_params(mhd_mlp* m, const float* host, size_t count);
+/* mean / scale = 1/std per feature and out_scale = std per target from a
+ * data set X (n x 24), T (n x 3) in device memory (FP64 reductions) */
+mhd_status mhd_mlp_fit_normalisation(mhd_mlp* m, const float* X, const float* T, long long n);
+/* Loss L = mean over n x 3 entries of (y / out_scale - T / out_scale)^2 and
+ * its gradient with respect to the blob (grad_host: MHD_MLP_PARAMS floats,
+ * zero for the normalisation entries), one full batch of n <= max_batch. */
+mhd_status mhd_mlp_gradients(mhd_mlp* m, const float* X, const float* T, long long n, float* grad_host,
+                             double* loss);
+/* Mini-batch Adam (beta1 0.9, beta2 0.999, eps 1e-8) over `epochs`
+ * passes of a SplitMix64(seed)-shuffled data set; *last_epoch_loss (may be
+ * NULL) is the mean batch loss of the last pass.  MHD_EUNSTABLE if it is
+ * not finite. */
+mhd_status mhd_mlp_train(mhd_mlp* m, const float* X, const float* T, long long n, int epochs, int batch,
+                         float lr, unsigned long long seed, double* last_epoch_loss);
+/* Y (n x 3, device) = dA predicted for the features X (n x 24, device). */
+mhd_status mhd_mlp_predict(mhd_mlp* m, const float* X, long long n, float* Y);
+
+/* Box filter (factor x factor block average) of a lattice's pre-collision
+ * populations at its current time into a packed coarse state
+ * (FP32 deviations f_i - w_i rho0 and g, 19 planes of
+ * (nx/factor)*(ny/factor) values, the layout of mhd_get_state for FP32).
+ * The lattice must be periodic and have taken at least one step since its
+ * state was set (MHD_ESTATE otherwise). */
+mhd_status mhd_closure_filter(mhd_lattice* l, int factor, float* coarse_state);
+/* Features (n x 24) of a packed FP32 pre-collision state (periodic). */
+mhd_status mhd_closure_features(const float* state, int nx, int ny, double rho0, float* X, void* stream);
+/* Targets (n x 3): the correction that makes one coarse collide-and-stream
+ * step from state_t reproduce state_t1 in its second-order moments:
+ * dA = (sum_i H2_i F_i(x + c_i, t+1) - a0^(2)) / (1 - 1/tau_f) - a1^(2)(t),
+ * with a0^(2) = rho u u + M (FP64 arithmetic).  Periodic. */
+mhd_status mhd_closure_targets(const float* state_t, const float* state_t1, int nx, int ny, double rho0,
+                               double tau_f, float* T, void* stream);
+/* Sub-grid stress targets (n_coarse x 3, device) from a lattice's
+ * pre-collision state at its current time: per coarse node (factor x factor
+ * block) tau_sgs = <rho u u + M(b)> - (<rho> u_t u_t + M(<b>)) with
+ * u_t = <rho u>/<rho> (xx, xy, yy, FP64 arithmetic), returned as the
+ * a1^(2) correction tau_sgs / (1 - 1/tau_coarse) that adds tau_sgs to the
+ * coarse post-collision momentum flux.  Periodic lattices with rho0 = 1,
+ * after at least one step (MHD_ESTATE otherwise). */
+mhd_status mhd_closure_sgs_targets(mhd_lattice* l, int factor, double tau_coarse, float* targets);
+/* Make `state` (device, packed FP32 pre-collision populations as written by
+ * mhd_closure_filter, of this lattice's size) the pre-collision state of the
+ * next step: the stored state becomes S_i(x) = F_i(x + c_i), so the next
+ * mhd_advance collides exactly F.  Fields and totals read before that step
+ * describe S, not F.  Periodic lattices. */
+mhd_status mhd_set_precollision_state(mhd_lattice* l, const float* state);
+/* Switch the lattice's step to the closure variant with a copy of the MLP's
+ * current parameters (the MLP may be destroyed afterwards), or back to the
+ * plain scheme with mlp = NULL.  FP32 storage and periodic axes only. */
+mhd_status mhd_set_closure(mhd_lattice* l, const mhd_mlp* mlp);
+
 #ifdef __cplusplus
 }
 #endif

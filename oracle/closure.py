@@ -13,6 +13,8 @@ plain reference for the GPU kernels (no shared code with them):
                   (d_x, d_y), the 9-point lattice Laplacian and d_xy;
 * targets      -- the correction that makes one coarse step reproduce the
                   filtered fine state one coarse step later (see targets());
+* sgs_targets  -- the filtered sub-grid momentum flux of the fine state,
+                  as a correction of a1^(2) (see sgs_targets());
 * MLP          -- 24 -> 64 -> 64 -> 3, ReLU, with input / output scaling,
                   forward and backward in FP64, optional BF16 rounding of the
                   weights and of each layer's input (as the tensor-core
@@ -94,6 +96,36 @@ def targets(p: Params, fT, gT, fT1, gT1) -> np.ndarray:
     om1 = 1.0 - 1.0 / p.tau_f
     tgt = np.stack([(sxx - a0xx) / om1, (sxy - a0xy) / om1, (syy - a0yy) / om1], axis=-1)
     return (tgt - a2).reshape(-1, 3)
+
+
+def sgs_targets(p_fine: Params, f, g, r: int, tau_coarse: float) -> np.ndarray:
+    """Sub-grid stress target per coarse node (n_coarse, 3).
+
+    From the fine pre-collision state: block averages over r x r of rho,
+    rho u, b and of the momentum flux rho u u + M(b); the resolved flux of the
+    averaged fields is rho_bar u_t u_t + M(b_bar) with u_t = (rho u)_bar /
+    rho_bar; tau_sgs = flux_bar - resolved flux (xx, xy, yy).  Adding
+    dA = tau_sgs / (1 - omega_coarse) to a1^(2) adds tau_sgs to the
+    post-collision momentum flux that streaming carries."""
+    info = node_info(p_fine, f, g)
+    rho, ux, uy, bx, by = (info[..., k] for k in range(5))
+
+    def avg(a):
+        ny, nx = a.shape
+        return a.reshape(ny // r, r, nx // r, r).mean(axis=(1, 3))
+
+    b2 = bx * bx + by * by
+    fxx = avg(rho * ux * ux + 0.5 * b2 - bx * bx)
+    fxy = avg(rho * ux * uy - bx * by)
+    fyy = avg(rho * uy * uy + 0.5 * b2 - by * by)
+    R, MX, MY, BX, BY = avg(rho), avg(rho * ux), avg(rho * uy), avg(bx), avg(by)
+    UX, UY = MX / R, MY / R
+    B2 = BX * BX + BY * BY
+    txx = fxx - (R * UX * UX + 0.5 * B2 - BX * BX)
+    txy = fxy - (R * UX * UY - BX * BY)
+    tyy = fyy - (R * UY * UY + 0.5 * B2 - BY * BY)
+    om1 = 1.0 - 1.0 / tau_coarse
+    return (np.stack([txx, txy, tyy], axis=-1) / om1).reshape(-1, 3)
 
 
 def bf16(x: np.ndarray) -> np.ndarray:

@@ -78,6 +78,22 @@ _SIGNATURES = {
     "mhd_batch_set_kernel_config": [_P, ctypes.POINTER(mhd_kernel_config)],
     "mhd_batch_autotune": [_P, ctypes.POINTER(mhd_kernel_config)],
     "mhd_batch_destroy": [_P],
+    "mhd_mlp_create": [ctypes.c_ulonglong, ctypes.c_int, _P, ctypes.POINTER(_P)],
+    "mhd_mlp_destroy": [_P],
+    "mhd_mlp_get_params": [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t],
+    "mhd_mlp_set_params": [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t],
+    "mhd_mlp_fit_normalisation": [_P, _P, _P, ctypes.c_longlong],
+    "mhd_mlp_gradients": [_P, _P, _P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_float),
+                          ctypes.POINTER(ctypes.c_double)],
+    "mhd_mlp_train": [_P, _P, _P, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                      ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_double)],
+    "mhd_mlp_predict": [_P, _P, ctypes.c_longlong, _P],
+    "mhd_closure_filter": [_P, ctypes.c_int, _P],
+    "mhd_closure_features": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P],
+    "mhd_closure_targets": [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P, _P],
+    "mhd_set_precollision_state": [_P, _P],
+    "mhd_closure_sgs_targets": [_P, ctypes.c_int, ctypes.c_double, _P],
+    "mhd_set_closure": [_P, _P],
     "mhd_get_state": [_P, _P, ctypes.c_size_t],
     "mhd_set_state": [_P, _P, ctypes.c_size_t],
 }
@@ -330,3 +346,101 @@ class Batch:
         c = mhd_kernel_config()
         check(lib().mhd_batch_autotune(self._h, ctypes.byref(c)), "mhd_batch_autotune")
         return c.nodes_per_thread, c.rows_per_block
+
+
+MLP_PARAMS = 6006
+
+
+def _ptr(t) -> "_P":
+    """Device pointer of a torch tensor (or an int address)."""
+    return _P(int(t) if isinstance(t, int) else t.data_ptr())
+
+
+class MLP:
+    """The closure network (owner of the C handle); tensors are torch CUDA tensors."""
+
+    def __init__(self, seed: int = 0, max_batch: int = 16384, stream=None):
+        self._h = _P()
+        self.stream = stream
+        check(lib().mhd_mlp_create(int(seed), int(max_batch), None if stream is None else _P(int(stream)),
+                                   ctypes.byref(self._h)), "mhd_mlp_create")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            check(lib().mhd_mlp_destroy(self._h), "mhd_mlp_destroy")
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(MLP_PARAMS, dtype=np.float32)
+        check(lib().mhd_mlp_get_params(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), out.size),
+              "mhd_mlp_get_params")
+        return out
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        check(lib().mhd_mlp_set_params(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size),
+              "mhd_mlp_set_params")
+
+    def fit_normalisation(self, X, T):
+        check(lib().mhd_mlp_fit_normalisation(self._h, _ptr(X), _ptr(T), X.shape[0]), "mhd_mlp_fit_normalisation")
+
+    def gradients(self, X, T):
+        g = np.empty(MLP_PARAMS, dtype=np.float32)
+        loss = ctypes.c_double()
+        check(lib().mhd_mlp_gradients(self._h, _ptr(X), _ptr(T), X.shape[0],
+                                      g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(loss)),
+              "mhd_mlp_gradients")
+        return loss.value, g
+
+    def train(self, X, T, epochs=10, batch=8192, lr=1e-3, seed=0) -> float:
+        loss = ctypes.c_double()
+        check(lib().mhd_mlp_train(self._h, _ptr(X), _ptr(T), X.shape[0], int(epochs), int(batch), float(lr),
+                                  int(seed), ctypes.byref(loss)), "mhd_mlp_train")
+        return loss.value
+
+    def predict(self, X, Y):
+        check(lib().mhd_mlp_predict(self._h, _ptr(X), X.shape[0], _ptr(Y)), "mhd_mlp_predict")
+
+
+def closure_filter(lattice: "Lattice", factor: int, out):
+    check(lib().mhd_closure_filter(lattice.handle, int(factor), _ptr(out)), "mhd_closure_filter")
+
+
+def closure_features(state, nx, ny, rho0, X, stream=None):
+    check(lib().mhd_closure_features(_ptr(state), int(nx), int(ny), float(rho0), _ptr(X),
+                                     None if stream is None else _P(int(stream))), "mhd_closure_features")
+
+
+def closure_targets(state_t, state_t1, nx, ny, rho0, tau_f, T, stream=None):
+    check(lib().mhd_closure_targets(_ptr(state_t), _ptr(state_t1), int(nx), int(ny), float(rho0),
+                                    float(tau_f), _ptr(T), None if stream is None else _P(int(stream))),
+          "mhd_closure_targets")
+
+
+def closure_sgs_targets(lattice: "Lattice", factor: int, tau_coarse: float, out):
+    check(lib().mhd_closure_sgs_targets(lattice.handle, int(factor), float(tau_coarse), _ptr(out)),
+          "mhd_closure_sgs_targets")
+
+
+def set_precollision_state(lattice: "Lattice", state):
+    check(lib().mhd_set_precollision_state(lattice.handle, _ptr(state)), "mhd_set_precollision_state")
+
+
+def set_closure(lattice: "Lattice", mlp):
+    check(lib().mhd_set_closure(lattice.handle, None if mlp is None else mlp.handle), "mhd_set_closure")

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/mhd.h"
+#include "closure_internal.h"
 #include "internal.h"
 
 namespace {
@@ -46,6 +47,8 @@ bool finite_array(const double* a, long long n) {
 
 void mhd::set_last_error(const std::string& msg) { g_err = msg; }
 
+void mhd_internal_closure_params(const mhd_mlp* m, mhd::ClosureParamsDev* cp);
+
 struct mhd_lattice {
     int nx = 0, ny = 0;
     mhd_params p{};
@@ -65,6 +68,8 @@ struct mhd_lattice {
     double* totals_h = nullptr;  // pinned
     mhd_kernel_config cfg{1, 8};
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    void* closure_buf = nullptr;  // lattice-owned copy of the closure's inference parameters
+    mhd::ClosureParamsDev closure{};
 
     long long n() const { return (long long)nx * ny; }
     size_t buf_bytes() const { return (size_t)mhd::kStatePlanes * L.plane * L.esize; }
@@ -88,6 +93,12 @@ mhd::StepLaunch step_launch(const mhd_lattice* l, int from) {
     s.V = l->cfg.nodes_per_thread;
     s.BY = l->cfg.rows_per_block;
     return s;
+}
+
+cudaError_t launch_lattice_step(const mhd_lattice* l, int from, cudaStream_t st) {
+    const mhd::StepLaunch s = step_launch(l, from);
+    if (l->closure_buf) return mhd::launch_step_closure(s, l->closure, st);
+    return mhd::launch_step(s, st);
 }
 
 void drop_graphs(mhd_lattice* l) {
@@ -228,6 +239,7 @@ mhd_status mhd_destroy(mhd_lattice* l) {
     for (auto& b : l->buf)
         if (b) cudaFree(b);
     if (l->io) cudaFree(l->io);
+    if (l->closure_buf) cudaFree(l->closure_buf);
     if (l->partials) cudaFree(l->partials);
     if (l->totals_d) cudaFree(l->totals_d);
     if (l->totals_h) cudaFreeHost(l->totals_h);
@@ -270,7 +282,7 @@ static mhd_status capture_graph(mhd_lattice* l, int from) {
     int c = from;
     cudaError_t le = cudaSuccess;
     for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k) {
-        le = mhd::launch_step(step_launch(l, c), l->cap);
+        le = launch_lattice_step(l, c, l->cap);
         c ^= 1;
     }
     cudaError_t ee = cudaStreamEndCapture(l->cap, &g);
@@ -301,7 +313,7 @@ mhd_status mhd_advance(mhd_lattice* l, long long nsteps) {
         l->step += kGraphSteps;
     }
     while (nsteps > 0) {
-        CK(mhd::launch_step(step_launch(l, l->cur), l->stream), "step launch");
+        CK(launch_lattice_step(l, l->cur, l->stream), "step launch");
         l->cur ^= 1;
         --nsteps;
         ++l->step;
@@ -409,6 +421,92 @@ mhd_status mhd_set_populations(mhd_lattice* l, const double* f, const double* g)
            "plane in kernel");
         CK(cudaStreamSynchronize(l->stream), "mhd_set_populations");
     }
+    l->fields_set = true;
+    l->prev_valid = false;
+    l->state_is_eq = false;
+    return MHD_OK;
+}
+
+mhd_status mhd_set_closure(mhd_lattice* l, const mhd_mlp* mlp) {
+    if (!l) return fail(MHD_EINVAL, "lattice is NULL");
+    CK(cudaSetDevice(l->dev), "cudaSetDevice");
+    CK(cudaStreamSynchronize(l->stream), "mhd_set_closure");
+    if (!mlp) {
+        if (l->closure_buf) cudaFree(l->closure_buf);
+        l->closure_buf = nullptr;
+        drop_graphs(l);
+        return MHD_OK;
+    }
+    if (l->p.precision != MHD_FP32 || l->p.bc_x != MHD_PERIODIC || l->p.bc_y != MHD_PERIODIC)
+        return fail(MHD_EINVAL, "the closure runs on FP32 periodic lattices");
+    using namespace mhd;
+    const size_t nbf = (size_t)kHid * kInPad + (size_t)kHid * kHid + (size_t)kOutPad * kHid;
+    const size_t nfl = 2 * kHid + kOutPad + 2 * kIn + kOut;
+    const size_t bytes = nbf * sizeof(__nv_bfloat16) + nfl * sizeof(float);
+    if (!l->closure_buf) CK(cudaMalloc(&l->closure_buf, bytes), "cudaMalloc(closure)");
+    ClosureParamsDev src;
+    mhd_internal_closure_params(mlp, &src);
+    auto* bf = static_cast<__nv_bfloat16*>(l->closure_buf);
+    auto* fl = reinterpret_cast<float*>(bf + nbf);
+    ClosureParamsDev& cp = l->closure;
+    cp.Wt1 = bf;
+    cp.Wt2 = bf + kHid * kInPad;
+    cp.Wt3 = bf + kHid * kInPad + kHid * kHid;
+    cp.b1 = fl;
+    cp.b2 = fl + kHid;
+    cp.b3 = fl + 2 * kHid;
+    cp.mean = fl + 2 * kHid + kOutPad;
+    cp.scale = fl + 2 * kHid + kOutPad + kIn;
+    cp.out_scale = fl + 2 * kHid + kOutPad + 2 * kIn;
+    struct { const void* s; const void* d; size_t b; } parts[] = {
+        {src.Wt1, cp.Wt1, sizeof(__nv_bfloat16) * kHid * kInPad},
+        {src.Wt2, cp.Wt2, sizeof(__nv_bfloat16) * kHid * kHid},
+        {src.Wt3, cp.Wt3, sizeof(__nv_bfloat16) * kOutPad * kHid},
+        {src.b1, cp.b1, sizeof(float) * kHid},
+        {src.b2, cp.b2, sizeof(float) * kHid},
+        {src.b3, cp.b3, sizeof(float) * kOutPad},
+        {src.mean, cp.mean, sizeof(float) * kIn},
+        {src.scale, cp.scale, sizeof(float) * kIn},
+        {src.out_scale, cp.out_scale, sizeof(float) * kOut}};
+    for (auto& q : parts)
+        CK(cudaMemcpyAsync(const_cast<void*>(q.d), q.s, q.b, cudaMemcpyDeviceToDevice, l->stream), "copy closure");
+    CK(cudaStreamSynchronize(l->stream), "mhd_set_closure");
+    drop_graphs(l);
+    return MHD_OK;
+}
+
+mhd_status mhd_closure_filter(mhd_lattice* l, int factor, float* coarse_state) {
+    if (!l || !coarse_state) return fail(MHD_EINVAL, "NULL argument");
+    if (factor < 1 || l->nx % factor || l->ny % factor) return fail(MHD_EINVAL, "factor must divide nx and ny");
+    if (l->p.bc_x != MHD_PERIODIC || l->p.bc_y != MHD_PERIODIC) return fail(MHD_EINVAL, "periodic lattices only");
+    if (!l->prev_valid) return fail(MHD_ESTATE, "needs the state after a step (advance first)");
+    CK(cudaSetDevice(l->dev), "cudaSetDevice");
+    CK(mhd::launch_filter(l->L, l->p.precision, l->buf[l->cur ^ 1], factor, coarse_state, l->stream), "filter kernel");
+    CK(cudaStreamSynchronize(l->stream), "mhd_closure_filter");
+    return MHD_OK;
+}
+
+mhd_status mhd_closure_sgs_targets(mhd_lattice* l, int factor, double tau_coarse, float* targets) {
+    if (!l || !targets) return fail(MHD_EINVAL, "NULL argument");
+    if (factor < 1 || l->nx % factor || l->ny % factor) return fail(MHD_EINVAL, "factor must divide nx and ny");
+    if (l->p.bc_x != MHD_PERIODIC || l->p.bc_y != MHD_PERIODIC) return fail(MHD_EINVAL, "periodic lattices only");
+    if (!(tau_coarse > 0.5) || std::fabs(1.0 - 1.0 / tau_coarse) < 1e-12)
+        return fail(MHD_EINVAL, "tau_coarse must be > 1/2 and != 1");
+    if (!l->prev_valid) return fail(MHD_ESTATE, "needs the state after a step (advance first)");
+    if (l->p.rho0 != 1.0) return fail(MHD_EINVAL, "rho0 = 1 only");
+    CK(cudaSetDevice(l->dev), "cudaSetDevice");
+    CK(mhd::launch_sgs(l->L, l->p.precision, l->buf[l->cur ^ 1], factor, tau_coarse, targets, l->stream),
+       "sgs kernel");
+    CK(cudaStreamSynchronize(l->stream), "mhd_closure_sgs_targets");
+    return MHD_OK;
+}
+
+mhd_status mhd_set_precollision_state(mhd_lattice* l, const float* state) {
+    if (!l || !state) return fail(MHD_EINVAL, "NULL argument");
+    if (l->p.bc_x != MHD_PERIODIC || l->p.bc_y != MHD_PERIODIC) return fail(MHD_EINVAL, "periodic lattices only");
+    CK(cudaSetDevice(l->dev), "cudaSetDevice");
+    CK(mhd::launch_unstream(l->L, l->p.precision, l->buf[l->cur], state, l->stream), "unstream kernel");
+    CK(cudaStreamSynchronize(l->stream), "mhd_set_precollision_state");
     l->fields_set = true;
     l->prev_valid = false;
     l->state_is_eq = false;

@@ -1,0 +1,840 @@
+// closure.cu -- learned sub-grid closure for coarse lattices: data
+// generation (box filter, features, one-step targets), BF16 tensor-core MLP
+// training (forward, backward, Adam with FP32 master weights), and a closure
+// variant of the fused step that evaluates the MLP per node and adds its
+// output to the projected a1^(2) before the recursion (task 3 of the
+// paper's "Algorithm of computation").  The closure is not part of the paper.
+//
+// MLP: 24 -> 64 -> 64 -> 3, ReLU, y = out_scale * (W3 h2 + b3) with
+// h1 = relu(W1 xn + b1), h2 = relu(W2 h1 + b2), xn = (x - mean) * scale.
+// All products run on mma.sync.m16n8k16 BF16 with FP32 accumulation; the
+// layer input (features, activations, output gradients) and the weights are
+// rounded to BF16 (round to nearest even), everything else is FP32.
+//
+// Feature columns (per node, from the pre-collision state):
+//   0 rho - rho0, 1 u_x, 2 u_y, 3 b_x, 4 b_y, 5..7 a1^(2) xx, xy, yy,
+//   then for q in (u_x, u_y, b_x, b_y): d_x q, d_y q (isotropic lattice
+//   gradient), the 9-point lattice Laplacian, d_xy q   (8 + 16 = 24).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mhd.h"
+#include "closure_internal.h"
+#include "internal.h"
+#include "lbm_device.cuh"
+#include "step_row.cuh"
+
+namespace mhd {
+
+using bf16 = __nv_bfloat16;
+
+// ---- MMA helpers -------------------------------------------------------------
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    uint32_t u;
+    memcpy(&u, &v, 4);
+    return u;
+}
+// two consecutive bf16 (4-byte aligned)
+__device__ __forceinline__ uint32_t ld2(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+// two separate bf16
+__device__ __forceinline__ uint32_t ld11(const bf16* lo, const bf16* hi) {
+    return (uint32_t)__bfloat16_as_ushort(*lo) | ((uint32_t)__bfloat16_as_ushort(*hi) << 16);
+}
+
+// ---- feature stencils -------------------------------------------------------
+// s[q][r][c] holds q in (u_x, u_y, b_x, b_y) for a tile plus a one-node
+// halo; (r, c) = (ly + 1, lx + 1) is the node.
+template <int HX, int HY>
+__device__ __forceinline__ void stencil_features(const float (*s)[HY][HX], int lx, int ly, float* out16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float C = s[q][ly + 1][lx + 1];
+        const float E = s[q][ly + 1][lx + 2], W = s[q][ly + 1][lx];
+        const float N = s[q][ly + 2][lx + 1], S = s[q][ly][lx + 1];
+        const float NE = s[q][ly + 2][lx + 2], NW = s[q][ly + 2][lx];
+        const float SE = s[q][ly][lx + 2], SW = s[q][ly][lx];
+        out16[4 * q + 0] = (1.0f / 3.0f) * (E - W) + (1.0f / 12.0f) * ((NE - NW) + (SE - SW));
+        out16[4 * q + 1] = (1.0f / 3.0f) * (N - S) + (1.0f / 12.0f) * ((NE - SE) + (NW - SW));
+        out16[4 * q + 2] = (4.0f * ((E + W) + (N + S)) + ((NE + NW) + (SE + SW)) - 20.0f * C) * (1.0f / 6.0f);
+        out16[4 * q + 3] = 0.25f * ((NE - NW) - (SE - SW));
+    }
+}
+
+// rho - rho0, u, b, projected a1^(2) of pre-collision deviations (FP32)
+__device__ __forceinline__ void point_features(const float (&f)[9], const float (&g)[10], float rho0,
+                                               float* out8) {
+    const Moments<float> m = moments(f, g, rho0);
+    const float Mxx = 0.5f * (m.by * m.by - m.bx * m.bx), Mxy = -m.bx * m.by;
+    const float Sxx = f[1] + f[2] + f[3] + f[5] + f[6] + f[7];
+    const float Syy = f[1] + f[3] + f[4] + f[5] + f[7] + f[8];
+    const float Sxy = (f[3] + f[7]) - (f[1] + f[5]);
+    out8[0] = m.drho;
+    out8[1] = m.ux;
+    out8[2] = m.uy;
+    out8[3] = m.bx;
+    out8[4] = m.by;
+    out8[5] = Sxx - (1.0f / 3.0f) * m.drho - m.mx * m.ux - Mxx;
+    out8[6] = Sxy - m.mx * m.uy - Mxy;
+    out8[7] = Syy - (1.0f / 3.0f) * m.drho - m.my * m.uy + Mxx;
+}
+
+// ---- data generation ---------------------------------------------------------
+// Box filter of the fine pre-collision populations (gathered from the buffer
+// the last step read) into a packed coarse state (FP32 deviations).
+template <int PREC>
+__global__ void filter_kernel(const void* prev, Layout L, int r, float* out) {
+    using S = typename Prec<PREC>::S;
+    const int ncx = L.nx / r, ncy = L.ny / r;
+    const long long nc = (long long)ncx * ncy;
+    const float inv = 1.0f / (float)(r * r);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nc;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int X = (int)(k % ncx), Y = (int)(k / ncx);
+        float acc[kPlanes];
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) acc[p] = 0.0f;
+        for (int dy = 0; dy < r; ++dy)
+            for (int dx = 0; dx < r; ++dx) {
+                float f[9], g[10];
+                gather_node<S, float>(static_cast<const S*>(prev), X * r + dx, Y * r + dy, L.nx, L.ny,
+                                      L.pitch, L.plane, 0, 0, f, g);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) acc[i] += f[i];
+#pragma unroll
+                for (int q = 0; q < 10; ++q) acc[9 + q] += g[q];
+            }
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) out[(long long)p * nc + k] = acc[p] * inv;
+    }
+}
+
+// Filtered sub-grid momentum flux of a fine lattice's pre-collision state
+// (FP64 arithmetic): per coarse node the r x r block averages of rho,
+// rho u, b and of rho u u + M(b); tau_sgs = <flux> - flux of the averaged
+// fields (u = <rho u>/<rho>); out = tau_sgs / (1 - omega_coarse).
+template <int PREC>
+__global__ void sgs_kernel(const void* prev, Layout L, int r, double inv_om1, float* out) {
+    using S = typename Prec<PREC>::S;
+    const int ncx = L.nx / r, ncy = L.ny / r;
+    const long long nc = (long long)ncx * ncy;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nc;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int X = (int)(k % ncx), Y = (int)(k / ncx);
+        double R = 0, MX = 0, MY = 0, BX = 0, BY = 0, Fxx = 0, Fxy = 0, Fyy = 0;
+        const double rho0 = 1.0;
+        for (int dy = 0; dy < r; ++dy)
+            for (int dx = 0; dx < r; ++dx) {
+                float f[9], g[10];
+                gather_node<S, float>(static_cast<const S*>(prev), X * r + dx, Y * r + dy, L.nx, L.ny,
+                                      L.pitch, L.plane, 0, 0, f, g);
+                double fd[9], gd[10];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) fd[i] = (double)f[i];
+#pragma unroll
+                for (int q = 0; q < 10; ++q) gd[q] = (double)g[q];
+                const Moments<double> m = moments<double>(fd, gd, rho0);
+                const double b2 = m.bx * m.bx + m.by * m.by;
+                R += m.rho; MX += m.mx; MY += m.my; BX += m.bx; BY += m.by;
+                Fxx += m.mx * m.ux + 0.5 * b2 - m.bx * m.bx;
+                Fxy += m.mx * m.uy - m.bx * m.by;
+                Fyy += m.my * m.uy + 0.5 * b2 - m.by * m.by;
+            }
+        const double a = 1.0 / (double)(r * r);
+        R *= a; MX *= a; MY *= a; BX *= a; BY *= a; Fxx *= a; Fxy *= a; Fyy *= a;
+        const double UX = MX / R, UY = MY / R, B2 = BX * BX + BY * BY;
+        out[3 * k + 0] = (float)((Fxx - (R * UX * UX + 0.5 * B2 - BX * BX)) * inv_om1);
+        out[3 * k + 1] = (float)((Fxy - (R * UX * UY - BX * BY)) * inv_om1);
+        out[3 * k + 2] = (float)((Fyy - (R * UY * UY + 0.5 * B2 - BY * BY)) * inv_om1);
+    }
+}
+
+constexpr int kFTX = 32, kFTY = 8, kFHX = kFTX + 2, kFHY = kFTY + 2;
+
+// Features of a packed coarse pre-collision state (FP32 deviations).
+__global__ void __launch_bounds__(256) features_kernel(const float* __restrict__ st, int nx, int ny,
+                                                       float rho0, float* __restrict__ X) {
+    __shared__ float sm[4][kFHY][kFHX];
+    const long long n = (long long)nx * ny;
+    const int tid = threadIdx.y * kFTX + threadIdx.x;
+    const int x0 = blockIdx.x * kFTX, y0 = blockIdx.y * kFTY;
+    for (int r = tid; r < kFHX * kFHY; r += kFTX * kFTY) {
+        const int hx = r % kFHX, hy = r / kFHX;
+        const int gx = ((x0 - 1 + hx) % nx + nx) % nx, gy = ((y0 - 1 + hy) % ny + ny) % ny;
+        const long long o = (long long)gy * nx + gx;
+        float f[9], g[10], pf[8];
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) {
+            const float v = st[(long long)p * n + o];
+            if (p < 9) f[p] = v; else g[p - 9] = v;
+        }
+        point_features(f, g, rho0, pf);
+        sm[0][hy][hx] = pf[1]; sm[1][hy][hx] = pf[2]; sm[2][hy][hx] = pf[3]; sm[3][hy][hx] = pf[4];
+    }
+    __syncthreads();
+    const int lx = threadIdx.x, ly = threadIdx.y, x = x0 + lx, y = y0 + ly;
+    if (x >= nx || y >= ny) return;
+    const long long o = (long long)y * nx + x;
+    float f[9], g[10], feat[kIn];
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        const float v = st[(long long)p * n + o];
+        if (p < 9) f[p] = v; else g[p - 9] = v;
+    }
+    point_features(f, g, rho0, feat);
+    stencil_features<kFHX, kFHY>(sm, lx, ly, feat + 8);
+#pragma unroll
+    for (int c = 0; c < kIn; ++c) X[o * kIn + c] = feat[c];
+}
+
+// One-step targets (FP64 arithmetic from FP32 states):
+//   dA = (sum_i H2_i F*_i - a0^(2)) / (1 - omega) - a1^(2)(T),
+//   F*_i(x) = F_i(x + c_i, T+1)   (periodic).
+__global__ void targets_kernel(const float* __restrict__ sT, const float* __restrict__ sT1, int nx, int ny,
+                               double rho0, double omega, float* __restrict__ out) {
+    const long long n = (long long)nx * ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(k % nx), y = (int)(k / nx);
+        double f[9], g[10];
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) {
+            const double v = (double)sT[(long long)p * n + k];
+            if (p < 9) f[p] = v; else g[p - 9] = v;
+        }
+        const Moments<double> m = moments<double>(f, g, rho0);
+        const double Mxx = 0.5 * (m.by * m.by - m.bx * m.bx), Mxy = -m.bx * m.by;
+        const double a2xx = (f[1] + f[2] + f[3] + f[5] + f[6] + f[7]) - m.drho / 3.0 - m.mx * m.ux - Mxx;
+        const double a2yy = (f[1] + f[3] + f[4] + f[5] + f[7] + f[8]) - m.drho / 3.0 - m.my * m.uy + Mxx;
+        const double a2xy = ((f[3] + f[7]) - (f[1] + f[5])) - m.mx * m.uy - Mxy;
+        double sxx = 0, sxy = 0, syy = 0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int cx = cx_of(i), cy = cy_of(i);
+            const int xs = (x + cx + nx) % nx, ys = (y + cy + ny) % ny;
+            const double v = (double)sT1[(long long)i * n + (long long)ys * nx + xs];
+            sxx += (cx * cx - 1.0 / 3.0) * v;
+            sxy += (double)(cx * cy) * v;
+            syy += (cy * cy - 1.0 / 3.0) * v;
+        }
+        const double om1 = 1.0 - omega;
+        out[3 * k + 0] = (float)((sxx - (m.mx * m.ux + Mxx)) / om1 - a2xx);
+        out[3 * k + 1] = (float)((sxy - (m.mx * m.uy + Mxy)) / om1 - a2xy);
+        out[3 * k + 2] = (float)((syy - (m.my * m.uy - Mxx)) / om1 - a2yy);
+    }
+}
+
+// ---- MLP training kernels ------------------------------------------------------
+// Layer forward on one warp per 16-row tile: out = A (M x K) * W^T + b with
+// Wt stored output-major (N x K).  RELU: write Z (FP32) and H = bf16(relu(Z));
+// else write Y (FP32).
+template <int K, int N, bool RELU>
+__global__ void mlp_fwd(const bf16* __restrict__ A, const bf16* __restrict__ Wt, const float* __restrict__ bias,
+                        int M, float* __restrict__ Z, bf16* __restrict__ H) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int mt = warp; mt * 16 < M; mt += nwarps) {
+        const int m0 = mt * 16;
+        uint32_t a[K / 16][4];
+#pragma unroll
+        for (int c = 0; c < K / 16; ++c) {
+            a[c][0] = ld2(A + (long long)(m0 + g) * K + 16 * c + 2 * t);
+            a[c][1] = ld2(A + (long long)(m0 + g + 8) * K + 16 * c + 2 * t);
+            a[c][2] = ld2(A + (long long)(m0 + g) * K + 16 * c + 2 * t + 8);
+            a[c][3] = ld2(A + (long long)(m0 + g + 8) * K + 16 * c + 2 * t + 8);
+        }
+#pragma unroll
+        for (int j = 0; j < N / 8; ++j) {
+            const float b0 = bias[8 * j + 2 * t], b1 = bias[8 * j + 2 * t + 1];
+            float d[4] = {b0, b1, b0, b1};
+#pragma unroll
+            for (int c = 0; c < K / 16; ++c) {
+                const uint32_t b[2] = {ld2(Wt + (8 * j + g) * K + 16 * c + 2 * t),
+                                       ld2(Wt + (8 * j + g) * K + 16 * c + 2 * t + 8)};
+                mma16816(d, a[c], b);
+            }
+            const long long r0 = (long long)(m0 + g) * N + 8 * j + 2 * t, r1 = r0 + 8LL * N;
+            Z[r0] = d[0]; Z[r0 + 1] = d[1]; Z[r1] = d[2]; Z[r1 + 1] = d[3];
+            if (RELU) {
+                *reinterpret_cast<uint32_t*>(H + r0) = pack2(fmaxf(d[0], 0.f), fmaxf(d[1], 0.f));
+                *reinterpret_cast<uint32_t*>(H + r1) = pack2(fmaxf(d[2], 0.f), fmaxf(d[3], 0.f));
+            }
+        }
+    }
+}
+
+// dH = (dZ (M x NO) * W^T) masked by relu'(Zprev), W stored input-major
+// (KI x NO).  Writes FP32 and BF16 copies.
+template <int NO, int KI>
+__global__ void mlp_bwd_data(const bf16* __restrict__ dZ, const bf16* __restrict__ W,
+                             const float* __restrict__ Zprev, int M, float* __restrict__ dH,
+                             bf16* __restrict__ dHb) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int mt = warp; mt * 16 < M; mt += nwarps) {
+        const int m0 = mt * 16;
+        uint32_t a[NO / 16][4];
+#pragma unroll
+        for (int c = 0; c < NO / 16; ++c) {
+            a[c][0] = ld2(dZ + (long long)(m0 + g) * NO + 16 * c + 2 * t);
+            a[c][1] = ld2(dZ + (long long)(m0 + g + 8) * NO + 16 * c + 2 * t);
+            a[c][2] = ld2(dZ + (long long)(m0 + g) * NO + 16 * c + 2 * t + 8);
+            a[c][3] = ld2(dZ + (long long)(m0 + g + 8) * NO + 16 * c + 2 * t + 8);
+        }
+#pragma unroll
+        for (int j = 0; j < KI / 8; ++j) {
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int c = 0; c < NO / 16; ++c) {
+                const uint32_t b[2] = {ld2(W + (8 * j + g) * NO + 16 * c + 2 * t),
+                                       ld2(W + (8 * j + g) * NO + 16 * c + 2 * t + 8)};
+                mma16816(d, a[c], b);
+            }
+            const long long r0 = (long long)(m0 + g) * KI + 8 * j + 2 * t, r1 = r0 + 8LL * KI;
+            const float v0 = Zprev[r0] > 0.f ? d[0] : 0.f, v1 = Zprev[r0 + 1] > 0.f ? d[1] : 0.f;
+            const float v2 = Zprev[r1] > 0.f ? d[2] : 0.f, v3 = Zprev[r1 + 1] > 0.f ? d[3] : 0.f;
+            dH[r0] = v0; dH[r0 + 1] = v1; dH[r1] = v2; dH[r1 + 1] = v3;
+            *reinterpret_cast<uint32_t*>(dHb + r0) = pack2(v0, v1);
+            *reinterpret_cast<uint32_t*>(dHb + r1) = pack2(v2, v3);
+        }
+    }
+}
+
+// Weight gradient partials: P[block][k][n] = sum over the block's rows m of
+// Act[m][k] * dZ[m][n] (KI x NO), as A = Act^T (rows k, columns m) times
+// B = dZ (rows m, columns n).  8 warps; warp w owns output tiles w, w+8, ...
+constexpr int kWgradWarps = 8;
+template <int KI, int NO>
+__global__ void __launch_bounds__(256) mlp_wgrad(const bf16* __restrict__ Act, const bf16* __restrict__ dZ,
+                                                 int M, int rows_per_block, float* __restrict__ P) {
+    constexpr int KT = KI / 16, NT = NO / 8, TILES = KT * NT;
+    constexpr int PER = (TILES + kWgradWarps - 1) / kWgradWarps;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, w = threadIdx.x >> 5;
+    float acc[PER][4];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) acc[u][0] = acc[u][1] = acc[u][2] = acc[u][3] = 0.f;
+    const int mb = blockIdx.x * rows_per_block, me = min(M, mb + rows_per_block);
+    for (int m0 = mb; m0 < me; m0 += 16) {
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int tile = w + u * kWgradWarps;
+            if (tile >= TILES) break;
+            const int kt = tile / NT, nt = tile % NT;
+            const bf16* a0 = Act + (long long)(m0 + 2 * t) * KI + 16 * kt + g;
+            const uint32_t a[4] = {ld11(a0, a0 + KI), ld11(a0 + 8, a0 + KI + 8),
+                                   ld11(a0 + 8LL * KI, a0 + 9LL * KI),
+                                   ld11(a0 + 8LL * KI + 8, a0 + 9LL * KI + 8)};
+            const bf16* b0 = dZ + (long long)(m0 + 2 * t) * NO + 8 * nt + g;
+            const uint32_t b[2] = {ld11(b0, b0 + NO), ld11(b0 + 8LL * NO, b0 + 9LL * NO)};
+            mma16816(acc[u], a, b);
+        }
+    }
+    float* out = P + (long long)blockIdx.x * KI * NO;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int tile = w + u * kWgradWarps;
+        if (tile >= TILES) break;
+        const int kt = tile / NT, nt = tile % NT;
+        const int r = 16 * kt + g, c = 8 * nt + 2 * t;
+        out[r * NO + c] = acc[u][0];
+        out[r * NO + c + 1] = acc[u][1];
+        out[(r + 8) * NO + c] = acc[u][2];
+        out[(r + 8) * NO + c + 1] = acc[u][3];
+    }
+}
+
+// Column sums of an FP32 (M x NO) matrix into per-block partials P[block][NO].
+template <int NO>
+__global__ void col_partials(const float* __restrict__ dZ, int M, int rows_per_block, float* __restrict__ P) {
+    const int mb = blockIdx.x * rows_per_block, me = min(M, mb + rows_per_block);
+    for (int c = threadIdx.x; c < NO; c += blockDim.x) {
+        float s = 0.f;
+        for (int m = mb; m < me; ++m) s += dZ[(long long)m * NO + c];
+        P[(long long)blockIdx.x * NO + c] = s;
+    }
+}
+
+// out[i] = sum_b P[b][i] in block order (deterministic).
+__global__ void reduce_partials(const float* __restrict__ P, int nblocks, int width, float* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < width; i += gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int b = 0; b < nblocks; ++b) s += P[(long long)b * width + i];
+        out[i] = s;
+    }
+}
+
+// Batch assembly: rows idx[r] of X (n x 24, raw) -> xb (rows x 32, bf16,
+// normalised, zero padded), T (n x 3) -> tb (rows x 3); rows beyond nreal zero.
+__global__ void gather_batch(const float* __restrict__ X, const float* __restrict__ T, const int* __restrict__ idx,
+                             int nreal, int rows, const float* __restrict__ prm, bf16* __restrict__ xb,
+                             float* __restrict__ tb) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+        const bool ok = r < nreal;
+        const long long s = ok ? (idx ? idx[r] : r) : 0;
+#pragma unroll
+        for (int c = 0; c < kInPad; ++c) {
+            float v = 0.f;
+            if (ok && c < kIn) v = (X[s * kIn + c] - prm[kOffMean + c]) * prm[kOffScale + c];
+            xb[(long long)r * kInPad + c] = __float2bfloat16_rn(v);
+        }
+#pragma unroll
+        for (int c = 0; c < kOut; ++c) tb[(long long)r * kOut + c] = (ok && T) ? T[s * kOut + c] : 0.f;
+    }
+}
+
+// Loss gradient in scaled output units: dY = 2 (yn - t / out_scale) / (nreal * 3)
+// for real rows / columns (0 elsewhere); loss partial sums per block.
+__global__ void loss_grad(const float* __restrict__ Y, const float* __restrict__ tb, int nreal, int rows,
+                          const float* __restrict__ prm, float* __restrict__ dYf, bf16* __restrict__ dYb,
+                          double* __restrict__ lossp) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    const float inv = 2.0f / (float)(nreal * kOut);
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < kOutPadK; ++c) {
+            float gr = 0.f;
+            if (r < nreal && c < kOut) {
+                const float d = Y[(long long)r * kOutPad + c] - tb[(long long)r * kOut + c] / prm[kOffOutScale + c];
+                acc += (double)d * (double)d;
+                gr = inv * d;
+            }
+            if (c < kOutPad) dYf[(long long)r * kOutPad + c] = gr;
+            dYb[(long long)r * kOutPadK + c] = __float2bfloat16_rn(gr);
+        }
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) lossp[blockIdx.x] = red[0];
+}
+
+// Adam on the trainable part of the parameter blob.
+__global__ void adam_kernel(float* __restrict__ prm, const float* __restrict__ grad, float* __restrict__ m,
+                            float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (int i = kOffW1 + blockIdx.x * blockDim.x + threadIdx.x; i < kBlob; i += gridDim.x * blockDim.x) {
+        const float gi = grad[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        prm[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// BF16 weight copies in both layouts and padded FP32 biases from the blob.
+__global__ void refresh_weights(const float* __restrict__ prm, MlpDev d) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // layer 1: W1[in 24][out 64] -> Wt1 (64 x 32), W1b (32 x 64)
+    if (i < kHid * kInPad) {
+        const int o = i / kInPad, k = i % kInPad;
+        const float w = k < kIn ? prm[kOffW1 + k * kHid + o] : 0.f;
+        d.Wt1[o * kInPad + k] = __float2bfloat16_rn(w);
+        d.W1[k * kHid + o] = __float2bfloat16_rn(w);
+    }
+    if (i < kHid * kHid) {
+        const int o = i / kHid, k = i % kHid;
+        const float w = prm[kOffW2 + k * kHid + o];
+        d.Wt2[o * kHid + k] = __float2bfloat16_rn(w);
+        d.W2[k * kHid + o] = __float2bfloat16_rn(w);
+    }
+    if (i < kOutPad * kHid) {  // Wt3: 8 x 64
+        const int o = i / kHid, k = i % kHid;
+        d.Wt3[o * kHid + k] = __float2bfloat16_rn(o < kOut ? prm[kOffW3 + k * kOut + o] : 0.f);
+    }
+    if (i < kHid * kOutPadK) {  // W3b: 64 x 16
+        const int k = i / kOutPadK, o = i % kOutPadK;
+        d.W3[k * kOutPadK + o] = __float2bfloat16_rn(o < kOut ? prm[kOffW3 + k * kOut + o] : 0.f);
+    }
+    if (i < kHid) {
+        d.b1[i] = prm[kOffB1 + i];
+        d.b2[i] = prm[kOffB2 + i];
+    }
+    if (i < kOutPad) d.b3[i] = i < kOut ? prm[kOffB3 + i] : 0.f;
+}
+
+// Per-column mean and scale (1 / std) of X (n x 24) and std of T (n x 3):
+// per-block FP64 partial sums, then a one-block finish.
+__global__ void stats_partials(const float* __restrict__ X, const float* __restrict__ T, long long n,
+                               double* __restrict__ P) {
+    constexpr int W = kIn + kOut;
+    __shared__ double s1[W][8], s2[W][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double a1[W], a2[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) a1[c] = a2[c] = 0.0;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+            const double v = c < kIn ? (double)X[r * kIn + c] : (double)T[r * kOut + c - kIn];
+            a1[c] += v;
+            a2[c] += v * v;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+        double v1 = a1[c], v2 = a2[c];
+        for (int o = 16; o > 0; o >>= 1) {
+            v1 += __shfl_down_sync(0xffffffffu, v1, o);
+            v2 += __shfl_down_sync(0xffffffffu, v2, o);
+        }
+        if (lane == 0) { s1[c][warp] = v1; s2[c][warp] = v2; }
+    }
+    __syncthreads();
+    if (threadIdx.x < W) {
+        double v1 = 0, v2 = 0;
+        for (int w = 0; w < 8; ++w) { v1 += s1[threadIdx.x][w]; v2 += s2[threadIdx.x][w]; }
+        P[(long long)blockIdx.x * 2 * W + threadIdx.x] = v1;
+        P[(long long)blockIdx.x * 2 * W + W + threadIdx.x] = v2;
+    }
+}
+
+__global__ void stats_finish(const double* __restrict__ P, int nblocks, long long n, float* __restrict__ prm) {
+    constexpr int W = kIn + kOut;
+    const int c = threadIdx.x;
+    if (c >= W) return;
+    double v1 = 0, v2 = 0;
+    for (int b = 0; b < nblocks; ++b) { v1 += P[(long long)b * 2 * W + c]; v2 += P[(long long)b * 2 * W + W + c]; }
+    const double mean = v1 / (double)n;
+    const double var = fmax(v2 / (double)n - mean * mean, 0.0);
+    const double sd = sqrt(var);
+    if (c < kIn) {
+        prm[kOffMean + c] = (float)mean;
+        prm[kOffScale + c] = (float)(sd > 0 ? 1.0 / sd : 1.0);
+    } else {
+        prm[kOffOutScale + c - kIn] = (float)(sd > 0 ? sd : 1.0);
+    }
+}
+
+// ---- closure step (inference fused beside the collision) ------------------------
+constexpr int kCTX = 32, kCTY = 8, kCHX = kCTX + 2, kCHY = kCTY + 2;
+constexpr int kFeatStride = 40;  // bf16 per feature row (conflict-free fragment loads)
+
+struct ClosureShared {
+    bf16 Wt1[kHid * kInPad];
+    bf16 Wt2[kHid * kHid];
+    bf16 Wt3[kOutPad * kHid];
+    float b1[kHid], b2[kHid], b3[kOutPad];
+    float mean[kIn], scale[kIn], out_scale[kOut];
+    float mom[4][kCHY][kCHX];
+    bf16 feat[kCTX * kCTY * kFeatStride];
+    float da[kCTX * kCTY][kOut];
+};
+
+// One warp evaluates the MLP for 16 nodes (rows m0..m0+15 of the feature
+// tile) and writes out_scale * y into sh.da.
+__device__ __forceinline__ void mlp_rows16(ClosureShared& sh, int m0, int lane) {
+    const int g = lane >> 2, t = lane & 3;
+    uint32_t a1[2][4];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const bf16* r0 = sh.feat + (m0 + g) * kFeatStride + 16 * c + 2 * t;
+        const bf16* r1 = r0 + 8 * kFeatStride;
+        a1[c][0] = ld2(r0); a1[c][1] = ld2(r1); a1[c][2] = ld2(r0 + 8); a1[c][3] = ld2(r1 + 8);
+    }
+    uint32_t h[4][4];  // layer input as A fragments (K = 64)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        float d[4] = {sh.b1[8 * j + 2 * t], sh.b1[8 * j + 2 * t + 1], sh.b1[8 * j + 2 * t], sh.b1[8 * j + 2 * t + 1]};
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const uint32_t b[2] = {ld2(sh.Wt1 + (8 * j + g) * kInPad + 16 * c + 2 * t),
+                                   ld2(sh.Wt1 + (8 * j + g) * kInPad + 16 * c + 2 * t + 8)};
+            mma16816(d, a1[c], b);
+        }
+        // accumulator of n-tile j becomes half of k-chunk j/2 of the next A
+        h[j >> 1][(j & 1) * 2 + 0] = pack2(fmaxf(d[0], 0.f), fmaxf(d[1], 0.f));
+        h[j >> 1][(j & 1) * 2 + 1] = pack2(fmaxf(d[2], 0.f), fmaxf(d[3], 0.f));
+    }
+    uint32_t h2[4][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        float d[4] = {sh.b2[8 * j + 2 * t], sh.b2[8 * j + 2 * t + 1], sh.b2[8 * j + 2 * t], sh.b2[8 * j + 2 * t + 1]};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const uint32_t a[4] = {h[c][0], h[c][1], h[c][2], h[c][3]};
+            const uint32_t b[2] = {ld2(sh.Wt2 + (8 * j + g) * kHid + 16 * c + 2 * t),
+                                   ld2(sh.Wt2 + (8 * j + g) * kHid + 16 * c + 2 * t + 8)};
+            mma16816(d, a, b);
+        }
+        h2[j >> 1][(j & 1) * 2 + 0] = pack2(fmaxf(d[0], 0.f), fmaxf(d[1], 0.f));
+        h2[j >> 1][(j & 1) * 2 + 1] = pack2(fmaxf(d[2], 0.f), fmaxf(d[3], 0.f));
+    }
+    float d[4] = {sh.b3[2 * t], sh.b3[2 * t + 1], sh.b3[2 * t], sh.b3[2 * t + 1]};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const uint32_t a[4] = {h2[c][0], h2[c][1], h2[c][2], h2[c][3]};
+        const uint32_t b[2] = {ld2(sh.Wt3 + g * kHid + 16 * c + 2 * t), ld2(sh.Wt3 + g * kHid + 16 * c + 2 * t + 8)};
+        mma16816(d, a, b);
+    }
+    // d0: (row g, col 2t), d1: (g, 2t+1), d2: (g+8, 2t), d3: (g+8, 2t+1)
+    if (2 * t < kOut) {
+        sh.da[m0 + g][2 * t] = d[0] * sh.out_scale[2 * t];
+        sh.da[m0 + g + 8][2 * t] = d[2] * sh.out_scale[2 * t];
+    }
+    if (2 * t + 1 < kOut) {
+        sh.da[m0 + g][2 * t + 1] = d[1] * sh.out_scale[2 * t + 1];
+        sh.da[m0 + g + 8][2 * t + 1] = d[3] * sh.out_scale[2 * t + 1];
+    }
+}
+
+__global__ void __launch_bounds__(256) step_closure(const StepArgs<float> a, const ClosureParamsDev cp,
+                                                    int ntx, int ntiles) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ClosureShared& sh = *reinterpret_cast<ClosureShared*>(smem_raw);
+    const int tid = threadIdx.y * kCTX + threadIdx.x, lane = threadIdx.x, ly = threadIdx.y;
+    for (int i = tid; i < kHid * kInPad; i += 256) sh.Wt1[i] = cp.Wt1[i];
+    for (int i = tid; i < kHid * kHid; i += 256) sh.Wt2[i] = cp.Wt2[i];
+    for (int i = tid; i < kOutPad * kHid; i += 256) sh.Wt3[i] = cp.Wt3[i];
+    for (int i = tid; i < kHid; i += 256) { sh.b1[i] = cp.b1[i]; sh.b2[i] = cp.b2[i]; }
+    if (tid < kOutPad) sh.b3[tid] = cp.b3[tid];
+    if (tid < kIn) { sh.mean[tid] = cp.mean[tid]; sh.scale[tid] = cp.scale[tid]; }
+    if (tid < kOut) sh.out_scale[tid] = cp.out_scale[tid];
+    const float* src = static_cast<const float*>(a.src);
+    float* dst = static_cast<float*>(a.dst);
+    for (int tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
+        __syncthreads();  // shared parameters loaded / previous tile done
+        const int x0 = (tl % ntx) * kCTX, y0 = (tl / ntx) * kCTY;
+        // halo and tile moments (pre-collision, gathered from the last post-collision state)
+        for (int r = tid; r < kCHX * kCHY; r += 256) {
+            const int hx = r % kCHX, hy = r / kCHX;
+            const int gx = ((x0 - 1 + hx) % a.nx + a.nx) % a.nx, gy = ((y0 - 1 + hy) % a.ny + a.ny) % a.ny;
+            float f[9], g[10];
+            gather_node<float, float>(src, gx, gy, a.nx, a.ny, a.pitch, a.plane, 0, 0, f, g);
+            const Moments<float> m = moments(f, g, a.np.rho0);
+            sh.mom[0][hy][hx] = m.ux; sh.mom[1][hy][hx] = m.uy;
+            sh.mom[2][hy][hx] = m.bx; sh.mom[3][hy][hx] = m.by;
+        }
+        const int x = x0 + lane, y = y0 + ly;
+        const bool inside = x < a.nx && y < a.ny;
+        float f[9], g[10];
+        if (inside) {
+            gather_node<float, float>(src, x, y, a.nx, a.ny, a.pitch, a.plane, 0, 0, f, g);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = 0.f;
+#pragma unroll
+            for (int q = 0; q < 10; ++q) g[q] = 0.f;
+        }
+        __syncthreads();
+        float feat[kIn];
+        if (inside) {
+            point_features(f, g, a.np.rho0, feat);
+            stencil_features<kCHX, kCHY>(sh.mom, lane, ly, feat + 8);
+        }
+        bf16* row = sh.feat + tid * kFeatStride;
+#pragma unroll
+        for (int c = 0; c < kInPad; c += 2) {
+            const float v0 = (inside && c < kIn) ? (feat[c] - sh.mean[c]) * sh.scale[c] : 0.f;
+            const float v1 = (inside && c + 1 < kIn) ? (feat[c + 1] - sh.mean[c + 1]) * sh.scale[c + 1] : 0.f;
+            *reinterpret_cast<uint32_t*>(row + c) = pack2(v0, v1);
+        }
+        __syncwarp();
+        // the warp's 32 nodes are rows 32*ly .. 32*ly + 31 of the feature tile
+        mlp_rows16(sh, 32 * ly, lane);
+        mlp_rows16(sh, 32 * ly + 16, lane);
+        __syncwarp();
+        if (inside) {
+            const float da[3] = {sh.da[tid][0], sh.da[tid][1], sh.da[tid][2]};
+            collide_impl<true, float>(f, g, a.np, da);
+            const long long o = (long long)y * a.pitch + x;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) dst[(long long)i * a.plane + o] = f[i];
+#pragma unroll
+            for (int q = 0; q < 10; ++q) dst[(long long)(9 + q) * a.plane + o] = g[q];
+        }
+    }
+}
+
+size_t closure_smem_bytes() { return sizeof(ClosureShared); }
+
+cudaError_t launch_step_closure(const StepLaunch& s, const ClosureParamsDev& cp, cudaStream_t st) {
+    if (s.prec != 1 || s.wall_x || s.wall_y) return cudaErrorInvalidValue;
+    StepArgs<float> a;
+    a.src = s.src;
+    a.dst = s.dst;
+    a.nx = s.L.nx;
+    a.ny = s.L.ny;
+    a.pitch = s.L.pitch;
+    a.plane = s.L.plane;
+    a.np.omega = (float)s.omega;
+    a.np.omega_m = (float)s.omega_m;
+    a.np.rho0 = (float)s.rho0;
+    a.np.variant = s.variant;
+    a.np.collision = s.collision;
+    a.wall_x = 0;
+    a.wall_y = 0;
+    const int ntx = (s.L.nx + kCTX - 1) / kCTX, nty = (s.L.ny + kCTY - 1) / kCTY, ntiles = ntx * nty;
+    const size_t smem = sizeof(ClosureShared);
+    cudaError_t e = cudaFuncSetAttribute(step_closure, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0, dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_closure, 256, smem);
+    if (e != cudaSuccess) return e;
+    const int blocks = std::max(1, std::min(ntiles, std::max(1, per_sm) * sms));
+    step_closure<<<blocks, dim3(kCTX, kCTY), smem, st>>>(a, cp, ntx, ntiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_filter(const Layout& L, int prec, const void* prev, int r, float* out, cudaStream_t st) {
+    const long long nc = (long long)(L.nx / r) * (L.ny / r);
+    const int blocks = (int)std::min<long long>((nc + 255) / 256, 152 * 16);
+    switch (prec) {
+    case 0: filter_kernel<0><<<blocks, 256, 0, st>>>(prev, L, r, out); break;
+    case 1: filter_kernel<1><<<blocks, 256, 0, st>>>(prev, L, r, out); break;
+    case 2: filter_kernel<2><<<blocks, 256, 0, st>>>(prev, L, r, out); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sgs(const Layout& L, int prec, const void* prev, int r, double tau_coarse, float* out,
+                       cudaStream_t st) {
+    const long long nc = (long long)(L.nx / r) * (L.ny / r);
+    const int blocks = (int)std::min<long long>((nc + 255) / 256, 152 * 16);
+    const double inv = 1.0 / (1.0 - 1.0 / tau_coarse);
+    switch (prec) {
+    case 0: sgs_kernel<0><<<blocks, 256, 0, st>>>(prev, L, r, inv, out); break;
+    case 1: sgs_kernel<1><<<blocks, 256, 0, st>>>(prev, L, r, inv, out); break;
+    case 2: sgs_kernel<2><<<blocks, 256, 0, st>>>(prev, L, r, inv, out); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_features(const float* st_, int nx, int ny, float rho0, float* X, cudaStream_t st) {
+    dim3 grid((nx + kFTX - 1) / kFTX, (ny + kFTY - 1) / kFTY);
+    features_kernel<<<grid, dim3(kFTX, kFTY), 0, st>>>(st_, nx, ny, rho0, X);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_targets(const float* sT, const float* sT1, int nx, int ny, double rho0, double omega,
+                           float* out, cudaStream_t st) {
+    const long long n = (long long)nx * ny;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 16);
+    targets_kernel<<<blocks, 256, 0, st>>>(sT, sT1, nx, ny, rho0, omega, out);
+    return cudaGetLastError();
+}
+
+// ---- training driver pieces ------------------------------------------------------
+constexpr int kRowsPerWgradBlock = 1024;
+
+__global__ void assemble_grad(const MlpDev d, float* __restrict__ grad);
+
+cudaError_t mlp_forward_backward(const MlpDev& d, const float* prm, int rows, int nreal, bool backward,
+                                 float* grad, double* lossp, int lossblocks, cudaStream_t st) {
+    const int fwd_blocks = std::max(1, std::min((rows / 16 + 7) / 8, 152 * 8));
+    mlp_fwd<kInPad, kHid, true><<<fwd_blocks, 256, 0, st>>>(d.xb, d.Wt1, d.b1, rows, d.Z1, d.H1);
+    mlp_fwd<kHid, kHid, true><<<fwd_blocks, 256, 0, st>>>(d.H1, d.Wt2, d.b2, rows, d.Z2, d.H2);
+    mlp_fwd<kHid, kOutPad, false><<<fwd_blocks, 256, 0, st>>>(d.H2, d.Wt3, d.b3, rows, d.Y, nullptr);
+    loss_grad<<<lossblocks, 256, 0, st>>>(d.Y, d.tb, nreal, rows, prm, d.dYf, d.dYb, lossp);
+    if (!backward) return cudaGetLastError();
+    const int wb = (rows + kRowsPerWgradBlock - 1) / kRowsPerWgradBlock;
+    // layer 3
+    mlp_wgrad<kHid, kOutPadK><<<wb, 256, 0, st>>>(d.H2, d.dYb, rows, kRowsPerWgradBlock, d.part);
+    reduce_partials<<<8, 256, 0, st>>>(d.part, wb, kHid * kOutPadK, d.gW3);
+    col_partials<kOutPad><<<wb, 32, 0, st>>>(d.dYf, rows, kRowsPerWgradBlock, d.part);
+    reduce_partials<<<1, 32, 0, st>>>(d.part, wb, kOutPad, d.gb3);
+    mlp_bwd_data<kOutPadK, kHid><<<fwd_blocks, 256, 0, st>>>(d.dYb, d.W3, d.Z2, rows, d.dH2f, d.dH2b);
+    // layer 2
+    mlp_wgrad<kHid, kHid><<<wb, 256, 0, st>>>(d.H1, d.dH2b, rows, kRowsPerWgradBlock, d.part);
+    reduce_partials<<<16, 256, 0, st>>>(d.part, wb, kHid * kHid, d.gW2);
+    col_partials<kHid><<<wb, 64, 0, st>>>(d.dH2f, rows, kRowsPerWgradBlock, d.part);
+    reduce_partials<<<1, 64, 0, st>>>(d.part, wb, kHid, d.gb2);
+    mlp_bwd_data<kHid, kHid><<<fwd_blocks, 256, 0, st>>>(d.dH2b, d.W2, d.Z1, rows, d.dH1f, d.dH1b);
+    // layer 1
+    mlp_wgrad<kInPad, kHid><<<wb, 256, 0, st>>>(d.xb, d.dH1b, rows, kRowsPerWgradBlock, d.part);
+    reduce_partials<<<8, 256, 0, st>>>(d.part, wb, kInPad * kHid, d.gW1);
+    col_partials<kHid><<<wb, 64, 0, st>>>(d.dH1f, rows, kRowsPerWgradBlock, d.part);
+    reduce_partials<<<1, 64, 0, st>>>(d.part, wb, kHid, d.gb1);
+    // assemble the blob-layout gradient
+    assemble_grad<<<(kBlob + 255) / 256, 256, 0, st>>>(d, grad);
+    return cudaGetLastError();
+}
+
+__global__ void assemble_grad(const MlpDev d, float* __restrict__ grad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kBlob) return;
+    float v = 0.f;
+    if (i >= kOffW1 && i < kOffB1) {
+        const int k = (i - kOffW1) / kHid, o = (i - kOffW1) % kHid;
+        v = d.gW1[k * kHid + o];
+    } else if (i >= kOffB1 && i < kOffW2) {
+        v = d.gb1[i - kOffB1];
+    } else if (i >= kOffW2 && i < kOffB2) {
+        v = d.gW2[i - kOffW2];
+    } else if (i >= kOffB2 && i < kOffW3) {
+        v = d.gb2[i - kOffB2];
+    } else if (i >= kOffW3 && i < kOffB3) {
+        const int k = (i - kOffW3) / kOut, o = (i - kOffW3) % kOut;
+        v = d.gW3[k * kOutPadK + o];
+    } else if (i >= kOffB3) {
+        v = d.gb3[i - kOffB3];
+    }
+    grad[i] = v;
+}
+
+cudaError_t launch_gather_batch(const float* X, const float* T, const int* idx, int nreal, int rows,
+                                const float* prm, const MlpDev& d, cudaStream_t st) {
+    const int blocks = std::max(1, std::min((rows + 255) / 256, 152 * 8));
+    gather_batch<<<blocks, 256, 0, st>>>(X, T, idx, nreal, rows, prm, d.xb, d.tb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* prm, const float* grad, float* m, float* v, float lr, float b1, float b2, float eps,
+                        long long t, cudaStream_t st) {
+    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    adam_kernel<<<24, 256, 0, st>>>(prm, grad, m, v, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refresh(const float* prm, const MlpDev& d, cudaStream_t st) {
+    refresh_weights<<<(kHid * kHid + 255) / 256, 256, 0, st>>>(prm, d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stats(const float* X, const float* T, long long n, double* P, int nblocks, float* prm,
+                         cudaStream_t st) {
+    stats_partials<<<nblocks, 256, 0, st>>>(X, T, n, P);
+    stats_finish<<<1, 32, 0, st>>>(P, nblocks, n, prm);
+    return cudaGetLastError();
+}
+
+__global__ void scale_outputs(const float* __restrict__ Y, int nreal, const float* __restrict__ prm,
+                              float* __restrict__ out) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreal; r += gridDim.x * blockDim.x)
+#pragma unroll
+        for (int c = 0; c < kOut; ++c) out[(long long)r * kOut + c] = Y[(long long)r * kOutPad + c] * prm[kOffOutScale + c];
+}
+
+cudaError_t launch_mlp_predict(const MlpDev& d, int rows, int nreal, const float* prm, float* Yraw, cudaStream_t st) {
+    const int fwd_blocks = std::max(1, std::min((rows / 16 + 7) / 8, 152 * 8));
+    mlp_fwd<kInPad, kHid, true><<<fwd_blocks, 256, 0, st>>>(d.xb, d.Wt1, d.b1, rows, d.Z1, d.H1);
+    mlp_fwd<kHid, kHid, true><<<fwd_blocks, 256, 0, st>>>(d.H1, d.Wt2, d.b2, rows, d.Z2, d.H2);
+    mlp_fwd<kHid, kOutPad, false><<<fwd_blocks, 256, 0, st>>>(d.H2, d.Wt3, d.b3, rows, d.Y, nullptr);
+    scale_outputs<<<std::max(1, std::min((nreal + 255) / 256, 1216)), 256, 0, st>>>(d.Y, nreal, prm, Yraw);
+    return cudaGetLastError();
+}
+
+}  // namespace mhd

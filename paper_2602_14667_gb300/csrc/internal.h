@@ -44,6 +44,9 @@ cudaError_t launch_init(const Layout& L, int prec, void* buf, const double* rho,
 // rho, u, b (FP64, nx*ny each, any may be null) of the stored state
 cudaError_t launch_fields(const Layout& L, int prec, const void* buf, double rho0, double* rho,
                           double* ux, double* uy, double* bx, double* by, cudaStream_t st);
+// stored state whose pull-gather reproduces the packed FP32 pre-collision
+// state F (periodic axes)
+cudaError_t launch_unstream(const Layout& L, int prec, void* buf, const float* F, cudaStream_t st);
 // one plane <-> unshifted FP64 array of nx*ny (population p = 0..18)
 cudaError_t launch_plane_out(const Layout& L, int prec, const void* buf, int p, double rho0,
                              double* out, cudaStream_t st);

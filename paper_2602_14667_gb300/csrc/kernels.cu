@@ -193,6 +193,25 @@ __global__ void plane_in_kernel(Layout L, void* buf, int p, double shift, const 
     }
 }
 
+// S_p(x) = F_p(x + c_p) (periodic): a stored state whose pull-gather gives
+// back the pre-collision state F (packed FP32 deviations) at every node.
+template <int PREC>
+__global__ void unstream_kernel(Layout L, void* buf, const float* F) {
+    using S = typename Prec<PREC>::S;
+    const long long n = (long long)L.nx * L.ny;
+    S* b = static_cast<S*>(buf);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / L.nx), x = (int)(k % L.nx);
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) {
+            const int xs = (x + pcx(p) + L.nx) % L.nx, ys = (y + pcy(p) + L.ny) % L.ny;
+            encode_d((double)F[(long long)p * n + (long long)ys * L.nx + xs],
+                     b[(long long)p * L.plane + (long long)y * L.pitch + x]);
+        }
+    }
+}
+
 static dim3 flat_grid(long long n) {
     long long b = (n + 255) / 256;
     if (b > 152 * 16) b = 152 * 16;
@@ -222,6 +241,11 @@ cudaError_t launch_fields(const Layout& L, int prec, const void* buf, double rho
                           double* ux, double* uy, double* bx, double* by, cudaStream_t st) {
     MHD_DISPATCH(prec, fields_kernel, flat_grid((long long)L.nx * L.ny), 256, st, L, buf, rho0, rho,
                  ux, uy, bx, by);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unstream(const Layout& L, int prec, void* buf, const float* F, cudaStream_t st) {
+    MHD_DISPATCH(prec, unstream_kernel, flat_grid((long long)L.nx * L.ny), 256, st, L, buf, F);
     return cudaGetLastError();
 }
 

@@ -152,8 +152,20 @@ __device__ __forceinline__ void hermite_eval(const Coeffs<C>& a, C (&out)[9]) {
 
 // Tasks 2-5 at one node, in place.  f holds deviations f_i - w_i rho0 of the
 // pre-collision populations, g the pre-collision g_{j,a} (index 2j + a).
+// With DA, da (xx, xy, yy) is added to the projected a1^(2) before the
+// recursion (the learned closure; mass and momentum are untouched).
+template <bool DA, typename C>
+__device__ __forceinline__ void collide_impl(C (&f)[9], C (&g)[10], const NodeParams<C>& p,
+                                             const C* da);
+
 template <typename C>
 __device__ __forceinline__ void collide(C (&f)[9], C (&g)[10], const NodeParams<C>& p) {
+    collide_impl<false, C>(f, g, p, nullptr);
+}
+
+template <bool DA, typename C>
+__device__ __forceinline__ void collide_impl(C (&f)[9], C (&g)[10], const NodeParams<C>& p,
+                                             const C* da) {
     const Moments<C> m = moments(f, g, p.rho0);
     const C ux = m.ux, uy = m.uy, bx = m.bx, by = m.by;
     // Maxwell stress M = |b|^2 I / 2 - b b (traceless in 2-D)
@@ -165,9 +177,14 @@ __device__ __forceinline__ void collide(C (&f)[9], C (&g)[10], const NodeParams<
     const C Sxy = (f[3] + f[7]) - (f[1] + f[5]);
     const C third = C(1.0 / 3.0);
     const C ruxx = m.mx * ux, ruyy = m.my * uy, ruxy = m.mx * uy;
-    const C a2xx = Sxx - third * m.drho - ruxx - Mxx;
-    const C a2yy = Syy - third * m.drho - ruyy + Mxx;
-    const C a2xy = Sxy - ruxy - Mxy;
+    C a2xx = Sxx - third * m.drho - ruxx - Mxx;
+    C a2yy = Syy - third * m.drho - ruyy + Mxx;
+    C a2xy = Sxy - ruxy - Mxy;
+    if constexpr (DA) {
+        a2xx += da[0];
+        a2xy += da[1];
+        a2yy += da[2];
+    }
     // recursion (task 3) on the supported components
     const C a3xxy = C(2) * ux * a2xy + uy * a2xx;
     const C a3xyy = C(2) * uy * a2xy + ux * a2yy;

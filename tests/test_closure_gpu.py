@@ -1,0 +1,241 @@
+"""GPU parity of the closure kernels against the FP64 closure oracle.
+
+Filter, features, targets, the pre-collision setter, the BF16 tensor-core MLP
+(prediction, gradients, training) and the closure step.  Where the GPU rounds
+to BF16 the oracle takes the same decisions (its bf16_like_gpu mode); the
+remaining differences are FP32 versus FP64 arithmetic, and BF16 rounding of
+the backward-pass intermediates, which the oracle keeps in FP64.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+W9 = np.array([4 / 9] + [1 / 36, 1 / 9] * 4)
+
+
+def _packed(f, g, rho0=1.0):
+    import torch
+    dev = np.concatenate([(f - W9[:, None, None] * rho0).reshape(9, -1), g.reshape(10, -1)])
+    return torch.from_numpy(dev.astype(np.float32)).cuda().contiguous()
+
+
+def _unpacked(t, nx, ny, rho0=1.0):
+    a = t.detach().cpu().numpy().astype(np.float64).reshape(19, ny, nx)
+    return a[:9] + W9[:, None, None] * rho0, a[9:].reshape(5, 2, ny, nx)
+
+
+def _state(orc, nx, ny, seed, steps=5, tau=(0.53, 0.56)):
+    import mhd_inputs
+    p = orc.Params(nx, ny, *tau)
+    f, g = orc.init(p, *mhd_inputs.random_spectrum(nx, ny, seed, 0.03, 0.03, kmax=4))
+    f, g = orc.run(p, f, g, steps)
+    return p, f, g
+
+
+def test_features_match_oracle(orc):
+    import torch
+
+    from oracle import closure as clo
+    from paper_2602_14667_gb300 import _abi
+    p, f, g = _state(orc, 40, 24, 1)
+    st = _packed(f, g)
+    f64, g64 = _unpacked(st, 40, 24)            # the FP32 values, in FP64
+    X = torch.empty((40 * 24, 24), dtype=torch.float32, device="cuda")
+    _abi.closure_features(st, 40, 24, 1.0, X)
+    got = X.cpu().numpy().astype(np.float64)
+    ref, _ = clo.features(p, f64, g64)
+    tol = 2e-5 * np.abs(ref).max(axis=0) + 1e-9
+    assert (np.abs(got - ref) <= tol).all(), np.abs(got - ref).max(axis=0)
+
+
+def test_targets_match_oracle(orc):
+    import torch
+
+    from oracle import closure as clo
+    from paper_2602_14667_gb300 import _abi
+    p, f, g = _state(orc, 32, 20, 2)
+    f1, g1 = clo.closure_step(p, f, g, None)
+    rng = np.random.default_rng(0)
+    f1 = f1 + rng.normal(0, 1e-6, f1.shape)     # a state the plain step does not reach
+    sT, sT1 = _packed(f, g), _packed(f1, g1)
+    fa, ga = _unpacked(sT, 32, 20)
+    fb, gb = _unpacked(sT1, 32, 20)
+    out = torch.empty((32 * 20, 3), dtype=torch.float32, device="cuda")
+    _abi.closure_targets(sT, sT1, 32, 20, 1.0, p.tau_f, out)
+    ref = clo.targets(p, fa, ga, fb, gb)
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.abs(ref).max() > 1e-7
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-6 * np.abs(ref).max() + 1e-12)
+
+
+def test_filter_of_a_fine_lattice(orc):
+    import torch
+
+    import mhd_inputs
+    from oracle import closure as clo
+    from paper_2602_14667_gb300 import Lattice, _abi
+    nx, ny, r = 64, 48, 4
+    p = orc.Params(nx, ny, 0.55, 0.6)
+    with Lattice(nx, ny, 0.55, 0.6, precision="fp32") as lat:
+        lat.set_fields(*mhd_inputs.random_spectrum(nx, ny, 3, 0.03, 0.03, kmax=5))
+        lat.advance(4)
+        Pf, Pg = lat.get_populations()          # post-collision state at t
+        lat.advance(1)
+        out = torch.empty((19, (nx // r) * (ny // r)), dtype=torch.float32, device="cuda")
+        _abi.closure_filter(lat, r, out)
+    fpre, gpre = orc.stream(p, Pf, Pg)          # pre-collision state at t + 1
+    fc, gc = clo.box_filter(fpre, gpre, r)
+    got_f, got_g = _unpacked(out, nx // r, ny // r)
+    np.testing.assert_allclose(got_f, fc, rtol=0, atol=2e-7)
+    np.testing.assert_allclose(got_g, gc, rtol=0, atol=2e-7)
+
+
+def test_sgs_targets_of_a_fine_lattice(orc):
+    import torch
+
+    import mhd_inputs
+    from oracle import closure as clo
+    from paper_2602_14667_gb300 import Lattice, _abi
+    nx, ny, r, tau_c = 64, 48, 4, 0.5125
+    p = orc.Params(nx, ny, 0.55, 0.6)
+    with Lattice(nx, ny, 0.55, 0.6, precision="fp32") as lat:
+        lat.set_fields(*mhd_inputs.random_spectrum(nx, ny, 5, 0.03, 0.03, kmax=8))
+        lat.advance(6)
+        Pf, Pg = lat.get_populations()
+        lat.advance(1)
+        out = torch.empty(((nx // r) * (ny // r), 3), dtype=torch.float32, device="cuda")
+        _abi.closure_sgs_targets(lat, r, tau_c, out)
+    fpre, gpre = orc.stream(p, Pf, Pg)
+    ref = clo.sgs_targets(p, fpre, gpre, r, tau_c)
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.abs(ref).max() > 1e-7
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-6 * np.abs(ref).max())
+
+
+def test_precollision_setter_collides_the_given_state(orc):
+    from paper_2602_14667_gb300 import Lattice, _abi
+    p, f, g = _state(orc, 48, 32, 4)
+    st = _packed(f, g)
+    f64, g64 = _unpacked(st, 48, 32)
+    with Lattice(48, 32, *(p.tau_f, p.tau_m), precision="fp32") as lat:
+        _abi.set_precollision_state(lat, st)
+        lat.advance(1)
+        fg, gg = lat.get_populations()
+    fo, go = orc.collide(p, f64, g64)
+    assert np.abs(fg - fo).max() < 2e-6 and np.abs(gg - go).max() < 2e-6
+
+
+def _random_net(clo, X, T, seed=0):
+    net = clo.MLP(seed=seed)
+    net.p["mean"] = X.mean(axis=0)
+    net.p["scale"] = 1.0 / np.maximum(X.std(axis=0), 1e-12)
+    net.p["out_scale"] = np.maximum(T.std(axis=0), 1e-12)
+    rng = np.random.default_rng(seed)
+    for b in ("b1", "b2", "b3"):
+        net.p[b] = rng.normal(0, 0.1, net.p[b].shape)
+    return net
+
+
+def _data(n, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(n, 24)) * rng.uniform(0.01, 2.0, 24) + rng.normal(size=24)
+    teacher_w = rng.normal(size=(24, 3))
+    T = np.tanh(X @ teacher_w * 0.3) * 1e-4
+    return X, T
+
+
+def test_mlp_predict_gradients_and_normalisation(orc):
+    import torch
+
+    from oracle import closure as clo
+    from paper_2602_14667_gb300 import _abi
+    X, T = _data(1000, 1)
+    net = _random_net(clo, X, T)
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    Td = torch.tensor(T, dtype=torch.float32, device="cuda")
+    X32, T32 = X.astype(np.float32).astype(np.float64), T.astype(np.float32).astype(np.float64)
+    with _abi.MLP(seed=0, max_batch=1024) as m:
+        m.fit_normalisation(Xd, Td)
+        prm = m.get_params()
+        np.testing.assert_allclose(prm[:24], X32.mean(axis=0), rtol=1e-5, atol=1e-6)
+        np.testing.assert_allclose(1 / prm[24:48], X32.std(axis=0), rtol=1e-4)
+        np.testing.assert_allclose(prm[48:51], T32.std(axis=0), rtol=1e-4)
+        m.set_params(net.flat())
+        ref_net = clo.MLP.from_flat(m.get_params())   # the FP32-rounded parameters
+        Y = torch.empty((1000, 3), dtype=torch.float32, device="cuda")
+        m.predict(Xd, Y)
+        ref, _ = ref_net.forward(X32, bf16_like_gpu=True)
+        np.testing.assert_allclose(Y.cpu().numpy(), ref, rtol=0, atol=2e-3 * np.abs(ref).max())
+        loss, grad = m.gradients(Xd, Td)
+    rloss, rgrads = ref_net.loss_and_grads(X32, T32, bf16_like_gpu=True)
+    assert abs(loss / rloss - 1) < 5e-3
+    off = 51
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        size = rgrads[name].size
+        g = grad[off:off + size].astype(np.float64)
+        r = rgrads[name].reshape(-1)
+        off += size
+        assert np.linalg.norm(g - r) <= 2e-2 * np.linalg.norm(r) + 1e-12, name
+    assert np.all(grad[:51] == 0)
+
+
+def test_training_reduces_the_loss():
+    import torch
+
+    from paper_2602_14667_gb300 import _abi
+    X, T = _data(20000, 2)
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    Td = torch.tensor(T, dtype=torch.float32, device="cuda")
+    with _abi.MLP(seed=1, max_batch=4096) as m:
+        m.fit_normalisation(Xd, Td)
+        loss0, _ = m.gradients(Xd[:4096], Td[:4096])
+        loss = m.train(Xd, Td, epochs=30, batch=1024, lr=2e-3, seed=5)
+    assert loss < 0.05 * loss0, (loss0, loss)
+
+
+def test_closure_step_matches_oracle(orc):
+    import torch
+
+    from oracle import closure as clo
+    from paper_2602_14667_gb300 import Lattice, _abi
+    nx, ny = 72, 40
+    p, f, g = _state(orc, nx, ny, 6, steps=6)
+    st = _packed(f, g)
+    f64, g64 = _unpacked(st, nx, ny)
+    Xo, _ = clo.features(p, f64, g64)
+    net = _random_net(clo, Xo, np.full((4, 3), 1.0), seed=3)
+    net.p["out_scale"][:] = 2e-5
+    with _abi.MLP(seed=0, max_batch=64) as m, Lattice(nx, ny, p.tau_f, p.tau_m, precision="fp32") as lat:
+        m.set_params(net.flat())
+        ref_net = clo.MLP.from_flat(m.get_params())
+        _abi.set_closure(lat, m)
+        _abi.set_precollision_state(lat, st)
+        lat.advance(1)
+        fg, gg = lat.get_populations()
+    da, _ = ref_net.forward(Xo, bf16_like_gpu=True)
+    assert np.abs(da).max() > 1e-6
+    fs, gs = orc.collide_da(p, f64, g64, da.reshape(ny, nx, 3))
+    fp, _ = orc.collide(p, f64, g64)
+    assert np.abs(fs - fp).max() > 1e-6                    # the correction is visible ...
+    assert np.abs(fg - fs).max() < 3e-6 and np.abs(gg - gs).max() < 2e-6   # ... and matched
+
+
+def test_closure_keeps_mass_and_momentum():
+    import mhd_inputs
+    from oracle import closure as clo
+    from paper_2602_14667_gb300 import Lattice, _abi
+    n = 64
+    net = clo.MLP(seed=4)
+    net.p["out_scale"][:] = 1e-5
+    with _abi.MLP(seed=0, max_batch=64) as m, Lattice(n, n, 0.52, 0.55, precision="fp32") as lat:
+        m.set_params(net.flat())
+        _abi.set_closure(lat, m)
+        lat.set_fields(*mhd_inputs.random_spectrum(n, n, 9, 0.03, 0.03))
+        t0 = lat.get_totals()
+        lat.advance(200)
+        t1 = lat.get_totals()
+        _abi.set_closure(lat, None)
+        lat.advance(10)
+    assert abs(t1["mass"] - t0["mass"]) < 1e-6 * n * n
+    assert abs(t1["mom_x"] - t0["mom_x"]) < 1e-6 * n * n and abs(t1["mom_y"] - t0["mom_y"]) < 1e-6 * n * n

@@ -129,3 +129,29 @@ def test_closure_keeps_mass_and_momentum_and_zero_net_is_plain(orc, clo):
     fp, gp = clo.closure_step(p, f, g, None)
     np.testing.assert_array_equal(fz, fp)
     assert np.abs(f1 - fp).max() > 1e-8
+
+
+def test_sgs_target_vanishes_for_block_constant_fields(orc, clo):
+    n, r = 16, 4
+    p = orc.Params(n, n, 0.6, 0.6)
+    rng = np.random.default_rng(8)
+    blocks = [np.kron(rng.uniform(-0.05, 0.05, (n // r, n // r)), np.ones((r, r))) for _ in range(4)]
+    f, g = orc.init(p, *blocks, rho=np.kron(rng.uniform(0.95, 1.05, (n // r, n // r)), np.ones((r, r))))
+    assert np.abs(clo.sgs_targets(p, f, g, r, 0.51)).max() < 1e-15
+
+
+def test_sgs_target_trace_is_the_weighted_velocity_variance(orc, clo):
+    """tr(tau_sgs) = <rho |u|^2> - <rho u>^2 / <rho> >= 0 (the Maxwell part
+    is traceless in 2-D)."""
+    n, r, tau_c = 16, 4, 0.52
+    p = orc.Params(n, n, 0.6, 0.6)
+    rng = np.random.default_rng(9)
+    ux, uy, bx, by = (rng.uniform(-0.05, 0.05, (n, n)) for _ in range(4))
+    rho = rng.uniform(0.95, 1.05, (n, n))
+    f, g = orc.init(p, ux, uy, bx, by, rho=rho)
+    t = clo.sgs_targets(p, f, g, r, tau_c) * (1 - 1 / tau_c)
+    def avg(a):
+        return a.reshape(n // r, r, n // r, r).mean(axis=(1, 3)).reshape(-1)
+    var = avg(rho * (ux ** 2 + uy ** 2)) - (avg(rho * ux) ** 2 + avg(rho * uy) ** 2) / avg(rho)
+    np.testing.assert_allclose(t[:, 0] + t[:, 2], var, rtol=1e-9, atol=1e-15)
+    assert (var > 0).all()
