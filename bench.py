@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="ot4096", choices=["ot4096", "ensemble"],
+    ap.add_argument("--workload", default="ot4096", choices=["ot4096", "ensemble", "closure", "closure_step"],
                     help="ot4096: the headline single lattice; ensemble: 512 random-spectrum "
                          "lattices in one persistent launch per step")
     ap.add_argument("--retune", action="store_true",
@@ -447,12 +447,98 @@ def run_ensemble(args):
         dist.destroy_process_group()
 
 
+def run_closure(args):
+    """The learned-closure workload: 2048^2 fine runs (random-spectrum fields,
+    rms 0.03) filtered 4x onto 512^2; MLP trained on the GPU on ~2 M samples
+    from two seeds, amplitude calibrated on one of them, coarse closure and
+    plain runs judged on a held-out seed against the filtered fine run.  The
+    fine relaxation time is 0.52 (coarse 0.505): the workload's nu = eta =
+    5e-5 lies beyond the scheme's stability limit near tau = 1/2."""
+    import torch
+
+    from paper_2602_14667_gb300 import closure_study as cs
+    torch.cuda.set_device(0)
+    cfg = cs.StudyConfig(n_fine=2048, factor=4, tau_fine=0.52, rms=0.03, sample_start=2000,
+                         sample_stride=1500, samples_per_seed=4,
+                         eval_coarse_steps=(500, 1000, 1500, 2000), epochs=20, batch=8192)
+    t0 = time.perf_counter()
+    res = cs.run(cfg)
+    wall = time.perf_counter() - t0
+    last = cfg.eval_coarse_steps[-1]
+    sp, jp = res["plain"][last]
+    sc, jc = res.get("closure", res["plain"])[last]
+    cost_p = res["plain"]["s_per_step"]
+    cost_c = res.get("closure", res["plain"])["s_per_step"]
+    out = {"metric": "coarse+closure vs plain error (energy spectrum, current density) against the "
+                     "filtered 2048^2 run",
+           "value": sc, "unit": "relative spectrum error (closure, last checkpoint)",
+           "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "f32 (bf16 MLP)",
+           "config": {"workload": "closure_2048_to_512", "tau_fine": cfg.tau_fine,
+                      "tau_coarse": cs.coarse_tau(cfg.tau_fine, cfg.factor), "rms": cfg.rms,
+                      "samples": res["samples"], "train_loss": res["train_loss"],
+                      "amplitude": res["amplitude"], "checkpoints": list(cfg.eval_coarse_steps),
+                      "calibration_scores": {str(k): v for k, v in res["calibration_scores"].items()}},
+           "plain": {str(k): res["plain"][k] for k in cfg.eval_coarse_steps},
+           "closure": {str(k): res["closure"][k] for k in cfg.eval_coarse_steps} if "closure" in res else None,
+           "spectrum_error": {"plain": sp, "closure": sc}, "current_error": {"plain": jp, "closure": jc},
+           "s_per_coarse_step": {"plain": cost_p, "closure": cost_c},
+           "equal_gpu_time_note": "a plain run at the next finer grid the fine run can be filtered to "
+                                  "(1024^2) costs 8x the plain 512^2 run",
+           "wall_s": wall}
+    print(json.dumps(out), flush=True)
+
+
+def run_closure_step(args):
+    """Cost of the closure step alone: a 512^2 FP32 lattice (random-spectrum
+    fields, tau 0.505) advanced with the plain step and with the closure step
+    (an untrained network: the MLP cost does not depend on the weights),
+    CUDA events around `steps` graph-launched steps each."""
+    import torch
+
+    import mhd_inputs
+    from paper_2602_14667_gb300 import Lattice, _abi
+    torch.cuda.set_device(0)
+    n = args.n if args.n != 4096 else 512
+    stream = torch.cuda.Stream()
+    fields = mhd_inputs.random_spectrum(n, n, 7, 0.03, 0.03)
+    out = {}
+    mlp = _abi.MLP(seed=3, max_batch=64)
+    prm = mlp.get_params()
+    prm[48:51] = 1e-7                       # small output scale: a stable, non-trivial correction
+    mlp.set_params(prm)
+    for name in ("plain", "closure"):
+        with Lattice(n, n, 0.505, 0.505, precision="fp32", stream=stream.cuda_stream) as lat:
+            if name == "closure":
+                _abi.set_closure(lat, mlp)
+            lat.set_fields(*fields)
+            lat.advance(args.warmup)
+            stream.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.advance(args.steps)
+            e1.record(stream)
+            e1.synchronize()
+            out[name] = e0.elapsed_time(e1) / args.steps
+    mlp.close()
+    res = {"metric": "closure step cost (512^2 coarse lattice)", "value": out["closure"] / out["plain"],
+           "unit": "closure / plain time per step", "higher_is_better": False, "n_gpus": 1,
+           "ms_per_step": out, "mlups": {k: n * n / (v * 1e-3) / 1e6 for k, v in out.items()},
+           "config": {"workload": f"closure_step_{n}x{n}_fp32", "tau": 0.505}, "data": "synthetic",
+           "steps": args.steps, "warmup": args.warmup}
+    print(json.dumps(res), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "ensemble":
         run_ensemble(args)
+    elif args.workload == "closure":
+        run_closure(args)
+    elif args.workload == "closure_step":
+        run_closure_step(args)
     else:
         run_gb300(args)
 

@@ -14,7 +14,7 @@ factor * tau_coarse / tau_fine times smaller than what the coarse lattice
 develops, so their values would not transfer.  The coarse runs start, like
 the fine run, from the t = 0 fields (block-averaged, equilibrium populations)
 and are judged against the filtered fine run at the same time by the
-relative error of the energy spectrum (kinetic + magnetic, shells
+rms log10 deviation of the energy spectrum (kinetic + magnetic, shells
 1 <= k <= n_coarse / 4) and the relative L2 error of the current density.
 The plain coarse RR run is over-dissipative at high k against the filtered
 fine run, while the filtered sub-grid stress is mostly dissipative; the
@@ -148,10 +148,14 @@ def current_density(bx, by):
 
 
 def errors(model, ref, kmax):
-    """(spectrum error, current-density error) of model fields against ref."""
+    """(spectrum error, current-density error) of model fields against ref.
+    The spectrum error is the rms over shells 1..kmax of log10(E / E_ref),
+    over the shells holding at least 1e-12 of the reference's largest shell
+    energy (the deviation on a log-log spectrum plot)."""
     em = energy_spectrum(*model[1:], kmax)
     er = energy_spectrum(*ref[1:], kmax)
-    spec = float(np.sqrt(np.mean(((em - er) / er) ** 2)))
+    keep = er > 1e-12 * er.max()
+    spec = float(np.sqrt(np.mean(np.log10(np.maximum(em[keep], 1e-300) / er[keep]) ** 2)))
     jm, jr = current_density(model[3], model[4]), current_density(ref[3], ref[4])
     return spec, float(np.linalg.norm(jm - jr) / np.linalg.norm(jr))
 
@@ -207,8 +211,10 @@ def coarse_run(cfg: StudyConfig, fields0, refs, mlp=None, timing=False):
     return res
 
 
-def _spectrum_score(res, cfg):
-    return sum(res[k][0] for k in cfg.eval_coarse_steps)
+def _score(res, cfg):
+    """Calibration objective: spectrum plus current-density errors, summed
+    over the checkpoints."""
+    return sum(res[k][0] + res[k][1] for k in cfg.eval_coarse_steps)
 
 
 CALIBRATION_GRID = (-2.0, -1.5, -1.0, -0.75, -0.5, -0.25, 0.0, 0.25, 0.5, 1.0)
@@ -217,8 +223,8 @@ CALIBRATION_GRID = (-2.0, -1.5, -1.0, -0.75, -0.5, -0.25, 0.0, 0.25, 0.5, 1.0)
 def calibrate(cfg: StudyConfig, mlp, seed=None):
     """A posteriori amplitude of the learned stress: scale out_scale by each c
     of CALIBRATION_GRID, run the coarse closure on a TRAINING seed and keep
-    the c with the smallest summed spectrum error (c = 0 is the plain
-    scheme).  Returns (c, scores)."""
+    the c with the smallest summed spectrum + current errors (c = 0 is the
+    plain scheme).  Returns (c, scores)."""
     seed = cfg.train_seeds[0] if seed is None else seed
     refs, fields0 = reference(cfg, seed)
     base = mlp.get_params()
@@ -227,7 +233,7 @@ def calibrate(cfg: StudyConfig, mlp, seed=None):
         p = base.copy()
         p[48:51] *= c
         mlp.set_params(p)
-        scores[c] = _spectrum_score(coarse_run(cfg, fields0, refs, None if c == 0.0 else mlp), cfg)
+        scores[c] = _score(coarse_run(cfg, fields0, refs, None if c == 0.0 else mlp), cfg)
     best = min(scores, key=scores.get)
     p = base.copy()
     p[48:51] *= best

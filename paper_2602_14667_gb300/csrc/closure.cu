@@ -528,14 +528,17 @@ __global__ void stats_finish(const double* __restrict__ P, int nblocks, long lon
 // ---- closure step (inference fused beside the collision) ------------------------
 constexpr int kCTX = 32, kCTY = 8, kCHX = kCTX + 2, kCHY = kCTY + 2;
 constexpr int kFeatStride = 40;  // bf16 per feature row (conflict-free fragment loads)
+constexpr int kW1Stride = 40;    // padded rows of the shared weights: row strides of 20 and
+constexpr int kW2Stride = 72;    // 36 words put the 32 lanes of a B-fragment load in 32 banks
 
 struct ClosureShared {
-    bf16 Wt1[kHid * kInPad];
-    bf16 Wt2[kHid * kHid];
-    bf16 Wt3[kOutPad * kHid];
+    bf16 Wt1[kHid * kW1Stride];
+    bf16 Wt2[kHid * kW2Stride];
+    bf16 Wt3[kOutPad * kW2Stride];
     float b1[kHid], b2[kHid], b3[kOutPad];
     float mean[kIn], scale[kIn], out_scale[kOut];
     float mom[4][kCHY][kCHX];
+    float pop[kPlanes][kCTX * kCTY];  // the tile's pre-collision populations, parked during the MLP
     bf16 feat[kCTX * kCTY * kFeatStride];
     float da[kCTX * kCTY][kOut];
 };
@@ -557,8 +560,8 @@ __device__ __forceinline__ void mlp_rows16(ClosureShared& sh, int m0, int lane) 
         float d[4] = {sh.b1[8 * j + 2 * t], sh.b1[8 * j + 2 * t + 1], sh.b1[8 * j + 2 * t], sh.b1[8 * j + 2 * t + 1]};
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            const uint32_t b[2] = {ld2(sh.Wt1 + (8 * j + g) * kInPad + 16 * c + 2 * t),
-                                   ld2(sh.Wt1 + (8 * j + g) * kInPad + 16 * c + 2 * t + 8)};
+            const uint32_t b[2] = {ld2(sh.Wt1 + (8 * j + g) * kW1Stride + 16 * c + 2 * t),
+                                   ld2(sh.Wt1 + (8 * j + g) * kW1Stride + 16 * c + 2 * t + 8)};
             mma16816(d, a1[c], b);
         }
         // accumulator of n-tile j becomes half of k-chunk j/2 of the next A
@@ -572,8 +575,8 @@ __device__ __forceinline__ void mlp_rows16(ClosureShared& sh, int m0, int lane) 
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const uint32_t a[4] = {h[c][0], h[c][1], h[c][2], h[c][3]};
-            const uint32_t b[2] = {ld2(sh.Wt2 + (8 * j + g) * kHid + 16 * c + 2 * t),
-                                   ld2(sh.Wt2 + (8 * j + g) * kHid + 16 * c + 2 * t + 8)};
+            const uint32_t b[2] = {ld2(sh.Wt2 + (8 * j + g) * kW2Stride + 16 * c + 2 * t),
+                                   ld2(sh.Wt2 + (8 * j + g) * kW2Stride + 16 * c + 2 * t + 8)};
             mma16816(d, a, b);
         }
         h2[j >> 1][(j & 1) * 2 + 0] = pack2(fmaxf(d[0], 0.f), fmaxf(d[1], 0.f));
@@ -583,7 +586,8 @@ __device__ __forceinline__ void mlp_rows16(ClosureShared& sh, int m0, int lane) 
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         const uint32_t a[4] = {h2[c][0], h2[c][1], h2[c][2], h2[c][3]};
-        const uint32_t b[2] = {ld2(sh.Wt3 + g * kHid + 16 * c + 2 * t), ld2(sh.Wt3 + g * kHid + 16 * c + 2 * t + 8)};
+        const uint32_t b[2] = {ld2(sh.Wt3 + g * kW2Stride + 16 * c + 2 * t),
+                               ld2(sh.Wt3 + g * kW2Stride + 16 * c + 2 * t + 8)};
         mma16816(d, a, b);
     }
     // d0: (row g, col 2t), d1: (g, 2t+1), d2: (g+8, 2t), d3: (g+8, 2t+1)
@@ -597,50 +601,54 @@ __device__ __forceinline__ void mlp_rows16(ClosureShared& sh, int m0, int lane) 
     }
 }
 
-__global__ void __launch_bounds__(256) step_closure(const StepArgs<float> a, const ClosureParamsDev cp,
-                                                    int ntx, int ntiles) {
+__global__ void __launch_bounds__(256, 3) step_closure(const StepArgs<float> a, const ClosureParamsDev cp,
+                                                       int ntx, int ntiles) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ClosureShared& sh = *reinterpret_cast<ClosureShared*>(smem_raw);
     const int tid = threadIdx.y * kCTX + threadIdx.x, lane = threadIdx.x, ly = threadIdx.y;
-    for (int i = tid; i < kHid * kInPad; i += 256) sh.Wt1[i] = cp.Wt1[i];
-    for (int i = tid; i < kHid * kHid; i += 256) sh.Wt2[i] = cp.Wt2[i];
-    for (int i = tid; i < kOutPad * kHid; i += 256) sh.Wt3[i] = cp.Wt3[i];
+    for (int i = tid; i < kHid * kInPad; i += 256) sh.Wt1[(i / kInPad) * kW1Stride + i % kInPad] = cp.Wt1[i];
+    for (int i = tid; i < kHid * kHid; i += 256) sh.Wt2[(i / kHid) * kW2Stride + i % kHid] = cp.Wt2[i];
+    for (int i = tid; i < kOutPad * kHid; i += 256) sh.Wt3[(i / kHid) * kW2Stride + i % kHid] = cp.Wt3[i];
     for (int i = tid; i < kHid; i += 256) { sh.b1[i] = cp.b1[i]; sh.b2[i] = cp.b2[i]; }
     if (tid < kOutPad) sh.b3[tid] = cp.b3[tid];
     if (tid < kIn) { sh.mean[tid] = cp.mean[tid]; sh.scale[tid] = cp.scale[tid]; }
     if (tid < kOut) sh.out_scale[tid] = cp.out_scale[tid];
     const float* src = static_cast<const float*>(a.src);
     float* dst = static_cast<float*>(a.dst);
+    constexpr int kHalo = kCHX * kCHY - kCTX * kCTY;  // 84 ring positions
     for (int tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
         __syncthreads();  // shared parameters loaded / previous tile done
         const int x0 = (tl % ntx) * kCTX, y0 = (tl / ntx) * kCTY;
-        // halo and tile moments (pre-collision, gathered from the last post-collision state)
-        for (int r = tid; r < kCHX * kCHY; r += 256) {
-            const int hx = r % kCHX, hy = r / kCHX;
+        const int x = x0 + lane, y = y0 + ly;
+        const bool inside = x < a.nx && y < a.ny;
+        // own node and (threads tid < 84) one ring node, loads issued together
+        float f[9], g[10], hf[9], hg[10];
+        // a thread past the lattice edge gathers its periodic image: it is the
+        // neighbour of the last in-range nodes
+        gather_node<float, float>(src, x % a.nx, y % a.ny, a.nx, a.ny, a.pitch, a.plane, 0, 0, f, g);
+        int hx = 0, hy = 0;
+        if (tid < kHalo) {
+            // ring order: top row (34), bottom row (34), left column (8), right column (8)
+            if (tid < kCHX) { hx = tid; hy = 0; }
+            else if (tid < 2 * kCHX) { hx = tid - kCHX; hy = kCHY - 1; }
+            else if (tid < 2 * kCHX + kCTY) { hx = 0; hy = 1 + tid - 2 * kCHX; }
+            else { hx = kCHX - 1; hy = 1 + tid - 2 * kCHX - kCTY; }
             const int gx = ((x0 - 1 + hx) % a.nx + a.nx) % a.nx, gy = ((y0 - 1 + hy) % a.ny + a.ny) % a.ny;
-            float f[9], g[10];
-            gather_node<float, float>(src, gx, gy, a.nx, a.ny, a.pitch, a.plane, 0, 0, f, g);
-            const Moments<float> m = moments(f, g, a.np.rho0);
+            gather_node<float, float>(src, gx, gy, a.nx, a.ny, a.pitch, a.plane, 0, 0, hf, hg);
+            const Moments<float> m = moments(hf, hg, a.np.rho0);
             sh.mom[0][hy][hx] = m.ux; sh.mom[1][hy][hx] = m.uy;
             sh.mom[2][hy][hx] = m.bx; sh.mom[3][hy][hx] = m.by;
         }
-        const int x = x0 + lane, y = y0 + ly;
-        const bool inside = x < a.nx && y < a.ny;
-        float f[9], g[10];
-        if (inside) {
-            gather_node<float, float>(src, x, y, a.nx, a.ny, a.pitch, a.plane, 0, 0, f, g);
-        } else {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) f[i] = 0.f;
-#pragma unroll
-            for (int q = 0; q < 10; ++q) g[q] = 0.f;
-        }
-        __syncthreads();
         float feat[kIn];
-        if (inside) {
-            point_features(f, g, a.np.rho0, feat);
-            stencil_features<kCHX, kCHY>(sh.mom, lane, ly, feat + 8);
-        }
+        point_features(f, g, a.np.rho0, feat);
+        sh.mom[0][ly + 1][lane + 1] = feat[1]; sh.mom[1][ly + 1][lane + 1] = feat[2];
+        sh.mom[2][ly + 1][lane + 1] = feat[3]; sh.mom[3][ly + 1][lane + 1] = feat[4];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) sh.pop[i][tid] = f[i];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) sh.pop[9 + q][tid] = g[q];
+        __syncthreads();
+        stencil_features<kCHX, kCHY>(sh.mom, lane, ly, feat + 8);
         bf16* row = sh.feat + tid * kFeatStride;
 #pragma unroll
         for (int c = 0; c < kInPad; c += 2) {
@@ -654,6 +662,10 @@ __global__ void __launch_bounds__(256) step_closure(const StepArgs<float> a, con
         mlp_rows16(sh, 32 * ly + 16, lane);
         __syncwarp();
         if (inside) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = sh.pop[i][tid];
+#pragma unroll
+            for (int q = 0; q < 10; ++q) g[q] = sh.pop[9 + q][tid];
             const float da[3] = {sh.da[tid][0], sh.da[tid][1], sh.da[tid][2]};
             collide_impl<true, float>(f, g, a.np, da);
             const long long o = (long long)y * a.pitch + x;
