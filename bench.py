@@ -452,13 +452,14 @@ def run_closure(args):
     rms 0.03) filtered 4x onto 512^2; MLP trained on the GPU on ~2 M samples
     from two seeds, amplitude calibrated on one of them, coarse closure and
     plain runs judged on a held-out seed against the filtered fine run.  The
-    fine relaxation time is 0.52 (coarse 0.505): the workload's nu = eta =
-    5e-5 lies beyond the scheme's stability limit near tau = 1/2."""
+    fine relaxation time is 0.54 (coarse 0.51): the workload's nu = eta =
+    5e-5 lies beyond the scheme's stability limit near tau = 1/2, and a
+    coarse 0.505 already lets some seeds go non-finite."""
     import torch
 
     from paper_2602_14667_gb300 import closure_study as cs
     torch.cuda.set_device(0)
-    cfg = cs.StudyConfig(n_fine=2048, factor=4, tau_fine=0.52, rms=0.03, sample_start=2000,
+    cfg = cs.StudyConfig(n_fine=2048, factor=4, tau_fine=0.54, rms=0.03, sample_start=2000,
                          sample_stride=1500, samples_per_seed=4,
                          eval_coarse_steps=(500, 1000, 1500, 2000), epochs=20, batch=8192)
     t0 = time.perf_counter()

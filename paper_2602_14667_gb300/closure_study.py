@@ -213,11 +213,12 @@ def coarse_run(cfg: StudyConfig, fields0, refs, mlp=None, timing=False):
 
 def _score(res, cfg):
     """Calibration objective: spectrum plus current-density errors, summed
-    over the checkpoints."""
-    return sum(res[k][0] + res[k][1] for k in cfg.eval_coarse_steps)
+    over the checkpoints (+inf for a run that went non-finite)."""
+    s = sum(res[k][0] + res[k][1] for k in cfg.eval_coarse_steps)
+    return s if math.isfinite(s) else math.inf
 
 
-CALIBRATION_GRID = (-2.0, -1.5, -1.0, -0.75, -0.5, -0.25, 0.0, 0.25, 0.5, 1.0)
+CALIBRATION_GRID = (-4.0, -3.0, -2.0, -1.5, -1.0, -0.5, 0.0, 0.5, 1.0)
 
 
 def calibrate(cfg: StudyConfig, mlp, seed=None):
