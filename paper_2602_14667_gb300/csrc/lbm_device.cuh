@@ -66,6 +66,55 @@ __device__ __forceinline__ void encode(double v, double& s) { s = v; }
 __device__ __forceinline__ void encode(float v, float& s) { s = v; }
 __device__ __forceinline__ void encode(float v, __half& s) { s = __float2half_rn(v * kHalfScale); }
 
+// Storage <-> compute values of V consecutive elements inside the fused
+// step.  FP16S values stay in storage units there (2^12 times the value; the
+// step's collision runs in those units), converted two at a time.
+template <typename S, int V> struct StepCodec {
+    template <typename C>
+    __device__ __forceinline__ static void to_compute(const S (&r)[V], C (&c)[V]) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) c[k] = decode(r[k]);
+    }
+    template <typename C>
+    __device__ __forceinline__ static C one(S r) { return decode(r); }
+    template <typename C>
+    __device__ __forceinline__ static void to_storage(const C (&c)[V], S (&r)[V]) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) encode(c[k], r[k]);
+    }
+};
+template <int V> struct StepCodec<__half, V> {
+    __device__ __forceinline__ static void to_compute(const __half (&r)[V], float (&c)[V]) {
+        if constexpr (V % 2 == 0) {
+#pragma unroll
+            for (int k = 0; k < V; k += 2) {
+                __half2 h;
+                memcpy(&h, &r[k], sizeof(h));
+                const float2 t = __half22float2(h);
+                c[k] = t.x;
+                c[k + 1] = t.y;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; ++k) c[k] = __half2float(r[k]);
+        }
+    }
+    template <typename C>
+    __device__ __forceinline__ static float one(__half r) { return __half2float(r); }
+    __device__ __forceinline__ static void to_storage(const float (&c)[V], __half (&r)[V]) {
+        if constexpr (V % 2 == 0) {
+#pragma unroll
+            for (int k = 0; k < V; k += 2) {
+                const __half2 h = __floats2half2_rn(c[k], c[k + 1]);
+                memcpy(&r[k], &h, sizeof(h));
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; ++k) r[k] = __float2half_rn(c[k]);
+        }
+    }
+};
+
 template <int BYTES> struct RawT;
 template <> struct RawT<2> { using T = unsigned short; };
 template <> struct RawT<4> { using T = unsigned int; };
@@ -100,21 +149,27 @@ template <typename C> struct Moments {
     C drho, mx, my, rho, ux, uy, bx, by;
 };
 
+// The linear sums drho, mx, my, bx, by of the populations as given.
 template <typename C>
-__device__ __forceinline__ Moments<C> moments(const C (&f)[9], const C (&g)[10], C rho0) {
-    Moments<C> m;
+__device__ __forceinline__ void moment_sums(const C (&f)[9], const C (&g)[10], Moments<C>& m) {
     // cx = -1: 1,2,3; cx = +1: 5,6,7; cy = +1: 1,7,8; cy = -1: 3,4,5
     C left = f[1] + f[2] + f[3], right = f[5] + f[6] + f[7];
     C up = f[1] + f[7] + f[8], down = f[3] + f[4] + f[5];
     m.drho = f[0] + f[4] + f[8] + left + right;
     m.mx = right - left;
     m.my = up - down;
+    m.bx = g[0] + g[2] + g[4] + g[6] + g[8];
+    m.by = g[1] + g[3] + g[5] + g[7] + g[9];
+}
+
+template <typename C>
+__device__ __forceinline__ Moments<C> moments(const C (&f)[9], const C (&g)[10], C rho0) {
+    Moments<C> m;
+    moment_sums(f, g, m);
     m.rho = rho0 + m.drho;
     C inv = C(1) / m.rho;
     m.ux = m.mx * inv;
     m.uy = m.my * inv;
-    m.bx = g[0] + g[2] + g[4] + g[6] + g[8];
-    m.by = g[1] + g[3] + g[5] + g[7] + g[9];
     return m;
 }
 
@@ -154,7 +209,13 @@ __device__ __forceinline__ void hermite_eval(const Coeffs<C>& a, C (&out)[9]) {
 // pre-collision populations, g the pre-collision g_{j,a} (index 2j + a).
 // With DA, da (xx, xy, yy) is added to the projected a1^(2) before the
 // recursion (the learned closure; mass and momentum are untouched).
-template <bool DA, typename C>
+// SCALED: f and g (in and out) are 2^12 times the deviations (the FP16S
+// storage units).  Every quantity linear in the populations (the moment
+// sums, a1^(2) and its recursion, the Hermite coefficients, g) is then
+// carried in those units and only u and the b entering the Maxwell stress
+// are brought back; scaling by a power of two commutes with rounding, so the
+// result is the unscaled one times 2^12, without a multiply per population.
+template <bool DA, typename C, bool SCALED = false>
 __device__ __forceinline__ void collide_impl(C (&f)[9], C (&g)[10], const NodeParams<C>& p,
                                              const C* da);
 
@@ -163,14 +224,29 @@ __device__ __forceinline__ void collide(C (&f)[9], C (&g)[10], const NodeParams<
     collide_impl<false, C>(f, g, p, nullptr);
 }
 
-template <bool DA, typename C>
+template <bool DA, typename C, bool SCALED>
 __device__ __forceinline__ void collide_impl(C (&f)[9], C (&g)[10], const NodeParams<C>& p,
                                              const C* da) {
-    const Moments<C> m = moments(f, g, p.rho0);
-    const C ux = m.ux, uy = m.uy, bx = m.bx, by = m.by;
-    // Maxwell stress M = |b|^2 I / 2 - b b (traceless in 2-D)
-    const C Mxx = C(0.5) * (by * by - bx * bx);
-    const C Mxy = -bx * by;
+    Moments<C> m;  // sums in the units of f, g; rho and u physical
+    moment_sums(f, g, m);
+    C bx = m.bx, by = m.by;  // physical b (Maxwell stress only)
+    if constexpr (SCALED) {
+        m.rho = p.rho0 + m.drho * C(kHalfInvScale);
+        const C inv = C(1) / m.rho;
+        m.ux = (m.mx * C(kHalfInvScale)) * inv;
+        m.uy = (m.my * C(kHalfInvScale)) * inv;
+        bx = m.bx * C(kHalfInvScale);
+        by = m.by * C(kHalfInvScale);
+    } else {
+        m.rho = p.rho0 + m.drho;
+        const C inv = C(1) / m.rho;
+        m.ux = m.mx * inv;
+        m.uy = m.my * inv;
+    }
+    const C ux = m.ux, uy = m.uy;
+    // Maxwell stress M = |b|^2 I / 2 - b b (traceless in 2-D), in the units of f
+    const C Mxx = C(0.5) * (by * m.by - bx * m.bx);
+    const C Mxy = -bx * m.by;
     // task 3: projection a1^(2) = sum H2 (f - f_eq) = sum cc df - cs^2 drho I - rho uu - M
     const C Sxx = f[1] + f[2] + f[3] + f[5] + f[6] + f[7];
     const C Syy = f[1] + f[3] + f[4] + f[5] + f[7] + f[8];
@@ -181,9 +257,10 @@ __device__ __forceinline__ void collide_impl(C (&f)[9], C (&g)[10], const NodePa
     C a2yy = Syy - third * m.drho - ruyy + Mxx;
     C a2xy = Sxy - ruxy - Mxy;
     if constexpr (DA) {
-        a2xx += da[0];
-        a2xy += da[1];
-        a2yy += da[2];
+        const C u = SCALED ? C(kHalfScale) : C(1);
+        a2xx += u * da[0];
+        a2xy += u * da[1];
+        a2yy += u * da[2];
     }
     // recursion (task 3) on the supported components
     const C a3xxy = C(2) * ux * a2xy + uy * a2xx;
@@ -231,22 +308,24 @@ __device__ __forceinline__ void collide_impl(C (&f)[9], C (&g)[10], const NodePa
     f[0] = m.drho - (((f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8])));
     // magnetic BGK (Eq. collide_g): g* = omega_m g_eq + (1 - omega_m) g,
     // g_eq_{j,a} = psi_j [b_a + 3 e_{j,c} (u_c b_a - u_a b_c)], E = ux by - uy bx
-    const C E3 = C(3) * (ux * by - uy * bx);
+    // (linear in b: evaluated in the units of g)
+    const C Bx = m.bx, By = m.by;
+    const C E3 = C(3) * (ux * By - uy * Bx);
     const C om = p.omega_m, omm1 = C(1) - p.omega_m;
     const C q1 = C(1.0 / 6.0);
-    const C gbx = q1 * bx, gby = q1 * by;
+    const C gbx = q1 * Bx, gby = q1 * By;
     g[2] = om * gbx + omm1 * g[2];               // j=1 (-1,0): x
-    g[3] = om * (q1 * (by - E3)) + omm1 * g[3];  // j=1: y
-    g[4] = om * (q1 * (bx + E3)) + omm1 * g[4];  // j=2 (0,-1): x
+    g[3] = om * (q1 * (By - E3)) + omm1 * g[3];  // j=1: y
+    g[4] = om * (q1 * (Bx + E3)) + omm1 * g[4];  // j=2 (0,-1): x
     g[5] = om * gby + omm1 * g[5];               // j=2: y
     g[6] = om * gbx + omm1 * g[6];               // j=3 (+1,0): x
-    g[7] = om * (q1 * (by + E3)) + omm1 * g[7];  // j=3: y
-    g[8] = om * (q1 * (bx - E3)) + omm1 * g[8];  // j=4 (0,+1): x
+    g[7] = om * (q1 * (By + E3)) + omm1 * g[7];  // j=3: y
+    g[8] = om * (q1 * (Bx - E3)) + omm1 * g[8];  // j=4 (0,+1): x
     g[9] = om * gby + omm1 * g[9];               // j=4: y
     // rest population by difference: sum_j g*_j = b exactly (psi_0 + 4 psi_1
     // = 1 + 6e-8 in FP32 would otherwise grow b by ~1e-7 per step)
-    g[0] = bx - ((g[2] + g[4]) + (g[6] + g[8]));
-    g[1] = by - ((g[3] + g[5]) + (g[7] + g[9]));
+    g[0] = Bx - ((g[2] + g[4]) + (g[6] + g[8]));
+    g[1] = By - ((g[3] + g[5]) + (g[7] + g[9]));
 }
 
 // Equilibrium deviations for given fields (initial state; a1 = 0).

@@ -71,27 +71,29 @@ __device__ __forceinline__ void step_row(const typename Prec<PREC>::S* __restric
         if (cx > 0 && !bounce && lane == 0 && active) edge[p] = row[xl];
         if (cx < 0 && !bounce && !right_by_shfl && active) edge[p] = row[xr];
     }
-    // Phase 2: decode and apply the +-1 x shift of the moving populations.
+    // Phase 2: decode and apply the +-1 x shift of the moving populations
+    // (FP16S values stay in storage units: the collision below runs in them).
+    constexpr bool kScaled = PREC == 2;
+    using Codec = StepCodec<S, V>;
     C v[kPlanes][V];
 #pragma unroll
     for (int p = 0; p < kPlanes; ++p) {
         const int cx = pcx(p), cy = pcy(p);
         const bool bounce = WALLY && (cy > 0 ? bm : (cy < 0 ? bp : false));
         C c[V];
-#pragma unroll
-        for (int k = 0; k < V; ++k) c[k] = decode(r[p][k]);
+        Codec::to_compute(r[p], c);
         if (cx == 0 || bounce) {
 #pragma unroll
             for (int k = 0; k < V; ++k) v[p][k] = c[k];
         } else if (cx > 0) {  // source x - 1
             C left = __shfl_up_sync(kFull, c[V - 1], 1);
-            if (lane == 0) left = decode(edge[p]);
+            if (lane == 0) left = Codec::template one<C>(edge[p]);
             v[p][0] = left;
 #pragma unroll
             for (int k = 1; k < V; ++k) v[p][k] = c[k - 1];
         } else {  // source x + 1
             C right = __shfl_down_sync(kFull, c[0], 1);
-            if (!right_by_shfl) right = decode(edge[p]);
+            if (!right_by_shfl) right = Codec::template one<C>(edge[p]);
 #pragma unroll
             for (int k = 0; k < V - 1; ++k) v[p][k] = c[k + 1];
             v[p][V - 1] = right;
@@ -105,7 +107,7 @@ __device__ __forceinline__ void step_row(const typename Prec<PREC>::S* __restric
         for (int i = 0; i < 9; ++i) f[i] = v[i][k];
 #pragma unroll
         for (int q = 0; q < 10; ++q) g[q] = v[9 + q][k];
-        collide(f, g, np);
+        collide_impl<false, C, kScaled>(f, g, np, nullptr);
 #pragma unroll
         for (int i = 0; i < 9; ++i) v[i][k] = f[i];
 #pragma unroll
@@ -114,8 +116,7 @@ __device__ __forceinline__ void step_row(const typename Prec<PREC>::S* __restric
 #pragma unroll
     for (int p = 0; p < kPlanes; ++p) {
         S r[V];
-#pragma unroll
-        for (int k = 0; k < V; ++k) encode(v[p][k], r[k]);
+        Codec::to_storage(v[p], r);
         VecIO<S, V>::store(dst + (long long)p * plane + rowy + x0, r);
     }
 }
