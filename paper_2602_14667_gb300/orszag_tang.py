@@ -1,11 +1,12 @@
 """Orszag-Tang vortex runs in the paper's physical units (Section
-"Orszag-Tang vortex", Eq. OT_initial, Tables 1-3).
+"Orszag-Tang vortex", Eq. OT_initial, Tables 1-3 at Re = 200 pi and Tables
+4, 5, 7, 8 at Re = 2500 and 5000).
 
 Physical-to-lattice mapping (the paper's wording of it is garbled; this is
 the reading taken): the field amplitude u0 = b0 = 2 is the rms of the
 initial fields and has the lattice value 0.2/pi; the domain [0, 2 pi)^2 has
 N x N nodes (dx = 2 pi / N), so one lattice step is dt = (0.2/pi) dx / u0
-of physical time (t = 1 is 2.5 N steps); Re = u0 L / nu with L = 2 pi gives
+of physical time (t = 1 is 5 N steps); Re = u0 L / nu with L = 2 pi gives
 nu in lattice units as nu dt / dx^2 and tau = 1/2 + 3 nu_lattice for both
 populations (magnetic Prandtl number 1).  Current density (Eq. current),
 vorticity and div b are converted back by 1 / (lattice speed per unit
@@ -46,9 +47,13 @@ def setup(n: int, reynolds: float = 200 * math.pi, u0: float = 2.0,
 
 
 def run(n: int, times, precision: str = "fp64", reynolds: float = 200 * math.pi,
-        collision: int = 0, stream=None):
+        collision: int = 0, stream=None, stop_on_failure: bool = False):
     """Advance the OT vortex on the GPU and return, for each physical time,
-    (t, j_max, omega_max, divb_max, step) in physical units."""
+    (t, j_max, omega_max, divb_max, step) in physical units.
+
+    A run that goes non-finite raises MhdError (MHD_EUNSTABLE), unless
+    stop_on_failure: then the first non-finite checkpoint is returned as
+    (t, None, None, None, step) and the run ends there (the paper's "Fail")."""
     import mhd_inputs
     s = setup(n, reynolds)
     out = []
@@ -59,7 +64,10 @@ def run(n: int, times, precision: str = "fp64", reynolds: float = 200 * math.pi,
             k = s.steps(t)
             lat.advance(k - done)
             done = k
-            tot = lat.get_totals()
+            tot = lat.get_totals(check_stable=not stop_on_failure)
+            if not all(math.isfinite(tot[q]) for q in ("mass", "e_kin", "e_mag", "jz_max", "omega_max")):
+                out.append((t, None, None, None, k))
+                break
             out.append((t, tot["jz_max"] * s.scale, tot["omega_max"] * s.scale,
                         tot["divb_max"] * s.scale, k))
     return out

@@ -4,7 +4,7 @@ Orszag-Tang runs (Tables 1-3, RR column, Re = 200 pi).
 Physical-to-lattice mapping (the paper's text on it is garbled; this is the
 reading taken): the Orszag-Tang amplitude is u0 = b0 = 2 (the rms of the
 fields), its lattice value is 0.2/pi, the domain [0, 2 pi) has N nodes, so
-dx = 2 pi / N, dt = (0.2/pi) dx / u0 (t = 1 is 2.5 N steps), Re = u0 L / nu
+dx = 2 pi / N, dt = (0.2/pi) dx / u0 (t = 1 is 5 N steps), Re = u0 L / nu
 with L = 2 pi, nu_lattice = nu dt / dx^2, tau = 1/2 + 3 nu_lattice (both
 populations, magnetic Prandtl number 1).  Quantities are converted back by
 1 / (lattice velocity per unit speed x dx).  j_z comes from the populations
