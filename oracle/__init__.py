@@ -51,6 +51,7 @@ class _Params(ctypes.Structure):
         ("rho0", ctypes.c_double), ("tau_f", ctypes.c_double), ("tau_m", ctypes.c_double),
         ("wall_x", ctypes.c_int), ("wall_y", ctypes.c_int),
         ("eq_variant", ctypes.c_int), ("collision", ctypes.c_int),
+        ("mag_collision", ctypes.c_int),
     ]
 
 
@@ -92,10 +93,11 @@ class Params:
     wall_y: bool = False
     eq_variant: int = 0
     collision: int = 0  # 0 recursive regularised, 1 BGK
+    mag_collision: int = 0  # 0 BGK, 1 regularised onto the first Hermite moment
 
     def c(self) -> _Params:
         return _Params(self.nx, self.ny, self.rho0, self.tau_f, self.tau_m, int(self.wall_x),
-                       int(self.wall_y), self.eq_variant, self.collision)
+                       int(self.wall_y), self.eq_variant, self.collision, self.mag_collision)
 
 
 def lattice():

@@ -75,8 +75,12 @@ def geq(ux, uy, bx, by):
     return out
 
 
-def collide_node(f, g, tau_f, tau_m, variant=0, collision=0):
-    """f: 9 Fractions, g: 5 pairs.  Returns (f*, g*)."""
+def collide_node(f, g, tau_f, tau_m, variant=0, collision=0, mag_collision=0):
+    """f: 9 Fractions, g: 5 pairs.  Returns (f*, g*).  mag_collision = 1:
+    only the first Hermite moment of g - g_eq relaxes; on D2Q5 that keeps
+    the antisymmetric half of each opposite pair's non-equilibrium,
+    (n_3 - n_1)/2 and (n_4 - n_2)/2 with opposite signs, and sets the rest
+    population's to zero."""
     rho = sum(f)
     ux = sum(f[i] * CX[i] for i in range(9)) / rho
     uy = sum(f[i] * CY[i] for i in range(9)) / rho
@@ -101,19 +105,28 @@ def collide_node(f, g, tau_f, tau_m, variant=0, collision=0):
         if collision == 1:
             fneq = f[i] - fe[i]
         fs.append(fe[i] + (1 - omega) * fneq)
-    gs = [(ge[j][0] + (1 - omega_m) * (g[j][0] - ge[j][0]),
-           ge[j][1] + (1 - omega_m) * (g[j][1] - ge[j][1])) for j in range(5)]
+    if mag_collision == 1:
+        n = [(g[j][0] - ge[j][0], g[j][1] - ge[j][1]) for j in range(5)]
+        h13 = [(n[3][a] - n[1][a]) / 2 for a in range(2)]
+        h24 = [(n[4][a] - n[2][a]) / 2 for a in range(2)]
+        reg = [(0, 0), (-h13[0], -h13[1]), (-h24[0], -h24[1]), (h13[0], h13[1]), (h24[0], h24[1])]
+        gs = [(ge[j][0] + (1 - omega_m) * reg[j][0], ge[j][1] + (1 - omega_m) * reg[j][1])
+              for j in range(5)]
+    else:
+        gs = [(ge[j][0] + (1 - omega_m) * (g[j][0] - ge[j][0]),
+               ge[j][1] + (1 - omega_m) * (g[j][1] - ge[j][1])) for j in range(5)]
     return fs, gs
 
 
-def step(f, g, nx, ny, tau_f, tau_m, wall_x=False, wall_y=False, variant=0, collision=0):
+def step(f, g, nx, ny, tau_f, tau_m, wall_x=False, wall_y=False, variant=0, collision=0,
+         mag_collision=0):
     """One collide-then-stream step.  f[i][y][x], g[j][y][x] = (gx, gy)."""
     fs = [[[None] * nx for _ in range(ny)] for _ in range(9)]
     gs = [[[None] * nx for _ in range(ny)] for _ in range(5)]
     for y in range(ny):
         for x in range(nx):
             fl, gl = collide_node([f[i][y][x] for i in range(9)], [g[j][y][x] for j in range(5)],
-                                  tau_f, tau_m, variant, collision)
+                                  tau_f, tau_m, variant, collision, mag_collision)
             for i in range(9):
                 fs[i][y][x] = fl[i]
             for j in range(5):

@@ -18,6 +18,7 @@
  *        the recursion, as full tensors over {x,y}^n
  *     4. f_neq,reg by Eq. fineq_reg (full contraction over the supported set)
  *     5. collide: f* = f_eq + (1-omega) f_neq,reg;  g* = g_eq + (1-omega_m) g_neq
+ *        (optionally with g_neq regularised onto its first Hermite moment)
  *     6. stream, push form f_i(x + c_i, t+1) = f*_i(x, t)
  *
  * Readings of the paper taken here (each is also listed in the design notes):
@@ -67,6 +68,10 @@ typedef struct {
     int wall_x, wall_y; /* 0: periodic axis, 1: half-way bounce-back walls */
     int eq_variant;     /* 0: A (Eq. feq_4th as printed), 1: B (Eq. a0_4 in full) */
     int collision;      /* 0: recursive regularised, 1: BGK (Eq. collide_f) */
+    int mag_collision;  /* 0: BGK (Eq. collide_g); 1: regularised -- only the first
+                           Hermite moment of g - g_eq relaxes (the extension of the
+                           regularisation to the magnetic populations that the
+                           Conclusions name as the next step) */
 } orc_params;
 
 static int opposite_f(int i) {
@@ -320,7 +325,27 @@ void orc_collide_node_da(const orc_params* p, const double* f, const double* g, 
         else
             fs[i] = feq[i] + (1.0 - omega) * fneq[i];
     }
-    for (int k = 0; k < 10; ++k) gs[k] = geq[k] + (1.0 - omega_m) * (g[k] - geq[k]);
+    if (p->mag_collision == 1) {
+        /* Regularised magnetic collision: project g - g_eq onto the first
+         * Hermite moment, Lambda_ac = sum_j e_{j,a} (g_{j,c} - g_eq_{j,c}), and
+         * rebuild g_neq,reg_{j,c} = psi_j e_{j,a} Lambda_ac / cs^2 (the zeroth
+         * moment of g - g_eq is zero: b is conserved). */
+        double lam[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+        for (int j = 0; j < 5; ++j) {
+            double e[2] = {(double)EX[j], (double)EY[j]};
+            for (int a = 0; a < 2; ++a)
+                for (int c = 0; c < 2; ++c) lam[a][c] += e[a] * (g[2 * j + c] - geq[2 * j + c]);
+        }
+        for (int j = 0; j < 5; ++j) {
+            double e[2] = {(double)EX[j], (double)EY[j]};
+            for (int c = 0; c < 2; ++c) {
+                double reg = PSI[j] * (e[0] * lam[0][c] + e[1] * lam[1][c]) / CS2;
+                gs[2 * j + c] = geq[2 * j + c] + (1.0 - omega_m) * reg;
+            }
+        }
+    } else {
+        for (int k = 0; k < 10; ++k) gs[k] = geq[k] + (1.0 - omega_m) * (g[k] - geq[k]);
+    }
 
     if (info) {
         info[0] = rho; info[1] = u[0]; info[2] = u[1]; info[3] = b[0]; info[4] = b[1];

@@ -49,13 +49,17 @@ def test_periodic_shear_wave(orc, nu):
     assert abs(rate / (nu * k * k) - 1) < 5e-3
 
 
+@pytest.mark.parametrize("mag_collision", [0, 1])
 @pytest.mark.parametrize("eta", [0.01, 0.05, 0.1])
-def test_periodic_magnetic_wave(orc, eta):
+def test_periodic_magnetic_wave(orc, eta, mag_collision):
+    """Also with the regularised magnetic collision: it keeps the first
+    moment of g - g_eq, which alone carries the diffusive flux, so eta is
+    unchanged."""
     nx, ny = 4, 64
     k = 2 * math.pi / ny
     y = np.arange(ny)
     shape = np.sin(k * y)
-    p = orc.Params(nx, ny, tau_f=0.8, tau_m=_tau(eta))
+    p = orc.Params(nx, ny, tau_f=0.8, tau_m=_tau(eta), mag_collision=mag_collision)
     bx = 1e-4 * np.tile(shape[:, None], (1, nx))
     z = np.zeros((ny, nx))
     rate = _decay_rate(orc, p, (z, z, bx, z), 3, shape, int(0.5 / (eta * k * k)))

@@ -43,25 +43,28 @@ def _to_np(f, g, nx, ny):
 
 
 CASES = [
-    # nx, ny, tau_f, tau_m, wall_x, wall_y, variant, collision, steps
-    (4, 4, Fr(3, 5), Fr(7, 10), False, False, 0, 0, 3),
-    (4, 6, Fr(11, 20), Fr(9, 10), False, True, 1, 0, 2),
-    (5, 4, Fr(13, 10), Fr(3, 5), True, True, 0, 1, 2),
-    (3, 5, Fr(51, 100), Fr(51, 100), True, False, 1, 0, 2),
+    # nx, ny, tau_f, tau_m, wall_x, wall_y, variant, collision, mag_collision, steps
+    (4, 4, Fr(3, 5), Fr(7, 10), False, False, 0, 0, 0, 3),
+    (4, 6, Fr(11, 20), Fr(9, 10), False, True, 1, 0, 0, 2),
+    (5, 4, Fr(13, 10), Fr(3, 5), True, True, 0, 1, 0, 2),
+    (3, 5, Fr(51, 100), Fr(51, 100), True, False, 1, 0, 0, 2),
+    (4, 4, Fr(3, 5), Fr(13, 20), False, False, 0, 0, 1, 3),
+    (5, 4, Fr(11, 20), Fr(3, 2), True, True, 1, 1, 1, 2),
 ]
 
 
-@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}_w{int(c[4])}{int(c[5])}_v{c[6]}_c{c[7]}")
+@pytest.mark.parametrize("case", CASES,
+                         ids=lambda c: f"{c[0]}x{c[1]}_w{int(c[4])}{int(c[5])}_v{c[6]}_c{c[7]}_m{c[8]}")
 def test_oracle_matches_exact_brute_force(orc, case):
-    nx, ny, tf, tm, wx, wy, variant, collision, steps = case
-    rng = np.random.default_rng(nx * 100 + ny)
+    nx, ny, tf, tm, wx, wy, variant, collision, mag, steps = case
+    rng = np.random.default_rng(nx * 100 + ny + 7 * mag)
     f, g = _state(rng, nx, ny, variant)
     f0, g0 = _to_np(f, g, nx, ny)
     for _ in range(steps):
-        f, g = exact.step(f, g, nx, ny, tf, tm, wx, wy, variant, collision)
+        f, g = exact.step(f, g, nx, ny, tf, tm, wx, wy, variant, collision, mag)
     fe, ge = _to_np(f, g, nx, ny)
     p = orc.Params(nx, ny, float(tf), float(tm), wall_x=wx, wall_y=wy, eq_variant=variant,
-                   collision=collision)
+                   collision=collision, mag_collision=mag)
     fo, go = orc.run(p, f0, g0, steps)
     np.testing.assert_allclose(fo, fe, rtol=0, atol=1e-14 * np.abs(fe).max())
     np.testing.assert_allclose(go, ge, rtol=0, atol=1e-14 * np.abs(ge).max())

@@ -275,11 +275,11 @@ def _transform(name, f, g, n):
 
 
 @pytest.mark.parametrize("name", sorted(SYMMETRIES))
-@pytest.mark.parametrize("variant", [0, 1])
-def test_step_commutes_with_lattice_symmetries(orc, name, variant):
+@pytest.mark.parametrize("variant,mag", [(0, 0), (1, 0), (0, 1)])
+def test_step_commutes_with_lattice_symmetries(orc, name, variant, mag):
     n = 6
     rng = np.random.default_rng(31)
-    p = orc.Params(n, n, tau_f=0.57, tau_m=0.83, eq_variant=variant)
+    p = orc.Params(n, n, tau_f=0.57, tau_m=0.83, eq_variant=variant, mag_collision=mag)
     ux, uy, bx, by = (rng.uniform(-0.08, 0.08, (n, n)) for _ in range(4))
     f, g = orc.init(p, ux, uy, bx, by, rho=rng.uniform(0.9, 1.1, (n, n)))
     f = f + rng.normal(0, 1e-3, f.shape) * W[:, None, None]
@@ -317,3 +317,43 @@ def test_stream_is_a_permutation(orc):
         np.testing.assert_allclose(np.sort(g.ravel()), np.sort(gs.ravel()))
         # rest populations do not move
         np.testing.assert_array_equal(f[0], fs[0]); np.testing.assert_array_equal(g[0], gs[0])
+
+
+# ---- regularised magnetic collision ------------------------------------------
+
+def test_regularised_magnetic_collision_moments(orc):
+    """g* - g_eq keeps sum = 0 (b conserved) and the first moment
+    (1 - omega_m) Lambda, and has no second-order content: sum_j e_jx^2 and
+    sum_j e_jy^2 of it vanish.  A non-equilibrium that is already first
+    order is left as BGK leaves it; omega_m = 1 gives g_eq."""
+    rng = np.random.default_rng(41)
+    tau_m = 0.74
+    om1 = 1 - 1 / tau_m
+    ex, ey = np.array(EX, float), np.array(EY, float)
+    for _ in range(20):
+        ux, uy, bx, by = rng.uniform(-0.1, 0.1, 4)
+        f = orc.feq(1.0 + rng.uniform(-0.05, 0.05), ux, uy, bx, by, 0)
+        f = f + rng.normal(0, 1e-3, 9) * W
+        rho = f.sum()
+        u = (f * CX).sum() / rho, (f * CY).sum() / rho
+        geq0 = orc.geq(u[0], u[1], bx, by).reshape(5, 2)
+        neq = rng.normal(0, 1e-3, (5, 2))
+        neq -= neq.mean(axis=0)                       # zero sum: the node's b is (bx, by)
+        g = geq0 + neq
+        fs, gs, _ = orc.collide_node(orc.Params(1, 1, 0.6, tau_m, mag_collision=1), f, g)
+        d = gs - geq0
+        np.testing.assert_allclose(d.sum(axis=0), 0, atol=1e-16)
+        lam = np.array([[(e * neq[:, c]).sum() for c in range(2)] for e in (ex, ey)])
+        got = np.array([[(e * d[:, c]).sum() for c in range(2)] for e in (ex, ey)])
+        np.testing.assert_allclose(got, om1 * lam, rtol=0, atol=1e-16)
+        for e in (ex, ey):
+            np.testing.assert_allclose(((e * e)[:, None] * d).sum(axis=0), 0, atol=1e-16)
+        # first-order non-equilibrium: regularised == BGK
+        first = np.array([[PSI[j] * (ex[j] * lam[0, c] + ey[j] * lam[1, c]) * 3 for c in range(2)]
+                          for j in range(5)])
+        g1 = geq0 + first
+        _, gr, _ = orc.collide_node(orc.Params(1, 1, 0.6, tau_m, mag_collision=1), f, g1)
+        _, gb, _ = orc.collide_node(orc.Params(1, 1, 0.6, tau_m, mag_collision=0), f, g1)
+        np.testing.assert_allclose(gr, gb, rtol=0, atol=1e-16)
+        _, g_one, _ = orc.collide_node(orc.Params(1, 1, 0.6, 1.0, mag_collision=1), f, g)
+        np.testing.assert_allclose(g_one, geq0, rtol=0, atol=1e-16)
