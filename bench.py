@@ -529,11 +529,22 @@ def run_closure_step(args):
             e1.synchronize()
             out[name] = e0.elapsed_time(e1) / args.steps
     mlp.close()
+    # Dominant kernel: step_closure.  Its algorithmic work is the MLP,
+    # 24x64 + 64x64 + 64x3 multiply-adds = 11,648 flop per node (BF16 tensor
+    # cores, FP32 accumulation); its state (2 x 19 planes FP32, 40 MB at
+    # 512^2) stays in L2 across steps.  Peak: the measured dense BF16 burst.
+    flops = 2 * (24 * 64 + 64 * 64 + 64 * 3) * n * n
+    achieved = flops / (out["closure"] * 1e-3) / 1e12
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+        peak = float(json.load(fh)["bf16_tflops"])
     res = {"metric": "closure step cost (512^2 coarse lattice)", "value": out["closure"] / out["plain"],
            "unit": "closure / plain time per step", "higher_is_better": False, "n_gpus": 1,
            "ms_per_step": out, "mlups": {k: n * n / (v * 1e-3) / 1e6 for k, v in out.items()},
            "config": {"workload": f"closure_step_{n}x{n}_fp32", "tau": 0.505}, "data": "synthetic",
-           "steps": args.steps, "warmup": args.warmup}
+           "steps": args.steps, "warmup": args.warmup,
+           "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "peak_source": "measured bf16 dense (burst)",
+                        "flops_per_node": flops // (n * n), "traffic": None}}
     print(json.dumps(res), flush=True)
 
 

@@ -61,6 +61,16 @@ typedef enum {
     MHD_BGK = 1 /* plain BGK fluid collision (Eq. collide_f), for comparison */
 } mhd_collision;
 
+/* Collision of the magnetic populations. */
+typedef enum {
+    MHD_MAG_BGK = 0,         /* Eq. collide_g (the paper's scheme) */
+    MHD_MAG_REGULARISED = 1  /* only the first Hermite moment of g - g_eq relaxes:
+                                Lambda_ab = sum_j e_{j,a} (g - g_eq)_{j,b},
+                                g* = g_eq + (1 - omega_m) psi_j e_{j,a} Lambda_ab / cs^2
+                                (the extension the Conclusions name as the next step;
+                                same magnetic diffusivity) */
+} mhd_mag_collision;
+
 typedef struct {
     double rho0;    /* reference density, > 0 (shift of the stored populations) */
     double tau_f;   /* fluid relaxation time, > 1/2 (omega = 1/tau_f) */
@@ -71,6 +81,7 @@ typedef struct {
                        only); 1: with the u (x) M terms of Eq. a0_4 at 3rd and
                        4th order */
     int collision;  /* mhd_collision */
+    int mag_collision; /* mhd_mag_collision */
 } mhd_params;
 
 /* Global diagnostics at the current time (mhd_get_totals).  Sums run over

@@ -88,6 +88,7 @@ mhd::StepLaunch step_launch(const mhd_lattice* l, int from) {
     s.rho0 = l->p.rho0;
     s.variant = l->p.eq_variant;
     s.collision = l->p.collision;
+    s.mag_collision = l->p.mag_collision;
     s.wall_x = l->p.bc_x == MHD_WALL;
     s.wall_y = l->p.bc_y == MHD_WALL;
     s.V = l->cfg.nodes_per_thread;
@@ -183,6 +184,8 @@ mhd_status check_params(const mhd_params* p) {
         return fail(MHD_EINVAL, "unknown precision");
     if (p->eq_variant != 0 && p->eq_variant != 1) return fail(MHD_EINVAL, "eq_variant must be 0 or 1");
     if (p->collision != MHD_RR && p->collision != MHD_BGK) return fail(MHD_EINVAL, "unknown collision");
+    if (p->mag_collision != MHD_MAG_BGK && p->mag_collision != MHD_MAG_REGULARISED)
+        return fail(MHD_EINVAL, "unknown mag_collision");
     return MHD_OK;
 }
 

@@ -197,8 +197,9 @@ mhd_status mhd_batch_create(int count, const int* nx, const int* ny, const mhd_p
         if (!(p.rho0 > 0) || !std::isfinite(p.rho0)) return bfail(MHD_EINVAL, "rho0 must be > 0");
         if (p.precision != MHD_FP32 || p.bc_x != MHD_PERIODIC || p.bc_y != MHD_PERIODIC)
             return bfail(MHD_EINVAL, "batched lattices are FP32 and periodic");
-        if ((p.eq_variant != 0 && p.eq_variant != 1) || (p.collision != MHD_RR && p.collision != MHD_BGK))
-            return bfail(MHD_EINVAL, "unknown eq_variant / collision");
+        if ((p.eq_variant != 0 && p.eq_variant != 1) || (p.collision != MHD_RR && p.collision != MHD_BGK) ||
+            (p.mag_collision != MHD_MAG_BGK && p.mag_collision != MHD_MAG_REGULARISED))
+            return bfail(MHD_EINVAL, "unknown eq_variant / collision / mag_collision");
     }
     auto* b = new (std::nothrow) mhd_batch();
     if (!b) return bfail(MHD_ENOMEM, "host allocation failed");
@@ -224,6 +225,7 @@ mhd_status mhd_batch_create(int count, const int* nx, const int* ny, const mhd_p
         lats[i].np.rho0 = (float)params[i].rho0;
         lats[i].np.variant = params[i].eq_variant;
         lats[i].np.collision = params[i].collision;
+        lats[i].np.mag_collision = params[i].mag_collision;
         b->total_elems += (long long)mhd::kStatePlanes * L.plane;
         b->nodes += (long long)nx[i] * ny[i];
         maxn = std::max(maxn, (long long)nx[i] * ny[i]);

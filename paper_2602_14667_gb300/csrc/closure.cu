@@ -693,6 +693,7 @@ cudaError_t launch_step_closure(const StepLaunch& s, const ClosureParamsDev& cp,
     a.np.rho0 = (float)s.rho0;
     a.np.variant = s.variant;
     a.np.collision = s.collision;
+    a.np.mag_collision = s.mag_collision;
     a.wall_x = 0;
     a.wall_y = 0;
     const int ntx = (s.L.nx + kCTX - 1) / kCTX, nty = (s.L.ny + kCTY - 1) / kCTY, ntiles = ntx * nty;

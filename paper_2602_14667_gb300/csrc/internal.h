@@ -27,7 +27,7 @@ struct StepLaunch {
     const void* src;
     void* dst;
     double omega, omega_m, rho0;
-    int variant, collision, wall_x, wall_y;
+    int variant, collision, mag_collision, wall_x, wall_y;
     int V;   // nodes per thread along x
     int BY;  // warps (rows) per block
 };

@@ -74,6 +74,7 @@ static cudaError_t launch_step_t(const StepLaunch& s, cudaStream_t st) {
     a.np.rho0 = C(s.rho0);
     a.np.variant = s.variant;
     a.np.collision = s.collision;
+    a.np.mag_collision = s.mag_collision;
     a.wall_x = s.wall_x;
     a.wall_y = s.wall_y;
     dim3 block(32, s.BY);

@@ -142,6 +142,7 @@ template <typename C> struct NodeParams {
     C rho0;
     int variant;    // 0: Eq. feq_4th; 1: + u (x) M terms of Eq. a0_4
     int collision;  // 0: recursive regularised; 1: BGK
+    int mag_collision;  // 0: BGK (Eq. collide_g); 1: first Hermite moment of g - g_eq only
 };
 
 // Moments of one node (task 1): rho = rho0 + sum df, m = sum df c, b = sum g.
@@ -314,14 +315,35 @@ __device__ __forceinline__ void collide_impl(C (&f)[9], C (&g)[10], const NodePa
     const C om = p.omega_m, omm1 = C(1) - p.omega_m;
     const C q1 = C(1.0 / 6.0);
     const C gbx = q1 * Bx, gby = q1 * By;
-    g[2] = om * gbx + omm1 * g[2];               // j=1 (-1,0): x
-    g[3] = om * (q1 * (By - E3)) + omm1 * g[3];  // j=1: y
-    g[4] = om * (q1 * (Bx + E3)) + omm1 * g[4];  // j=2 (0,-1): x
-    g[5] = om * gby + omm1 * g[5];               // j=2: y
-    g[6] = om * gbx + omm1 * g[6];               // j=3 (+1,0): x
-    g[7] = om * (q1 * (By + E3)) + omm1 * g[7];  // j=3: y
-    g[8] = om * (q1 * (Bx - E3)) + omm1 * g[8];  // j=4 (0,+1): x
-    g[9] = om * gby + omm1 * g[9];               // j=4: y
+    if (p.mag_collision == 0) {
+        g[2] = om * gbx + omm1 * g[2];               // j=1 (-1,0): x
+        g[3] = om * (q1 * (By - E3)) + omm1 * g[3];  // j=1: y
+        g[4] = om * (q1 * (Bx + E3)) + omm1 * g[4];  // j=2 (0,-1): x
+        g[5] = om * gby + omm1 * g[5];               // j=2: y
+        g[6] = om * gbx + omm1 * g[6];               // j=3 (+1,0): x
+        g[7] = om * (q1 * (By + E3)) + omm1 * g[7];  // j=3: y
+        g[8] = om * (q1 * (Bx - E3)) + omm1 * g[8];  // j=4 (0,+1): x
+        g[9] = om * gby + omm1 * g[9];               // j=4: y
+    } else {
+        // Regularised: psi_j e_{j,a} Lambda_ab / cs^2 with Lambda the first
+        // moment of g - g_eq keeps, on D2Q5, the antisymmetric half h of
+        // each opposite pair's non-equilibrium (-h on j = 1, 2; +h on
+        // j = 3, 4) and none on j = 0.
+        const C e1y = q1 * (By - E3), e2x = q1 * (Bx + E3);
+        const C e3y = q1 * (By + E3), e4x = q1 * (Bx - E3);
+        const C h13x = C(0.5) * (g[6] - g[2]);  // g_eq equal on the pair
+        const C h13y = C(0.5) * ((g[7] - e3y) - (g[3] - e1y));
+        const C h24x = C(0.5) * ((g[8] - e4x) - (g[4] - e2x));
+        const C h24y = C(0.5) * (g[9] - g[5]);
+        g[2] = gbx - omm1 * h13x;
+        g[6] = gbx + omm1 * h13x;
+        g[3] = e1y - omm1 * h13y;
+        g[7] = e3y + omm1 * h13y;
+        g[4] = e2x - omm1 * h24x;
+        g[8] = e4x + omm1 * h24x;
+        g[5] = gby - omm1 * h24y;
+        g[9] = gby + omm1 * h24y;
+    }
     // rest population by difference: sum_j g*_j = b exactly (psi_0 + 4 psi_1
     // = 1 + 6e-8 in FP32 would otherwise grow b by ~1e-7 per step)
     g[0] = Bx - ((g[2] + g[4]) + (g[6] + g[8]));

@@ -47,7 +47,8 @@ def setup(n: int, reynolds: float = 200 * math.pi, u0: float = 2.0,
 
 
 def run(n: int, times, precision: str = "fp64", reynolds: float = 200 * math.pi,
-        collision: int = 0, stream=None, stop_on_failure: bool = False):
+        collision: int = 0, stream=None, stop_on_failure: bool = False, eq_variant: int = 0,
+        mag_collision: int = 0):
     """Advance the OT vortex on the GPU and return, for each physical time,
     (t, j_max, omega_max, divb_max, step) in physical units.
 
@@ -57,7 +58,8 @@ def run(n: int, times, precision: str = "fp64", reynolds: float = 200 * math.pi,
     import mhd_inputs
     s = setup(n, reynolds)
     out = []
-    with Lattice(n, n, s.tau, s.tau, precision=precision, collision=collision, stream=stream) as lat:
+    with Lattice(n, n, s.tau, s.tau, precision=precision, collision=collision, stream=stream,
+                 eq_variant=eq_variant, mag_collision=mag_collision) as lat:
         lat.set_fields(*mhd_inputs.orszag_tang(n, 2.0 * s.u_lattice, 2.0 * s.u_lattice))
         done = 0
         for t in times:
