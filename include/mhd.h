@@ -61,6 +61,17 @@ typedef enum {
     MHD_BGK = 1 /* plain BGK fluid collision (Eq. collide_f), for comparison */
 } mhd_collision;
 
+/* Storage of the state.  MHD_TWO_BUFFERS: the pull scheme reads one buffer
+ * and writes the other.  MHD_IN_PLACE: one buffer, updated in place by a
+ * pair of alternating kernels (the "AA" access pattern: the first streams
+ * and collides and writes each population back into the cell it came from,
+ * the second collides locally); half the device memory for the same bytes
+ * moved per step, bitwise the same states.  In-place lattices need a
+ * periodic x axis, and have no closure and no access to the previous step's
+ * state (mhd_closure_filter / mhd_closure_sgs_targets / mhd_set_closure
+ * return MHD_EINVAL). */
+typedef enum { MHD_TWO_BUFFERS = 0, MHD_IN_PLACE = 1 } mhd_streaming;
+
 /* Collision of the magnetic populations. */
 typedef enum {
     MHD_MAG_BGK = 0,         /* Eq. collide_g (the paper's scheme) */
@@ -82,6 +93,7 @@ typedef struct {
                        4th order */
     int collision;  /* mhd_collision */
     int mag_collision; /* mhd_mag_collision */
+    int streaming;     /* mhd_streaming (single lattices; batches use MHD_TWO_BUFFERS) */
 } mhd_params;
 
 /* Global diagnostics at the current time (mhd_get_totals).  Sums run over

@@ -20,6 +20,7 @@ MHD_FP64, MHD_FP32, MHD_FP16S = range(3)
 MHD_PERIODIC, MHD_WALL = range(2)
 MHD_RR, MHD_BGK = range(2)
 MHD_MAG_BGK, MHD_MAG_REGULARISED = range(2)
+MHD_TWO_BUFFERS, MHD_IN_PLACE = range(2)
 STATUS_NAMES = {0: "MHD_OK", 1: "MHD_EINVAL", 2: "MHD_ENOMEM", 3: "MHD_ECUDA", 4: "MHD_EUNSTABLE",
                 5: "MHD_ESTATE"}
 PRECISIONS = {"fp64": MHD_FP64, "fp32": MHD_FP32, "fp16s": MHD_FP16S}
@@ -29,7 +30,7 @@ class mhd_params(ctypes.Structure):
     _fields_ = [("rho0", ctypes.c_double), ("tau_f", ctypes.c_double), ("tau_m", ctypes.c_double),
                 ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int), ("precision", ctypes.c_int),
                 ("eq_variant", ctypes.c_int), ("collision", ctypes.c_int),
-                ("mag_collision", ctypes.c_int)]
+                ("mag_collision", ctypes.c_int), ("streaming", ctypes.c_int)]
 
 
 TOTAL_FIELDS = ("mass", "mom_x", "mom_y", "e_kin", "e_mag", "cross_hel", "bsum_x", "bsum_y",
@@ -142,11 +143,12 @@ class Lattice:
 
     def __init__(self, nx: int, ny: int, tau_f: float, tau_m: float, precision="fp32",
                  rho0: float = 1.0, wall_x: bool = False, wall_y: bool = False, eq_variant: int = 0,
-                 collision: int = MHD_RR, stream=None, mag_collision: int = MHD_MAG_BGK):
+                 collision: int = MHD_RR, stream=None, mag_collision: int = MHD_MAG_BGK,
+                 in_place: bool = False):
         self.nx, self.ny = int(nx), int(ny)
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.params = mhd_params(rho0, tau_f, tau_m, int(wall_x), int(wall_y), prec, eq_variant,
-                                 collision, mag_collision)
+                                 collision, mag_collision, MHD_IN_PLACE if in_place else MHD_TWO_BUFFERS)
         self._h = _P()
         s = None if stream is None else _P(int(stream))
         check(lib().mhd_create(self.nx, self.ny, ctypes.byref(self.params), s, ctypes.byref(self._h)),
@@ -277,7 +279,7 @@ class Batch:
         nx = (ctypes.c_int * n)(*[s[0] for s in self.sizes])
         ny = (ctypes.c_int * n)(*[s[1] for s in self.sizes])
         ps = (mhd_params * n)(*[mhd_params(rho0, tf, tm, MHD_PERIODIC, MHD_PERIODIC, MHD_FP32, eq_variant,
-                                           collision, mag_collision) for tf, tm in taus])
+                                           collision, mag_collision, MHD_TWO_BUFFERS) for tf, tm in taus])
         self._h = _P()
         s = None if stream is None else _P(int(stream))
         check(lib().mhd_batch_create(n, nx, ny, ps, s, ctypes.byref(self._h)), "mhd_batch_create")

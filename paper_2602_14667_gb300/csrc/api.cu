@@ -13,6 +13,7 @@
 
 #include "../../include/mhd.h"
 #include "closure_internal.h"
+#include "inplace.h"
 #include "internal.h"
 
 namespace {
@@ -56,8 +57,10 @@ struct mhd_lattice {
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;
     mhd::Layout L{};
-    void* buf[2] = {nullptr, nullptr};
+    void* buf[2] = {nullptr, nullptr};  // in place: buf[0] only
     int cur = 0;
+    bool in_place = false;
+    bool aa_streamed = false;  // in place, after an odd number of steps: streamed layout
     bool fields_set = false;
     bool prev_valid = false;  // buf[cur^1] holds the state the last step read
     bool state_is_eq = false; // current state has zero non-equilibrium
@@ -102,6 +105,23 @@ cudaError_t launch_lattice_step(const mhd_lattice* l, int from, cudaStream_t st)
     return mhd::launch_step(s, st);
 }
 
+// In place: one step on `buf` (phase 0 from the canonical layout, 1 from
+// the streamed one).
+cudaError_t launch_inplace_step(const mhd_lattice* l, void* buf, int phase, cudaStream_t st) {
+    mhd::StepLaunch s = step_launch(l, 0);
+    s.src = buf;
+    s.dst = buf;
+    return mhd::launch_aa_step(s, phase, st);
+}
+
+// Bring an in-place lattice to the canonical layout (same time step).
+cudaError_t normalize(mhd_lattice* l) {
+    if (!l->in_place || !l->aa_streamed) return cudaSuccess;
+    cudaError_t e = mhd::launch_aa_unstream(l->L, l->p.precision, l->buf[0], l->p.bc_y == MHD_WALL, l->stream);
+    if (e == cudaSuccess) l->aa_streamed = false;
+    return e;
+}
+
 void drop_graphs(mhd_lattice* l) {
     for (auto& g : l->graph)
         if (g) {
@@ -137,8 +157,8 @@ std::string cache_key(const mhd_lattice* l) {
     std::string name = "gpu";
     if (cudaGetDeviceProperties(&prop, l->dev) == cudaSuccess) name = prop.name;
     char buf[256];
-    snprintf(buf, sizeof buf, "%s|p%d|%dx%d|bc%d%d", name.c_str(), l->p.precision, l->nx, l->ny,
-             l->p.bc_x, l->p.bc_y);
+    snprintf(buf, sizeof buf, "%s|p%d|%dx%d|bc%d%d%s", name.c_str(), l->p.precision, l->nx, l->ny,
+             l->p.bc_x, l->p.bc_y, l->in_place ? "|inplace" : "");
     return buf;
 }
 
@@ -186,6 +206,10 @@ mhd_status check_params(const mhd_params* p) {
     if (p->collision != MHD_RR && p->collision != MHD_BGK) return fail(MHD_EINVAL, "unknown collision");
     if (p->mag_collision != MHD_MAG_BGK && p->mag_collision != MHD_MAG_REGULARISED)
         return fail(MHD_EINVAL, "unknown mag_collision");
+    if (p->streaming != MHD_TWO_BUFFERS && p->streaming != MHD_IN_PLACE)
+        return fail(MHD_EINVAL, "unknown streaming");
+    if (p->streaming == MHD_IN_PLACE && p->bc_x != MHD_PERIODIC)
+        return fail(MHD_EINVAL, "in-place streaming needs a periodic x axis");
     return MHD_OK;
 }
 
@@ -209,9 +233,10 @@ mhd_status mhd_create(int nx, int ny, const mhd_params* p, void* stream, mhd_lat
     l->p = *p;
     l->stream = static_cast<cudaStream_t>(stream);
     l->L = mhd::make_layout(nx, ny, p->precision);
+    l->in_place = p->streaming == MHD_IN_PLACE;
     cudaError_t e = cudaGetDevice(&l->dev);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&l->cap, cudaStreamNonBlocking);
-    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&l->buf[b], l->buf_bytes());
+    for (int b = 0; b < (l->in_place ? 1 : 2) && e == cudaSuccess; ++b) e = cudaMalloc(&l->buf[b], l->buf_bytes());
     if (e == cudaSuccess)
         e = cudaMalloc(&l->partials, sizeof(double) * mhd::kDiagSlots * mhd::diag_blocks(l->L));
     if (e == cudaSuccess) e = cudaMalloc(&l->totals_d, sizeof(double) * mhd::kDiagSlots);
@@ -276,16 +301,19 @@ mhd_status mhd_set_fields(mhd_lattice* l, const double* ux, const double* uy, co
     l->fields_set = true;
     l->prev_valid = false;
     l->state_is_eq = true;
+    l->aa_streamed = false;
     return MHD_OK;
 }
 
+// Graph of kGraphSteps steps starting from buffer `from` (two buffers) or
+// from phase `from` (in place); kGraphSteps is even, so it ends where it began.
 static mhd_status capture_graph(mhd_lattice* l, int from) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(l->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
     int c = from;
     cudaError_t le = cudaSuccess;
     for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k) {
-        le = launch_lattice_step(l, c, l->cap);
+        le = l->in_place ? launch_inplace_step(l, l->buf[0], c, l->cap) : launch_lattice_step(l, c, l->cap);
         c ^= 1;
     }
     cudaError_t ee = cudaStreamEndCapture(l->cap, &g);
@@ -306,6 +334,26 @@ mhd_status mhd_advance(mhd_lattice* l, long long nsteps) {
     if (!l->fields_set) return fail(MHD_ESTATE, "set fields or populations first");
     if (nsteps == 0) return MHD_OK;
     CK(cudaSetDevice(l->dev), "cudaSetDevice");
+    if (l->in_place) {
+        while (nsteps >= kGraphSteps) {
+            const int ph = l->aa_streamed ? 1 : 0;
+            if (!l->graph[ph]) {
+                mhd_status s = capture_graph(l, ph);
+                if (s != MHD_OK) return s;
+            }
+            CK(cudaGraphLaunch(l->graph[ph], l->stream), "graph launch");
+            nsteps -= kGraphSteps;
+            l->step += kGraphSteps;
+        }
+        while (nsteps > 0) {
+            CK(launch_inplace_step(l, l->buf[0], l->aa_streamed ? 1 : 0, l->stream), "step launch");
+            l->aa_streamed = !l->aa_streamed;
+            --nsteps;
+            ++l->step;
+        }
+        l->state_is_eq = false;
+        return MHD_OK;
+    }
     while (nsteps >= kGraphSteps) {
         if (!l->graph[l->cur]) {
             mhd_status s = capture_graph(l, l->cur);
@@ -330,6 +378,7 @@ mhd_status mhd_get_fields(mhd_lattice* l, double* rho, double* ux, double* uy, d
     if (!l) return fail(MHD_EINVAL, "lattice is NULL");
     if (!l->fields_set) return fail(MHD_ESTATE, "set fields or populations first");
     CK(cudaSetDevice(l->dev), "cudaSetDevice");
+    CK(normalize(l), "unstream kernel");
     mhd_status s = ensure_io(l);
     if (s != MHD_OK) return s;
     const long long n = l->n();
@@ -351,6 +400,7 @@ mhd_status mhd_get_totals(mhd_lattice* l, mhd_totals* out) {
     if (!l || !out) return fail(MHD_EINVAL, "NULL argument");
     if (!l->fields_set) return fail(MHD_ESTATE, "set fields or populations first");
     CK(cudaSetDevice(l->dev), "cudaSetDevice");
+    CK(normalize(l), "unstream kernel");
     mhd::DiagLaunch d;
     d.L = l->L;
     d.prec = l->p.precision;
@@ -394,6 +444,7 @@ mhd_status mhd_get_populations(mhd_lattice* l, double* f, double* g) {
     if (!l || !f || !g) return fail(MHD_EINVAL, "NULL argument");
     if (!l->fields_set) return fail(MHD_ESTATE, "set fields or populations first");
     CK(cudaSetDevice(l->dev), "cudaSetDevice");
+    CK(normalize(l), "unstream kernel");
     mhd_status s = ensure_io(l);
     if (s != MHD_OK) return s;
     const long long n = l->n();
@@ -427,6 +478,7 @@ mhd_status mhd_set_populations(mhd_lattice* l, const double* f, const double* g)
     l->fields_set = true;
     l->prev_valid = false;
     l->state_is_eq = false;
+    l->aa_streamed = false;
     return MHD_OK;
 }
 
@@ -440,8 +492,8 @@ mhd_status mhd_set_closure(mhd_lattice* l, const mhd_mlp* mlp) {
         drop_graphs(l);
         return MHD_OK;
     }
-    if (l->p.precision != MHD_FP32 || l->p.bc_x != MHD_PERIODIC || l->p.bc_y != MHD_PERIODIC)
-        return fail(MHD_EINVAL, "the closure runs on FP32 periodic lattices");
+    if (l->p.precision != MHD_FP32 || l->p.bc_x != MHD_PERIODIC || l->p.bc_y != MHD_PERIODIC || l->in_place)
+        return fail(MHD_EINVAL, "the closure runs on FP32 periodic two-buffer lattices");
     using namespace mhd;
     const size_t nbf = (size_t)kHid * kInPad + (size_t)kHid * kHid + (size_t)kOutPad * kHid;
     const size_t nfl = 2 * kHid + kOutPad + 2 * kIn + kOut;
@@ -482,6 +534,7 @@ mhd_status mhd_closure_filter(mhd_lattice* l, int factor, float* coarse_state) {
     if (!l || !coarse_state) return fail(MHD_EINVAL, "NULL argument");
     if (factor < 1 || l->nx % factor || l->ny % factor) return fail(MHD_EINVAL, "factor must divide nx and ny");
     if (l->p.bc_x != MHD_PERIODIC || l->p.bc_y != MHD_PERIODIC) return fail(MHD_EINVAL, "periodic lattices only");
+    if (l->in_place) return fail(MHD_EINVAL, "in-place lattices keep no previous state");
     if (!l->prev_valid) return fail(MHD_ESTATE, "needs the state after a step (advance first)");
     CK(cudaSetDevice(l->dev), "cudaSetDevice");
     CK(mhd::launch_filter(l->L, l->p.precision, l->buf[l->cur ^ 1], factor, coarse_state, l->stream), "filter kernel");
@@ -495,6 +548,7 @@ mhd_status mhd_closure_sgs_targets(mhd_lattice* l, int factor, double tau_coarse
     if (l->p.bc_x != MHD_PERIODIC || l->p.bc_y != MHD_PERIODIC) return fail(MHD_EINVAL, "periodic lattices only");
     if (!(tau_coarse > 0.5) || std::fabs(1.0 - 1.0 / tau_coarse) < 1e-12)
         return fail(MHD_EINVAL, "tau_coarse must be > 1/2 and != 1");
+    if (l->in_place) return fail(MHD_EINVAL, "in-place lattices keep no previous state");
     if (!l->prev_valid) return fail(MHD_ESTATE, "needs the state after a step (advance first)");
     if (l->p.rho0 != 1.0) return fail(MHD_EINVAL, "rho0 = 1 only");
     CK(cudaSetDevice(l->dev), "cudaSetDevice");
@@ -513,6 +567,7 @@ mhd_status mhd_set_precollision_state(mhd_lattice* l, const float* state) {
     l->fields_set = true;
     l->prev_valid = false;
     l->state_is_eq = false;
+    l->aa_streamed = false;
     return MHD_OK;
 }
 
@@ -528,6 +583,7 @@ mhd_status mhd_get_state(mhd_lattice* l, void* host, size_t bytes) {
     if (bytes != need) return fail(MHD_EINVAL, "state buffer has the wrong size");
     if (!l->fields_set) return fail(MHD_ESTATE, "set fields or populations first");
     CK(cudaSetDevice(l->dev), "cudaSetDevice");
+    CK(normalize(l), "unstream kernel");
     const size_t es = l->L.esize, row = (size_t)l->nx * es;
     for (int p = 0; p < mhd::kStatePlanes; ++p) {
         char* dst = static_cast<char*>(host) + (size_t)p * l->n() * es;
@@ -557,6 +613,7 @@ mhd_status mhd_set_state(mhd_lattice* l, const void* host, size_t bytes) {
     l->fields_set = true;
     l->prev_valid = false;
     l->state_is_eq = false;
+    l->aa_streamed = false;
     return MHD_OK;
 }
 
@@ -595,6 +652,18 @@ mhd_status mhd_autotune(mhd_lattice* l, mhd_kernel_config* best) {
         }
     }
     CK(cudaStreamSynchronize(l->stream), "mhd_autotune");
+    // In place there is no spare buffer: candidates run on a scratch copy of
+    // the state (held only while tuning), one phase-0 / phase-1 pair per step pair.
+    void* scratch = nullptr;
+    if (l->in_place) {
+        CK(normalize(l), "unstream kernel");
+        CK(cudaMalloc(&scratch, l->buf_bytes()), "cudaMalloc(autotune scratch)");
+        cudaError_t ce = cudaMemcpyAsync(scratch, l->buf[0], l->buf_bytes(), cudaMemcpyDeviceToDevice, l->stream);
+        if (ce != cudaSuccess) {
+            cudaFree(scratch);
+            return cuda_fail(ce, "autotune scratch copy");
+        }
+    }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event");
     CK(cudaEventCreate(&e1), "event");
@@ -608,10 +677,14 @@ mhd_status mhd_autotune(mhd_lattice* l, mhd_kernel_config* best) {
             if (!config_ok(l, c)) continue;
             l->cfg = c;
             mhd::StepLaunch s = step_launch(l, l->cur);  // reads cur, writes the spare buffer
+            auto one = [&](int k) {
+                return l->in_place ? launch_inplace_step(l, scratch, k & 1, l->stream)
+                                   : mhd::launch_step(s, l->stream);
+            };
             cudaError_t err = cudaSuccess;
-            for (int k = 0; k < 3 && err == cudaSuccess; ++k) err = mhd::launch_step(s, l->stream);
+            for (int k = 0; k < 4 && err == cudaSuccess; ++k) err = one(k);
             if (err == cudaSuccess) err = cudaEventRecord(e0, l->stream);
-            for (int k = 0; k < iters && err == cudaSuccess; ++k) err = mhd::launch_step(s, l->stream);
+            for (int k = 0; k < iters && err == cudaSuccess; ++k) err = one(k);
             if (err == cudaSuccess) err = cudaEventRecord(e1, l->stream);
             if (err == cudaSuccess) err = cudaEventSynchronize(e1);
             float ms = 0;
@@ -620,6 +693,7 @@ mhd_status mhd_autotune(mhd_lattice* l, mhd_kernel_config* best) {
                 l->cfg = saved;
                 cudaEventDestroy(e0);
                 cudaEventDestroy(e1);
+                if (scratch) cudaFree(scratch);
                 return cuda_fail(err, "autotune candidate");
             }
             if (getenv("MHD_TUNE_VERBOSE"))
@@ -633,6 +707,10 @@ mhd_status mhd_autotune(mhd_lattice* l, mhd_kernel_config* best) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (scratch) {
+        CK(cudaStreamSynchronize(l->stream), "mhd_autotune");
+        cudaFree(scratch);
+    }
     l->cfg = saved;
     l->prev_valid = false;  // the spare buffer was overwritten
     mhd_status s = mhd_set_kernel_config(l, &chosen);

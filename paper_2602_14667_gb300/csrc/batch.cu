@@ -200,6 +200,7 @@ mhd_status mhd_batch_create(int count, const int* nx, const int* ny, const mhd_p
         if ((p.eq_variant != 0 && p.eq_variant != 1) || (p.collision != MHD_RR && p.collision != MHD_BGK) ||
             (p.mag_collision != MHD_MAG_BGK && p.mag_collision != MHD_MAG_REGULARISED))
             return bfail(MHD_EINVAL, "unknown eq_variant / collision / mag_collision");
+        if (p.streaming != MHD_TWO_BUFFERS) return bfail(MHD_EINVAL, "batched lattices use two buffers");
     }
     auto* b = new (std::nothrow) mhd_batch();
     if (!b) return bfail(MHD_ENOMEM, "host allocation failed");

@@ -1,0 +1,240 @@
+// inplace_row.cuh -- the fused step on ONE state buffer (in-place streaming).
+//
+// The two-buffer pull scheme reads f*(t) from one buffer and writes f*(t+1)
+// to the other.  Here a pair of kernels updates a single buffer in place
+// (the "AA" access pattern), so a lattice needs half the memory for the
+// same bytes moved per step:
+//
+//   phase A (buffer holds the canonical state f*_p(x) at plane p):
+//     gather f_p(x) exactly as the pull step does (plane p at x - c_p, or
+//     plane opp(p) at x across a half-way bounce-back wall), collide, and
+//     write every post-collision population back into the cell its
+//     opposite's slot was read from: slot p receives f*_opp(p)(x).  After
+//     it, plane opp(q) at x + c_q holds f*_q(x) = f_q(x + c_q, t+1), the
+//     pre-collision state of the next step, stored in the opposite plane.
+//   phase B (buffer holds that streamed state): every node reads its own
+//     pre-collision populations locally (population q from plane opp(q)),
+//     collides, and writes f*_q(x) to plane q: the canonical layout again.
+//
+// Each node writes exactly the cells it read, so no two threads touch the
+// same cell and the update needs no second buffer.  Both phases evaluate
+// the same collision on the same inputs as the two-buffer step, so the
+// state after an even number of steps is bitwise that of the pull scheme.
+// In phase A the warp-edge lanes own one cell of the neighbouring warp's
+// aligned vector: they write it with a scalar store and the neighbour's
+// vector store leaves it out (the neighbour's vector load of that cell is
+// discarded).  Loads are plain (coherent) loads: the buffer is written by
+// the same kernel.
+#pragma once
+
+#include "step_row.cuh"
+
+namespace mhd {
+
+template <typename S, int V> struct VecRW {
+    using Raw = typename RawT<sizeof(S) * V>::T;
+    __device__ __forceinline__ static void load(const S* p, S (&out)[V]) {
+        const Raw r = *reinterpret_cast<const Raw*>(p);
+        memcpy(out, &r, sizeof(Raw));
+    }
+    // Aligned store of the V elements, except the first and/or the last.
+    __device__ __forceinline__ static void store(S* p, const S (&in)[V], bool skip_first,
+                                                 bool skip_last) {
+        if (!skip_first && !skip_last) {
+            Raw r;
+            memcpy(&r, in, sizeof(Raw));
+            *reinterpret_cast<Raw*>(p) = r;
+            return;
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+            if (!((k == 0 && skip_first) || (k == V - 1 && skip_last))) p[k] = in[k];
+    }
+};
+
+// One value into the step's storage units (FP16S: the stored half of a
+// value already in 2^12 units; otherwise the storage type itself).
+__device__ __forceinline__ double step_store_one(double c, double) { return c; }
+__device__ __forceinline__ float step_store_one(float c, float) { return c; }
+__device__ __forceinline__ __half step_store_one(float c, __half) { return __float2half_rn(c); }
+
+// Phase A for one warp: 32*V consecutive nodes of row y (requires nx % V
+// == 0, all 32 lanes present, y < ny; periodic in x).
+template <int PREC, int V, bool WALLY>
+__device__ __forceinline__ void aa_row_a(typename Prec<PREC>::S* buf, int nx, int ny,
+                                         long long pitch, long long plane,
+                                         const NodeParams<typename Prec<PREC>::C>& np, int xblock,
+                                         int y, int lane) {
+    using S = typename Prec<PREC>::S;
+    using C = typename Prec<PREC>::C;
+    constexpr bool kScaled = PREC == 2;
+    using Codec = StepCodec<S, V>;
+    const int x0 = (xblock * 32 + lane) * V;
+    const bool active = x0 < nx;
+    int ym = y - 1, yp = y + 1;
+    bool bm = false, bp = false;
+    if (WALLY) {
+        bm = ym < 0;
+        bp = yp >= ny;
+    } else {
+        if (ym < 0) ym += ny;
+        if (yp >= ny) yp -= ny;
+    }
+    const int xl = (x0 == 0) ? nx - 1 : x0 - 1;
+    const int xr = (x0 + V >= nx) ? x0 + V - nx : x0 + V;
+    const bool right_by_shfl = (lane < 31) && (x0 + V < nx);
+    const long long rowy = (long long)y * pitch;
+
+    auto slot_row = [&](int p) -> S* {  // the cells slot p reads and writes
+        const int cy = pcy(p);
+        const bool bounce = WALLY && (cy > 0 ? bm : (cy < 0 ? bp : false));
+        const int sy = cy > 0 ? ym : (cy < 0 ? yp : y);
+        return bounce ? buf + (long long)popp(p) * plane + rowy
+                      : buf + (long long)p * plane + (long long)sy * pitch;
+    };
+    auto slot_bounce = [&](int p) -> bool {
+        const int cy = pcy(p);
+        return WALLY && (cy > 0 ? bm : (cy < 0 ? bp : false));
+    };
+
+    // gather: all loads first, then the shuffles (as in step_row)
+    S r[kPlanes][V];
+    S edge[kPlanes];
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        const int cx = pcx(p);
+        const bool bounce = slot_bounce(p);
+        const S* row = slot_row(p);
+#pragma unroll
+        for (int k = 0; k < V; ++k) r[p][k] = S(0);
+        edge[p] = S(0);
+        if (active) VecRW<S, V>::load(row + x0, r[p]);
+        if (cx > 0 && !bounce && lane == 0 && active) edge[p] = row[xl];
+        if (cx < 0 && !bounce && !right_by_shfl && active) edge[p] = row[xr];
+    }
+    C v[kPlanes][V];
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        const int cx = pcx(p);
+        const bool bounce = slot_bounce(p);
+        C c[V];
+        Codec::to_compute(r[p], c);
+        if (cx == 0 || bounce) {
+#pragma unroll
+            for (int k = 0; k < V; ++k) v[p][k] = c[k];
+        } else if (cx > 0) {
+            C left = __shfl_up_sync(kFull, c[V - 1], 1);
+            if (lane == 0) left = Codec::template one<C>(edge[p]);
+            v[p][0] = left;
+#pragma unroll
+            for (int k = 1; k < V; ++k) v[p][k] = c[k - 1];
+        } else {
+            C right = __shfl_down_sync(kFull, c[0], 1);
+            if (!right_by_shfl) right = Codec::template one<C>(edge[p]);
+#pragma unroll
+            for (int k = 0; k < V - 1; ++k) v[p][k] = c[k + 1];
+            v[p][V - 1] = right;
+        }
+    }
+    // collide (inactive lanes hold zero deviations: a harmless rest state;
+    // they stay in the warp for the shuffles below)
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        C f[9], g[10];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = v[i][k];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) g[q] = v[9 + q][k];
+        collide_impl<false, C, kScaled>(f, g, np, nullptr);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) v[i][k] = f[i];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) v[9 + q][k] = g[q];
+    }
+    // write back: slot p's cells receive f*_opp(p) of the nodes that read them.
+    // A fresh copy of the base pointer makes the compiler recompute the 19
+    // slot addresses here instead of keeping them live across the collision.
+    S* wbuf;
+    asm volatile("mov.b64 %0, %1;" : "=l"(wbuf) : "l"(buf));
+    auto wslot_row = [&](int p) -> S* {
+        const int cy = pcy(p);
+        const bool bounce = WALLY && (cy > 0 ? bm : (cy < 0 ? bp : false));
+        const int sy = cy > 0 ? ym : (cy < 0 ? yp : y);
+        return bounce ? wbuf + (long long)popp(p) * plane + rowy
+                      : wbuf + (long long)p * plane + (long long)sy * pitch;
+    };
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        const int cx = pcx(p);
+        const bool bounce = slot_bounce(p);
+        S* row = wslot_row(p);
+        const int q = popp(p);
+        if (cx == 0 || bounce) {
+            S w[V];
+            Codec::to_storage(v[q], w);
+            if (active) VecRW<S, V>::store(row + x0, w, false, false);
+        } else if (cx > 0) {
+            // slot read x - 1: node x0+k owns cell x0+k-1
+            C u[V];
+#pragma unroll
+            for (int k = 0; k < V - 1; ++k) u[k] = v[q][k + 1];
+            u[V - 1] = __shfl_down_sync(kFull, v[q][0], 1);
+            S w[V];
+            Codec::to_storage(u, w);
+            if (active) VecRW<S, V>::store(row + x0, w, false, !right_by_shfl);
+            if (active && lane == 0) row[xl] = step_store_one(v[q][0], S());
+        } else {
+            // slot read x + 1: node x0+k owns cell x0+k+1
+            C u[V];
+            u[0] = __shfl_up_sync(kFull, v[q][V - 1], 1);
+#pragma unroll
+            for (int k = 1; k < V; ++k) u[k] = v[q][k - 1];
+            S w[V];
+            Codec::to_storage(u, w);
+            if (active) VecRW<S, V>::store(row + x0, w, lane == 0, false);
+            if (active && !right_by_shfl) row[xr] = step_store_one(v[q][V - 1], S());
+        }
+    }
+}
+
+// Phase B for one thread: V consecutive nodes of row y, all accesses local.
+template <int PREC, int V>
+__device__ __forceinline__ void aa_row_b(typename Prec<PREC>::S* buf, int nx, long long pitch,
+                                         long long plane,
+                                         const NodeParams<typename Prec<PREC>::C>& np, int xblock,
+                                         int y, int lane) {
+    using S = typename Prec<PREC>::S;
+    using C = typename Prec<PREC>::C;
+    constexpr bool kScaled = PREC == 2;
+    using Codec = StepCodec<S, V>;
+    const int x0 = (xblock * 32 + lane) * V;
+    if (x0 >= nx) return;
+    S* base = buf + (long long)y * pitch + x0;
+    S r[kPlanes][V];
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) VecRW<S, V>::load(base + (long long)p * plane, r[p]);
+    C v[kPlanes][V];  // v[q]: population q, read from plane opp(q)
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) Codec::to_compute(r[p], v[popp(p)]);
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        C f[9], g[10];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = v[i][k];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) g[q] = v[9 + q][k];
+        collide_impl<false, C, kScaled>(f, g, np, nullptr);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) v[i][k] = f[i];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) v[9 + q][k] = g[q];
+    }
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        S w[V];
+        Codec::to_storage(v[p], w);
+        VecRW<S, V>::store(base + (long long)p * plane, w, false, false);
+    }
+}
+
+}  // namespace mhd

@@ -1,0 +1,184 @@
+"""In-place (single-buffer) streaming against the two-buffer pull scheme
+and the FP64 oracle.
+
+The in-place pair of kernels evaluates the same collision on the same
+inputs as the pull step, so after any number of steps the canonical state
+read back (populations, raw state image) must be bitwise that of a
+two-buffer lattice with the same launch shape -- including after an odd
+number of steps, where the library first converts the streamed layout back.
+Sizes include ragged warps, a lattice narrower than one warp, y walls and
+every launch shape; all three storage precisions.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _fields(nx, ny, seed):
+    import mhd_inputs
+    return mhd_inputs.random_spectrum(nx, ny, seed, 0.03, 0.03, kmax=6)
+
+
+def _pair(nx, ny, prec, shape, wall_y=False, tau=(0.56, 0.71), variant=0):
+    from paper_2602_14667_gb300 import Lattice
+    a = Lattice(nx, ny, *tau, precision=prec, wall_y=wall_y, eq_variant=variant)
+    b = Lattice(nx, ny, *tau, precision=prec, wall_y=wall_y, eq_variant=variant, in_place=True)
+    a.kernel_config = shape
+    b.kernel_config = shape
+    f = _fields(nx, ny, nx + ny)
+    a.set_fields(*f)
+    b.set_fields(*f)
+    return a, b
+
+
+SHAPES = {"fp64": [(1, 1), (2, 8), (1, 8)], "fp32": [(1, 4), (2, 8), (4, 2), (4, 16)],
+          "fp16s": [(2, 2), (4, 2), (1, 8)]}
+CASES = [(p, s) for p in SHAPES for s in SHAPES[p]]
+
+
+@pytest.mark.parametrize("prec,shape", CASES, ids=lambda c: str(c))
+@pytest.mark.parametrize("nx,ny,wall_y", [(256, 24, False), (136, 20, True), (8, 6, False), (520, 9, True)])
+def test_in_place_equals_two_buffers_bitwise(prec, shape, nx, ny, wall_y):
+    if nx % shape[0]:
+        pytest.skip("nodes_per_thread must divide nx")
+    a, b = _pair(nx, ny, prec, shape, wall_y)
+    with a, b:
+        done = 0
+        for steps in (1, 2, 3, 64, 65, 131):
+            a.advance(steps - done)
+            b.advance(steps - done)
+            done = steps
+            fa, ga = a.get_populations()
+            fb, gb = b.get_populations()
+            assert np.array_equal(fa, fb) and np.array_equal(ga, gb), (prec, shape, steps)
+        sa, sb = a.get_state(), b.get_state()
+        assert np.array_equal(sa, sb)
+
+
+def test_in_place_one_step_matches_oracle_with_walls(orc):
+    from paper_2602_14667_gb300 import Lattice
+    nx, ny = 96, 40
+    p = orc.Params(nx, ny, 0.56, 0.71, wall_y=True, eq_variant=1)
+    rng = np.random.default_rng(3)
+    ux, uy, bx, by = (rng.uniform(-0.06, 0.06, (ny, nx)) for _ in range(4))
+    f, g = orc.init(p, ux, uy, bx, by, rho=rng.uniform(0.95, 1.05, (ny, nx)))
+    f = f + rng.normal(0, 3e-4, f.shape) * np.array([4 / 9] + [1 / 36, 1 / 9] * 4)[:, None, None]
+    g = g + rng.normal(0, 3e-4, g.shape)
+    fs, gs = orc.collide(p, f, g)
+    with Lattice(nx, ny, 0.56, 0.71, precision="fp64", wall_y=True, eq_variant=1, in_place=True) as lat:
+        lat.set_populations(fs, gs)
+        for k in (1, 2):
+            lat.advance(1)
+            fg, gg = lat.get_populations()
+            fs, gs = orc.collide(p, *orc.stream(p, fs, gs))
+            np.testing.assert_allclose(fg, fs, rtol=0, atol=1e-14, err_msg=f"step {k}")
+            np.testing.assert_allclose(gg, gs, rtol=0, atol=1e-14, err_msg=f"step {k}")
+
+
+@pytest.mark.parametrize("steps", [100, 101])
+def test_in_place_totals_and_fields_match_two_buffers(steps):
+    a, b = _pair(128, 96, "fp64", (2, 8))
+    with a, b:
+        a.advance(steps)
+        b.advance(steps)
+        ta, tb = a.get_totals(), b.get_totals()
+        fa, fb = a.get_fields(), b.get_fields()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+    # the two-buffer lattice gathers the pre-collision state for the totals,
+    # the in-place one recovers it from the stored post-collision state
+    for k, v in ta.items():
+        if k in ("mass", "mom_x", "mom_y", "bsum_x", "bsum_y", "step"):
+            assert abs(tb[k] - v) <= 1e-12 * 128 * 96, (k, v, tb[k])
+        else:
+            assert abs(tb[k] - v) <= 1e-10 * abs(v) + 1e-16, (k, v, tb[k])
+
+
+def test_checkpoint_from_in_place_into_two_buffers_and_back():
+    from paper_2602_14667_gb300 import Lattice
+    a, b = _pair(192, 64, "fp32", (2, 8))
+    with a, b:
+        a.advance(37)
+        b.advance(37)
+        img = b.get_state()                       # streamed layout: converted on the way out
+        with Lattice(192, 64, 0.56, 0.71, precision="fp32") as c, \
+                Lattice(192, 64, 0.56, 0.71, precision="fp32", in_place=True) as d:
+            c.kernel_config = (2, 8)
+            d.kernel_config = (2, 8)
+            c.set_state(img)
+            d.set_state(a.get_state())
+            for lat in (a, b, c, d):
+                lat.advance(29)
+            ref = a.get_state()
+            for lat in (b, c, d):
+                assert np.array_equal(lat.get_state(), ref)
+
+
+def test_in_place_autotune_keeps_state_and_graph_path():
+    a, b = _pair(512, 128, "fp32", (2, 8))
+    with a, b:
+        a.advance(7)
+        b.advance(7)
+        before = b.get_state()
+        shape = b.autotune()
+        assert shape == b.kernel_config
+        assert np.array_equal(b.get_state(), before)
+        a.kernel_config = shape
+        a.advance(200)                             # graphs of 64 steps plus singles, odd start
+        b.advance(200)
+        assert np.array_equal(a.get_state(), b.get_state())
+
+
+def test_in_place_uses_one_state_buffer():
+    import torch
+
+    from paper_2602_14667_gb300 import Lattice
+    n = 2048
+    torch.cuda.synchronize()
+    used = {}
+    for in_place in (False, True):
+        free0, _ = torch.cuda.mem_get_info()
+        lat = Lattice(n, n, 0.6, 0.6, precision="fp32", in_place=in_place)
+        free1, _ = torch.cuda.mem_get_info()
+        used[in_place] = free0 - free1
+        lat.close()
+    state = 19 * n * n * 4
+    assert used[False] >= 2 * state and used[True] < 1.1 * state + (64 << 20), used
+
+
+def test_in_place_rejections():
+    from paper_2602_14667_gb300 import Lattice, MhdError, _abi
+    with pytest.raises(MhdError):
+        Lattice(64, 64, 0.6, 0.6, precision="fp32", wall_x=True, in_place=True)
+    with _abi.MLP(seed=0, max_batch=64) as m, Lattice(64, 64, 0.6, 0.6, precision="fp32", in_place=True) as lat:
+        with pytest.raises(MhdError):
+            _abi.set_closure(lat, m)
+        lat.set_fields(*_fields(64, 64, 1))
+        lat.advance(2)
+        import torch
+        out = torch.empty((19, 16 * 16), dtype=torch.float32, device="cuda")
+        with pytest.raises(MhdError):
+            _abi.closure_filter(lat, 4, out)
+
+
+def test_in_place_orszag_tang_4096_bitwise_at_the_bench_shape():
+    """The benchmark's workload and launch shape, an odd step count."""
+    import json
+    import os
+
+    import mhd_inputs
+    from paper_2602_14667_gb300 import Lattice
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with open(os.path.join(root, "paper_2602_14667_gb300", "tune_cache.json")) as fh:
+        shape = tuple(json.load(fh)["NVIDIA GB300|p1|4096x4096|bc00"])
+    n = 4096
+    f = mhd_inputs.orszag_tang(n, 0.04, 0.04)
+    states = []
+    for in_place in (False, True):
+        with Lattice(n, n, 0.50006, 0.50006, precision="fp32", in_place=in_place) as lat:
+            lat.kernel_config = shape
+            lat.set_fields(*f)
+            lat.advance(601)
+            states.append(lat.get_state())
+    assert np.array_equal(states[0], states[1])

@@ -75,7 +75,7 @@ def test_noalloc_rejects_lattices_beyond_the_scratch():
 
     from paper_2602_14667_gb300 import MhdError, _abi
     dummy = torch.zeros(16, dtype=torch.float32, device="cuda")  # never read: rejected first
-    params = _abi.mhd_params(1.0, 0.6, 0.6, 0, 0, _abi.MHD_FP32, 0, 0, 0)
+    params = _abi.mhd_params(1.0, 0.6, 0.6, 0, 0, _abi.MHD_FP32, 0, 0, 0, 0)
     with pytest.raises(MhdError, match="too large"):
         _abi.totals_noalloc(dummy.data_ptr(), 4096, 4096, params)
     with pytest.raises(MhdError, match="EINVAL"):
