@@ -18,6 +18,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cstddef>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -53,6 +55,17 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
 }
 // two consecutive bf16 (4-byte aligned)
 __device__ __forceinline__ uint32_t ld2(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+// Four 8x8 bf16 matrices from shared memory in one instruction: lanes
+// 8m .. 8m+7 give the 16-byte-aligned row addresses of matrix m, and r[m]
+// receives this lane's share of matrix m in the mma fragment layout (row
+// lane/4, columns 2(lane%4), 2(lane%4)+1).
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const bf16* p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a)
+                 : "memory");
+}
 // two separate bf16
 __device__ __forceinline__ uint32_t ld11(const bf16* lo, const bf16* hi) {
     return (uint32_t)__bfloat16_as_ushort(*lo) | ((uint32_t)__bfloat16_as_ushort(*hi) << 16);
@@ -539,31 +552,42 @@ struct ClosureShared {
     float mean[kIn], scale[kIn], out_scale[kOut];
     float mom[4][kCHY][kCHX];
     float pop[kPlanes][kCTX * kCTY];  // the tile's pre-collision populations, parked during the MLP
-    bf16 feat[kCTX * kCTY * kFeatStride];
+    alignas(16) bf16 feat[kCTX * kCTY * kFeatStride];
     float da[kCTX * kCTY][kOut];
 };
+// ldmatrix reads 16-byte rows: the fragment sources and their row strides
+// must keep every row address 16-byte aligned.
+static_assert(offsetof(ClosureShared, Wt1) % 16 == 0 && offsetof(ClosureShared, Wt2) % 16 == 0 &&
+                  offsetof(ClosureShared, Wt3) % 16 == 0 && offsetof(ClosureShared, feat) % 16 == 0,
+              "ldmatrix sources must be 16-byte aligned");
+static_assert((kW1Stride * sizeof(bf16)) % 16 == 0 && (kW2Stride * sizeof(bf16)) % 16 == 0 &&
+                  (kFeatStride * sizeof(bf16)) % 16 == 0,
+              "ldmatrix row strides must be multiples of 16 bytes");
+static_assert(offsetof(ClosureShared, b1) % 8 == 0 && offsetof(ClosureShared, b2) % 8 == 0 &&
+                  offsetof(ClosureShared, b3) % 8 == 0,
+              "bias pairs are read as float2");
 
 // One warp evaluates the MLP for 16 nodes (rows m0..m0+15 of the feature
-// tile) and writes out_scale * y into sh.da.
+// tile) and writes out_scale * y into sh.da.  Fragments come from shared
+// memory by ldmatrix: the A fragment of a 16 x 16 k-chunk is matrices (rows
+// 0-7 | 8-15) x (k 0-7 | 8-15); one x4 load of a weight row block [n][k]
+// gives the B fragments of two consecutive k-chunks of an 8-wide n-tile.
 __device__ __forceinline__ void mlp_rows16(ClosureShared& sh, int m0, int lane) {
-    const int g = lane >> 2, t = lane & 3;
+    const int t = lane & 3, lr = lane & 7, lm = lane >> 3;
     uint32_t a1[2][4];
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        const bf16* r0 = sh.feat + (m0 + g) * kFeatStride + 16 * c + 2 * t;
-        const bf16* r1 = r0 + 8 * kFeatStride;
-        a1[c][0] = ld2(r0); a1[c][1] = ld2(r1); a1[c][2] = ld2(r0 + 8); a1[c][3] = ld2(r1 + 8);
-    }
+    for (int c = 0; c < 2; ++c)
+        ldsm_x4(a1[c], sh.feat + (m0 + lr + 8 * (lm & 1)) * kFeatStride + 16 * c + 8 * (lm >> 1));
     uint32_t h[4][4];  // layer input as A fragments (K = 64)
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        float d[4] = {sh.b1[8 * j + 2 * t], sh.b1[8 * j + 2 * t + 1], sh.b1[8 * j + 2 * t], sh.b1[8 * j + 2 * t + 1]};
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const uint32_t b[2] = {ld2(sh.Wt1 + (8 * j + g) * kW1Stride + 16 * c + 2 * t),
-                                   ld2(sh.Wt1 + (8 * j + g) * kW1Stride + 16 * c + 2 * t + 8)};
-            mma16816(d, a1[c], b);
-        }
+        const float2 bb = *reinterpret_cast<const float2*>(sh.b1 + 8 * j + 2 * t);
+        float d[4] = {bb.x, bb.y, bb.x, bb.y};
+        uint32_t w[4];
+        ldsm_x4(w, sh.Wt1 + (8 * j + lr) * kW1Stride + 8 * lm);
+        const uint32_t b0[2] = {w[0], w[1]}, b1[2] = {w[2], w[3]};
+        mma16816(d, a1[0], b0);
+        mma16816(d, a1[1], b1);
         // accumulator of n-tile j becomes half of k-chunk j/2 of the next A
         h[j >> 1][(j & 1) * 2 + 0] = pack2(fmaxf(d[0], 0.f), fmaxf(d[1], 0.f));
         h[j >> 1][(j & 1) * 2 + 1] = pack2(fmaxf(d[2], 0.f), fmaxf(d[3], 0.f));
@@ -571,26 +595,31 @@ __device__ __forceinline__ void mlp_rows16(ClosureShared& sh, int m0, int lane) 
     uint32_t h2[4][4];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        float d[4] = {sh.b2[8 * j + 2 * t], sh.b2[8 * j + 2 * t + 1], sh.b2[8 * j + 2 * t], sh.b2[8 * j + 2 * t + 1]};
+        const float2 bb = *reinterpret_cast<const float2*>(sh.b2 + 8 * j + 2 * t);
+        float d[4] = {bb.x, bb.y, bb.x, bb.y};
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const uint32_t a[4] = {h[c][0], h[c][1], h[c][2], h[c][3]};
-            const uint32_t b[2] = {ld2(sh.Wt2 + (8 * j + g) * kW2Stride + 16 * c + 2 * t),
-                                   ld2(sh.Wt2 + (8 * j + g) * kW2Stride + 16 * c + 2 * t + 8)};
-            mma16816(d, a, b);
+        for (int c = 0; c < 4; c += 2) {
+            uint32_t w[4];
+            ldsm_x4(w, sh.Wt2 + (8 * j + lr) * kW2Stride + 16 * c + 8 * lm);
+            const uint32_t b0[2] = {w[0], w[1]}, b1[2] = {w[2], w[3]};
+            mma16816(d, h[c], b0);
+            mma16816(d, h[c + 1], b1);
         }
         h2[j >> 1][(j & 1) * 2 + 0] = pack2(fmaxf(d[0], 0.f), fmaxf(d[1], 0.f));
         h2[j >> 1][(j & 1) * 2 + 1] = pack2(fmaxf(d[2], 0.f), fmaxf(d[3], 0.f));
     }
-    float d[4] = {sh.b3[2 * t], sh.b3[2 * t + 1], sh.b3[2 * t], sh.b3[2 * t + 1]};
+    const float2 bb = *reinterpret_cast<const float2*>(sh.b3 + 2 * t);
+    float d[4] = {bb.x, bb.y, bb.x, bb.y};
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const uint32_t a[4] = {h2[c][0], h2[c][1], h2[c][2], h2[c][3]};
-        const uint32_t b[2] = {ld2(sh.Wt3 + g * kW2Stride + 16 * c + 2 * t),
-                               ld2(sh.Wt3 + g * kW2Stride + 16 * c + 2 * t + 8)};
-        mma16816(d, a, b);
+    for (int c = 0; c < 4; c += 2) {
+        uint32_t w[4];
+        ldsm_x4(w, sh.Wt3 + lr * kW2Stride + 16 * c + 8 * lm);
+        const uint32_t b0[2] = {w[0], w[1]}, b1[2] = {w[2], w[3]};
+        mma16816(d, h2[c], b0);
+        mma16816(d, h2[c + 1], b1);
     }
     // d0: (row g, col 2t), d1: (g, 2t+1), d2: (g+8, 2t), d3: (g+8, 2t+1)
+    const int g = lane >> 2;
     if (2 * t < kOut) {
         sh.da[m0 + g][2 * t] = d[0] * sh.out_scale[2 * t];
         sh.da[m0 + g + 8][2 * t] = d[2] * sh.out_scale[2 * t];
@@ -601,7 +630,7 @@ __device__ __forceinline__ void mlp_rows16(ClosureShared& sh, int m0, int lane) 
     }
 }
 
-__global__ void __launch_bounds__(256, 3) step_closure(const StepArgs<float> a, const ClosureParamsDev cp,
+__global__ void __launch_bounds__(256, 2) step_closure(const StepArgs<float> a, const ClosureParamsDev cp,
                                                        int ntx, int ntiles) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ClosureShared& sh = *reinterpret_cast<ClosureShared*>(smem_raw);
