@@ -551,7 +551,10 @@ struct ClosureShared {
     float b1[kHid], b2[kHid], b3[kOutPad];
     float mean[kIn], scale[kIn], out_scale[kOut];
     float mom[4][kCHY][kCHX];
-    float pop[kPlanes][kCTX * kCTY];  // the tile's pre-collision populations, parked during the MLP
+    // pre-collision populations of the tile and of its halo ring, double
+    // buffered: cp.async fills one while the other tile is processed
+    float pop[2][kPlanes][kCTX * kCTY];
+    float hpop[2][kPlanes][kCHX * kCHY - kCTX * kCTY];
     alignas(16) bf16 feat[kCTX * kCTY * kFeatStride];
     float da[kCTX * kCTY][kOut];
 };
@@ -630,52 +633,119 @@ __device__ __forceinline__ void mlp_rows16(ClosureShared& sh, int m0, int lane) 
     }
 }
 
+// 4-byte asynchronous global -> shared copy (completes at cp_async_wait)
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// 16-byte asynchronous copy (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+// wait until at most N of this thread's committed groups are still in flight
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+constexpr int kHalo = kCHX * kCHY - kCTX * kCTY;  // 84 ring positions
+
+// Ring position h (0..83) of a tile: top row (34), bottom row (34), left
+// column (8), right column (8), as (column, row) of the 34 x 10 halo tile.
+__device__ __forceinline__ void ring_pos(int h, int& hx, int& hy) {
+    if (h < kCHX) { hx = h; hy = 0; }
+    else if (h < 2 * kCHX) { hx = h - kCHX; hy = kCHY - 1; }
+    else if (h < 2 * kCHX + kCTY) { hx = 0; hy = 1 + h - 2 * kCHX; }
+    else { hx = kCHX - 1; hy = 1 + h - 2 * kCHX - kCTY; }
+}
+
+// Issue the pull gather of tile tl (every thread its node, threads < 84 one
+// ring node; periodic) into buffer b, as one cp.async group.
+__device__ __forceinline__ void closure_prefetch(ClosureShared& sh, const float* src, const StepArgs<float>& a,
+                                                 int ntx, int tl, int b, int tid, int lane, int ly) {
+    const int x0 = (tl % ntx) * kCTX, y0 = (tl / ntx) * kCTY;
+    // a thread past the lattice edge gathers its periodic image: it is the
+    // neighbour of the last in-range nodes
+    const int x = (x0 + lane) % a.nx, y = (y0 + ly) % a.ny;
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        int sx = x - pcx(p), sy = y - pcy(p);
+        sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
+        sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
+        cp_async4(&sh.pop[b][p][tid], src + (long long)p * a.plane + (long long)sy * a.pitch + sx);
+    }
+    if (tid < kHalo) {
+        int hx, hy;
+        ring_pos(tid, hx, hy);
+        const int gx = ((x0 - 1 + hx) % a.nx + a.nx) % a.nx, gy = ((y0 - 1 + hy) % a.ny + a.ny) % a.ny;
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) {
+            int sx = gx - pcx(p), sy = gy - pcy(p);
+            sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
+            sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
+            cp_async4(&sh.hpop[b][p][tid], src + (long long)p * a.plane + (long long)sy * a.pitch + sx);
+        }
+    }
+    cp_async_commit();
+}
+
+// Persistent 32 x 8-node tiles.  The populations of the next tile are
+// gathered by cp.async into the other buffer while this tile's features,
+// MLP and collision run.
 __global__ void __launch_bounds__(256, 2) step_closure(const StepArgs<float> a, const ClosureParamsDev cp,
                                                        int ntx, int ntiles) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ClosureShared& sh = *reinterpret_cast<ClosureShared*>(smem_raw);
     const int tid = threadIdx.y * kCTX + threadIdx.x, lane = threadIdx.x, ly = threadIdx.y;
-    for (int i = tid; i < kHid * kInPad; i += 256) sh.Wt1[(i / kInPad) * kW1Stride + i % kInPad] = cp.Wt1[i];
-    for (int i = tid; i < kHid * kHid; i += 256) sh.Wt2[(i / kHid) * kW2Stride + i % kHid] = cp.Wt2[i];
-    for (int i = tid; i < kOutPad * kHid; i += 256) sh.Wt3[(i / kHid) * kW2Stride + i % kHid] = cp.Wt3[i];
-    for (int i = tid; i < kHid; i += 256) { sh.b1[i] = cp.b1[i]; sh.b2[i] = cp.b2[i]; }
+    const float* src = static_cast<const float*>(a.src);
+    float* dst = static_cast<float*>(a.dst);
+    // the network: weight rows in 16-byte pieces into the padded shared rows
+    // (issued together, ahead of the first tile's gather)
+    constexpr int kC1 = kInPad * 2 / 16, kC2 = kHid * 2 / 16;  // 16-byte pieces per weight row
+    for (int i = tid; i < kHid * kC1; i += 256)
+        cp_async16(sh.Wt1 + (i / kC1) * kW1Stride + (i % kC1) * 8, cp.Wt1 + (i / kC1) * kInPad + (i % kC1) * 8);
+    for (int i = tid; i < kHid * kC2; i += 256)
+        cp_async16(sh.Wt2 + (i / kC2) * kW2Stride + (i % kC2) * 8, cp.Wt2 + (i / kC2) * kHid + (i % kC2) * 8);
+    for (int i = tid; i < kOutPad * kC2; i += 256)
+        cp_async16(sh.Wt3 + (i / kC2) * kW2Stride + (i % kC2) * 8, cp.Wt3 + (i / kC2) * kHid + (i % kC2) * 8);
+    if (tid < kHid) { sh.b1[tid] = cp.b1[tid]; sh.b2[tid] = cp.b2[tid]; }
     if (tid < kOutPad) sh.b3[tid] = cp.b3[tid];
     if (tid < kIn) { sh.mean[tid] = cp.mean[tid]; sh.scale[tid] = cp.scale[tid]; }
     if (tid < kOut) sh.out_scale[tid] = cp.out_scale[tid];
-    const float* src = static_cast<const float*>(a.src);
-    float* dst = static_cast<float*>(a.dst);
-    constexpr int kHalo = kCHX * kCHY - kCTX * kCTY;  // 84 ring positions
-    for (int tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
-        __syncthreads();  // shared parameters loaded / previous tile done
+    // one group with the first tile's gather: the first wait covers both
+    if ((int)blockIdx.x < ntiles) closure_prefetch(sh, src, a, ntx, blockIdx.x, 0, tid, lane, ly);
+    else cp_async_commit();
+    int b = 0;
+    for (int tl = blockIdx.x; tl < ntiles; tl += gridDim.x, b ^= 1) {
+        const int next = tl + gridDim.x;
+        __syncthreads();  // the other buffer's previous tile is done; shared parameters loaded
+        if (next < ntiles) closure_prefetch(sh, src, a, ntx, next, b ^ 1, tid, lane, ly);
+        else cp_async_commit();  // empty group: keeps the wait count uniform
+        cp_async_wait<1>();      // this tile's group has landed (for this thread)
+        __syncthreads();         // ... and for every thread
         const int x0 = (tl % ntx) * kCTX, y0 = (tl / ntx) * kCTY;
         const int x = x0 + lane, y = y0 + ly;
         const bool inside = x < a.nx && y < a.ny;
-        // own node and (threads tid < 84) one ring node, loads issued together
-        float f[9], g[10], hf[9], hg[10];
-        // a thread past the lattice edge gathers its periodic image: it is the
-        // neighbour of the last in-range nodes
-        gather_node<float, float>(src, x % a.nx, y % a.ny, a.nx, a.ny, a.pitch, a.plane, 0, 0, f, g);
-        int hx = 0, hy = 0;
+        float f[9], g[10];
         if (tid < kHalo) {
-            // ring order: top row (34), bottom row (34), left column (8), right column (8)
-            if (tid < kCHX) { hx = tid; hy = 0; }
-            else if (tid < 2 * kCHX) { hx = tid - kCHX; hy = kCHY - 1; }
-            else if (tid < 2 * kCHX + kCTY) { hx = 0; hy = 1 + tid - 2 * kCHX; }
-            else { hx = kCHX - 1; hy = 1 + tid - 2 * kCHX - kCTY; }
-            const int gx = ((x0 - 1 + hx) % a.nx + a.nx) % a.nx, gy = ((y0 - 1 + hy) % a.ny + a.ny) % a.ny;
-            gather_node<float, float>(src, gx, gy, a.nx, a.ny, a.pitch, a.plane, 0, 0, hf, hg);
-            const Moments<float> m = moments(hf, hg, a.np.rho0);
+            int hx, hy;
+            ring_pos(tid, hx, hy);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = sh.hpop[b][i][tid];
+#pragma unroll
+            for (int q = 0; q < 10; ++q) g[q] = sh.hpop[b][9 + q][tid];
+            const Moments<float> m = moments(f, g, a.np.rho0);
             sh.mom[0][hy][hx] = m.ux; sh.mom[1][hy][hx] = m.uy;
             sh.mom[2][hy][hx] = m.bx; sh.mom[3][hy][hx] = m.by;
         }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = sh.pop[b][i][tid];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) g[q] = sh.pop[b][9 + q][tid];
         float feat[kIn];
         point_features(f, g, a.np.rho0, feat);
         sh.mom[0][ly + 1][lane + 1] = feat[1]; sh.mom[1][ly + 1][lane + 1] = feat[2];
         sh.mom[2][ly + 1][lane + 1] = feat[3]; sh.mom[3][ly + 1][lane + 1] = feat[4];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) sh.pop[i][tid] = f[i];
-#pragma unroll
-        for (int q = 0; q < 10; ++q) sh.pop[9 + q][tid] = g[q];
         __syncthreads();
         stencil_features<kCHX, kCHY>(sh.mom, lane, ly, feat + 8);
         bf16* row = sh.feat + tid * kFeatStride;
@@ -692,9 +762,9 @@ __global__ void __launch_bounds__(256, 2) step_closure(const StepArgs<float> a, 
         __syncwarp();
         if (inside) {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) f[i] = sh.pop[i][tid];
+            for (int i = 0; i < 9; ++i) f[i] = sh.pop[b][i][tid];
 #pragma unroll
-            for (int q = 0; q < 10; ++q) g[q] = sh.pop[9 + q][tid];
+            for (int q = 0; q < 10; ++q) g[q] = sh.pop[b][9 + q][tid];
             const float da[3] = {sh.da[tid][0], sh.da[tid][1], sh.da[tid][2]};
             collide_impl<true, float>(f, g, a.np, da);
             const long long o = (long long)y * a.pitch + x;
@@ -704,12 +774,16 @@ __global__ void __launch_bounds__(256, 2) step_closure(const StepArgs<float> a, 
             for (int q = 0; q < 10; ++q) dst[(long long)(9 + q) * a.plane + o] = g[q];
         }
     }
+    cp_async_wait<0>();  // nothing left in flight when the block exits
 }
 
 size_t closure_smem_bytes() { return sizeof(ClosureShared); }
 
 cudaError_t launch_step_closure(const StepLaunch& s, const ClosureParamsDev& cp, cudaStream_t st) {
     if (s.prec != 1 || s.wall_x || s.wall_y) return cudaErrorInvalidValue;
+    // the weight blocks are staged in 16-byte pieces
+    for (const void* w : {(const void*)cp.Wt1, (const void*)cp.Wt2, (const void*)cp.Wt3})
+        if (reinterpret_cast<uintptr_t>(w) % 16) return cudaErrorInvalidValue;
     StepArgs<float> a;
     a.src = s.src;
     a.dst = s.dst;
