@@ -519,10 +519,12 @@ def run_closure_step(args):
     prm = mlp.get_params()
     prm[48:51] = 1e-7                       # small output scale: a stable, non-trivial correction
     mlp.set_params(prm)
-    for name in ("plain", "closure"):
+    for name in ("plain", "closure", "closure_tcgen05"):
         with Lattice(n, n, 0.505, 0.505, precision="fp32", stream=stream.cuda_stream) as lat:
-            if name == "closure":
+            if name != "plain":
                 _abi.set_closure(lat, mlp)
+                _abi.set_closure_kernel(lat, _abi.MHD_CLOSURE_TCGEN05 if name == "closure_tcgen05"
+                                        else _abi.MHD_CLOSURE_WARP_MMA)
             lat.set_fields(*fields)
             lat.advance(args.warmup)
             stream.synchronize()
@@ -539,13 +541,17 @@ def run_closure_step(args):
     # cores, FP32 accumulation); its state (2 x 19 planes FP32, 40 MB at
     # 512^2) stays in L2 across steps.  Peak: the measured dense BF16 burst.
     flops = 2 * (24 * 64 + 64 * 64 + 64 * 3) * n * n
-    achieved = flops / (out["closure"] * 1e-3) / 1e12
+    # the closure kernel autotune would keep: the faster of the two
+    best_kind = "closure" if out["closure"] <= out["closure_tcgen05"] else "closure_tcgen05"
+    achieved = flops / (out[best_kind] * 1e-3) / 1e12
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
         peak = float(json.load(fh)["bf16_tflops"])
-    res = {"metric": "closure step cost (512^2 coarse lattice)", "value": out["closure"] / out["plain"],
+    res = {"metric": "closure step cost (512^2 coarse lattice)", "value": out[best_kind] / out["plain"],
            "unit": "closure / plain time per step", "higher_is_better": False, "n_gpus": 1,
            "ms_per_step": out, "mlups": {k: n * n / (v * 1e-3) / 1e6 for k, v in out.items()},
-           "config": {"workload": f"closure_step_{n}x{n}_fp32", "tau": 0.505}, "data": "synthetic",
+           "config": {"workload": f"closure_step_{n}x{n}_fp32", "tau": 0.505,
+                      "closure_kernel": "warp_mma" if best_kind == "closure" else "tcgen05"},
+           "data": "synthetic",
            "steps": args.steps, "warmup": args.warmup,
            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                         "frac": achieved / peak, "peak_source": "measured bf16 dense (burst)",

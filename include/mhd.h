@@ -349,6 +349,19 @@ mhd_status mhd_set_precollision_state(mhd_lattice* l, const float* state);
  * current parameters (the MLP may be destroyed afterwards), or back to the
  * plain scheme with mlp = NULL.  FP32 storage and periodic axes only. */
 mhd_status mhd_set_closure(mhd_lattice* l, const mhd_mlp* mlp);
+/* The kernel that evaluates the closure MLP inside the step (an
+ * implementation choice with no counterpart in the paper; the results agree
+ * to BF16 rounding of the summation order):
+ *   MHD_CLOSURE_WARP_MMA: warp-level mma.sync BF16 fragments, activations kept
+ *     in registers between layers (the default);
+ *   MHD_CLOSURE_TCGEN05: 5th-generation tensor cores, two M = 128 MMAs per
+ *     32 x 8-node tile issued by one thread, accumulators in tensor memory.
+ * mhd_autotune on a lattice with a closure times both and keeps the faster.
+ * A tcgen05 wait that gives up (after ~0.1 s) is reported as MHD_ECUDA by the
+ * next read of fields, totals, populations or state. */
+typedef enum { MHD_CLOSURE_WARP_MMA = 0, MHD_CLOSURE_TCGEN05 = 1 } mhd_closure_kernel;
+mhd_status mhd_set_closure_kernel(mhd_lattice* l, int kind);
+mhd_status mhd_get_closure_kernel(const mhd_lattice* l, int* kind);
 
 #ifdef __cplusplus
 }

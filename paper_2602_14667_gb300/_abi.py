@@ -95,6 +95,8 @@ _SIGNATURES = {
     "mhd_closure_features": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P],
     "mhd_closure_targets": [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P, _P],
     "mhd_set_precollision_state": [_P, _P],
+    "mhd_set_closure_kernel": [_P, ctypes.c_int],
+    "mhd_get_closure_kernel": [_P, ctypes.POINTER(ctypes.c_int)],
     "mhd_closure_sgs_targets": [_P, ctypes.c_int, ctypes.c_double, _P],
     "mhd_set_closure": [_P, _P],
     "mhd_get_state": [_P, _P, ctypes.c_size_t],
@@ -444,6 +446,20 @@ def closure_sgs_targets(lattice: "Lattice", factor: int, tau_coarse: float, out)
 
 def set_precollision_state(lattice: "Lattice", state):
     check(lib().mhd_set_precollision_state(lattice.handle, _ptr(state)), "mhd_set_precollision_state")
+
+
+MHD_CLOSURE_WARP_MMA, MHD_CLOSURE_TCGEN05 = range(2)
+
+
+def set_closure_kernel(lattice: "Lattice", kind: int):
+    """MLP kernel of the closure step: MHD_CLOSURE_WARP_MMA or MHD_CLOSURE_TCGEN05."""
+    check(lib().mhd_set_closure_kernel(lattice.handle, int(kind)), "mhd_set_closure_kernel")
+
+
+def get_closure_kernel(lattice: "Lattice") -> int:
+    k = ctypes.c_int()
+    check(lib().mhd_get_closure_kernel(lattice.handle, ctypes.byref(k)), "mhd_get_closure_kernel")
+    return k.value
 
 
 def set_closure(lattice: "Lattice", mlp):

@@ -72,6 +72,7 @@ struct mhd_lattice {
     mhd_kernel_config cfg{1, 8};
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     void* closure_buf = nullptr;  // lattice-owned copy of the closure's inference parameters
+    int closure_kind = MHD_CLOSURE_WARP_MMA;
     mhd::ClosureParamsDev closure{};
 
     long long n() const { return (long long)nx * ny; }
@@ -101,7 +102,9 @@ mhd::StepLaunch step_launch(const mhd_lattice* l, int from) {
 
 cudaError_t launch_lattice_step(const mhd_lattice* l, int from, cudaStream_t st) {
     const mhd::StepLaunch s = step_launch(l, from);
-    if (l->closure_buf) return mhd::launch_step_closure(s, l->closure, st);
+    if (l->closure_buf)
+        return l->closure_kind == MHD_CLOSURE_TCGEN05 ? mhd::launch_step_closure_tc(s, l->closure, st)
+                                                      : mhd::launch_step_closure(s, l->closure, st);
     return mhd::launch_step(s, st);
 }
 
@@ -112,6 +115,16 @@ cudaError_t launch_inplace_step(const mhd_lattice* l, void* buf, int phase, cuda
     s.src = buf;
     s.dst = buf;
     return mhd::launch_aa_step(s, phase, st);
+}
+
+// A closure step whose tensor-core wait gave up leaves a flag behind.
+mhd_status closure_status(mhd_lattice* l) {
+    if (!l->closure_buf || !l->closure.err) return MHD_OK;
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, l->closure.err, sizeof(int), cudaMemcpyDeviceToHost, l->stream), "closure status");
+    CK(cudaStreamSynchronize(l->stream), "closure status");
+    if (err) return fail(MHD_ECUDA, "closure step: a tensor-core MMA did not complete (wait limit reached)");
+    return MHD_OK;
 }
 
 // Bring an in-place lattice to the canonical layout (same time step).
@@ -379,6 +392,10 @@ mhd_status mhd_get_fields(mhd_lattice* l, double* rho, double* ux, double* uy, d
     if (!l->fields_set) return fail(MHD_ESTATE, "set fields or populations first");
     CK(cudaSetDevice(l->dev), "cudaSetDevice");
     CK(normalize(l), "unstream kernel");
+    {
+        const mhd_status cs = closure_status(l);
+        if (cs != MHD_OK) return cs;
+    }
     mhd_status s = ensure_io(l);
     if (s != MHD_OK) return s;
     const long long n = l->n();
@@ -401,6 +418,10 @@ mhd_status mhd_get_totals(mhd_lattice* l, mhd_totals* out) {
     if (!l->fields_set) return fail(MHD_ESTATE, "set fields or populations first");
     CK(cudaSetDevice(l->dev), "cudaSetDevice");
     CK(normalize(l), "unstream kernel");
+    {
+        const mhd_status cs = closure_status(l);
+        if (cs != MHD_OK) return cs;
+    }
     mhd::DiagLaunch d;
     d.L = l->L;
     d.prec = l->p.precision;
@@ -445,6 +466,10 @@ mhd_status mhd_get_populations(mhd_lattice* l, double* f, double* g) {
     if (!l->fields_set) return fail(MHD_ESTATE, "set fields or populations first");
     CK(cudaSetDevice(l->dev), "cudaSetDevice");
     CK(normalize(l), "unstream kernel");
+    {
+        const mhd_status cs = closure_status(l);
+        if (cs != MHD_OK) return cs;
+    }
     mhd_status s = ensure_io(l);
     if (s != MHD_OK) return s;
     const long long n = l->n();
@@ -497,7 +522,8 @@ mhd_status mhd_set_closure(mhd_lattice* l, const mhd_mlp* mlp) {
     using namespace mhd;
     const size_t nbf = (size_t)kHid * kInPad + (size_t)kHid * kHid + (size_t)kOutPad * kHid;
     const size_t nfl = 2 * kHid + kOutPad + 2 * kIn + kOut;
-    const size_t bytes = nbf * sizeof(__nv_bfloat16) + nfl * sizeof(float);
+    const size_t err_off = (nbf * sizeof(__nv_bfloat16) + nfl * sizeof(float) + 15) / 16 * 16;
+    const size_t bytes = err_off + 16;
     if (!l->closure_buf) CK(cudaMalloc(&l->closure_buf, bytes), "cudaMalloc(closure)");
     ClosureParamsDev src;
     mhd_internal_closure_params(mlp, &src);
@@ -513,6 +539,8 @@ mhd_status mhd_set_closure(mhd_lattice* l, const mhd_mlp* mlp) {
     cp.mean = fl + 2 * kHid + kOutPad;
     cp.scale = fl + 2 * kHid + kOutPad + kIn;
     cp.out_scale = fl + 2 * kHid + kOutPad + 2 * kIn;
+    cp.err = reinterpret_cast<int*>(static_cast<char*>(l->closure_buf) + err_off);
+    CK(cudaMemsetAsync(cp.err, 0, sizeof(int), l->stream), "clear closure status");
     struct { const void* s; const void* d; size_t b; } parts[] = {
         {src.Wt1, cp.Wt1, sizeof(__nv_bfloat16) * kHid * kInPad},
         {src.Wt2, cp.Wt2, sizeof(__nv_bfloat16) * kHid * kHid},
@@ -527,6 +555,24 @@ mhd_status mhd_set_closure(mhd_lattice* l, const mhd_mlp* mlp) {
         CK(cudaMemcpyAsync(const_cast<void*>(q.d), q.s, q.b, cudaMemcpyDeviceToDevice, l->stream), "copy closure");
     CK(cudaStreamSynchronize(l->stream), "mhd_set_closure");
     drop_graphs(l);
+    return MHD_OK;
+}
+
+mhd_status mhd_set_closure_kernel(mhd_lattice* l, int kind) {
+    if (!l) return fail(MHD_EINVAL, "lattice is NULL");
+    if (kind != MHD_CLOSURE_WARP_MMA && kind != MHD_CLOSURE_TCGEN05) return fail(MHD_EINVAL, "unknown closure kernel");
+    if (kind != l->closure_kind) {
+        CK(cudaSetDevice(l->dev), "cudaSetDevice");
+        CK(cudaStreamSynchronize(l->stream), "mhd_set_closure_kernel");
+        drop_graphs(l);
+        l->closure_kind = kind;
+    }
+    return MHD_OK;
+}
+
+mhd_status mhd_get_closure_kernel(const mhd_lattice* l, int* kind) {
+    if (!l || !kind) return fail(MHD_EINVAL, "NULL argument");
+    *kind = l->closure_kind;
     return MHD_OK;
 }
 
@@ -584,6 +630,10 @@ mhd_status mhd_get_state(mhd_lattice* l, void* host, size_t bytes) {
     if (!l->fields_set) return fail(MHD_ESTATE, "set fields or populations first");
     CK(cudaSetDevice(l->dev), "cudaSetDevice");
     CK(normalize(l), "unstream kernel");
+    {
+        const mhd_status cs = closure_status(l);
+        if (cs != MHD_OK) return cs;
+    }
     const size_t es = l->L.esize, row = (size_t)l->nx * es;
     for (int p = 0; p < mhd::kStatePlanes; ++p) {
         char* dst = static_cast<char*>(host) + (size_t)p * l->n() * es;
@@ -634,9 +684,47 @@ mhd_status mhd_set_kernel_config(mhd_lattice* l, const mhd_kernel_config* cfg) {
     return MHD_OK;
 }
 
+// With a closure the step is the closure kernel (fixed 32 x 8-node tiles):
+// time its two MLP kernels (reading the current buffer, writing the spare
+// one) and keep the faster.
+static mhd_status autotune_closure(mhd_lattice* l, mhd_kernel_config* best) {
+    CK(cudaStreamSynchronize(l->stream), "mhd_autotune");
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    const mhd::StepLaunch s = step_launch(l, l->cur);
+    float ms[2] = {0.f, 0.f};
+    cudaError_t err = cudaSuccess;
+    for (int kind = 0; kind < 2 && err == cudaSuccess; ++kind) {
+        auto one = [&]() {
+            return kind == MHD_CLOSURE_TCGEN05 ? mhd::launch_step_closure_tc(s, l->closure, l->stream)
+                                               : mhd::launch_step_closure(s, l->closure, l->stream);
+        };
+        for (int k = 0; k < 3 && err == cudaSuccess; ++k) err = one();
+        if (err == cudaSuccess) err = cudaEventRecord(e0, l->stream);
+        for (int k = 0; k < 20 && err == cudaSuccess; ++k) err = one();
+        if (err == cudaSuccess) err = cudaEventRecord(e1, l->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms[kind], e0, e1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return cuda_fail(err, "closure autotune");
+    l->prev_valid = false;  // the spare buffer was overwritten
+    mhd_status st = closure_status(l);
+    if (st != MHD_OK) return st;
+    if (getenv("MHD_TUNE_VERBOSE"))
+        fprintf(stderr, "mhd_autotune closure %dx%d: warp-MMA %.4f ms/step, tcgen05 %.4f ms/step\n", l->nx, l->ny,
+                ms[0] / 20, ms[1] / 20);
+    st = mhd_set_closure_kernel(l, ms[1] < ms[0] ? MHD_CLOSURE_TCGEN05 : MHD_CLOSURE_WARP_MMA);
+    if (best) *best = l->cfg;
+    return st;
+}
+
 mhd_status mhd_autotune(mhd_lattice* l, mhd_kernel_config* best) {
     if (!l) return fail(MHD_EINVAL, "lattice is NULL");
     CK(cudaSetDevice(l->dev), "cudaSetDevice");
+    if (l->closure_buf) return autotune_closure(l, best);
     const char* path = getenv("MHD_TUNE_CACHE");
     const std::string key = cache_key(l);
     if (path) {

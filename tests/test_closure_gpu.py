@@ -194,7 +194,11 @@ def test_training_reduces_the_loss():
     assert loss < 0.05 * loss0, (loss0, loss)
 
 
-def test_closure_step_matches_oracle(orc):
+KINDS = pytest.mark.parametrize("kind", [0, 1], ids=["warp_mma", "tcgen05"])
+
+
+@KINDS
+def test_closure_step_matches_oracle(orc, kind):
     import torch
 
     from oracle import closure as clo
@@ -210,6 +214,8 @@ def test_closure_step_matches_oracle(orc):
         m.set_params(net.flat())
         ref_net = clo.MLP.from_flat(m.get_params())
         _abi.set_closure(lat, m)
+        _abi.set_closure_kernel(lat, kind)
+        assert _abi.get_closure_kernel(lat) == kind
         _abi.set_precollision_state(lat, st)
         lat.advance(1)
         fg, gg = lat.get_populations()
@@ -221,7 +227,8 @@ def test_closure_step_matches_oracle(orc):
     assert np.abs(fg - fs).max() < 3e-6 and np.abs(gg - gs).max() < 2e-6   # ... and matched
 
 
-def test_closure_keeps_mass_and_momentum():
+@KINDS
+def test_closure_keeps_mass_and_momentum(kind):
     import mhd_inputs
     from oracle import closure as clo
     from paper_2602_14667_gb300 import Lattice, _abi
@@ -231,6 +238,7 @@ def test_closure_keeps_mass_and_momentum():
     with _abi.MLP(seed=0, max_batch=64) as m, Lattice(n, n, 0.52, 0.55, precision="fp32") as lat:
         m.set_params(net.flat())
         _abi.set_closure(lat, m)
+        _abi.set_closure_kernel(lat, kind)
         lat.set_fields(*mhd_inputs.random_spectrum(n, n, 9, 0.03, 0.03))
         t0 = lat.get_totals()
         lat.advance(200)
@@ -239,3 +247,38 @@ def test_closure_keeps_mass_and_momentum():
         lat.advance(10)
     assert abs(t1["mass"] - t0["mass"]) < 1e-6 * n * n
     assert abs(t1["mom_x"] - t0["mom_x"]) < 1e-6 * n * n and abs(t1["mom_y"] - t0["mom_y"]) < 1e-6 * n * n
+
+
+def test_closure_kernels_agree_and_autotune_picks_one():
+    """The two MLP kernels of the closure step (warp-level MMA and tcgen05)
+    differ only in the BF16 summation order: after 60 steps of a 200 x 136
+    lattice (ragged tiles) their fields agree to 1e-5.  autotune selects one
+    of them and leaves the state alone."""
+    import mhd_inputs
+    from oracle import closure as clo
+    from paper_2602_14667_gb300 import Lattice, _abi
+    nx, ny = 200, 136
+    net = clo.MLP(seed=6)
+    net.p["out_scale"][:] = 2e-5
+    fields = mhd_inputs.random_spectrum(nx, ny, 21, 0.03, 0.03)
+    out = []
+    with _abi.MLP(seed=0, max_batch=64) as m:
+        m.set_params(net.flat())
+        for kind in (0, 1):
+            with Lattice(nx, ny, 0.53, 0.56, precision="fp32") as lat:
+                _abi.set_closure(lat, m)
+                _abi.set_closure_kernel(lat, kind)
+                lat.set_fields(*fields)
+                lat.advance(60)
+                out.append(lat.get_fields())
+        with Lattice(nx, ny, 0.53, 0.56, precision="fp32") as lat:
+            _abi.set_closure(lat, m)
+            lat.set_fields(*fields)
+            lat.advance(3)
+            before = lat.get_state()
+            lat.autotune()
+            assert _abi.get_closure_kernel(lat) in (0, 1)
+            assert np.array_equal(lat.get_state(), before)
+    for k in ("ux", "uy", "bx", "by"):
+        err = np.linalg.norm(out[0][k] - out[1][k]) / np.linalg.norm(out[0][k])
+        assert err < 1e-5, (k, err)
