@@ -96,9 +96,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(prec, n, shape):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken
-    from the current kernel sources with the same launch shape (else None)."""
+def profiled(prec, shape, key):
+    """A per-node figure from a committed ncu summary, if it was taken from
+    the current kernel sources with the same launch shape (else None)."""
     path = os.path.join(ROOT, "profiles", f"rr_step_{prec}_ncu.md")
     if not os.path.exists(path):
         return None
@@ -113,10 +113,20 @@ def profiled_traffic(prec, n, shape):
     if vals.get("shape") != f"{shape[0]},{shape[1]}":
         return None
     try:
-        per_node = float(vals["dram_bytes_per_node"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
-    return per_node * n * n
+
+
+def profiled_traffic(prec, n, shape):
+    """DRAM bytes per launch (see profiled)."""
+    per_node = profiled(prec, shape, "dram_bytes_per_node")
+    return None if per_node is None else per_node * n * n
+
+
+# FP64 units of a GB300: 2 DFMA per clock per SM (ncu peak_sustained: 304 per
+# cycle on 152 SMs) at the 2070 MHz maximum SM clock
+FP64_INSTR_PEAK = 304 * 2.07e9
 
 
 class ClockSampler:
@@ -368,15 +378,27 @@ def run_gb300(args):
                 "l2": (f"no flush: the {nbuf} x 19-plane state ({nbuf * 19 * n * n * ESIZE[prec] / 1e9:.2f} GB "
                        f"{prec.upper()}) is far above the 129 MB L2"),
                 "stable": stable, "replicas": world})
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "frac_of_nominal_8tbs": achieved / 8000.0,
+                "bytes_per_node": BYTES_PER_NODE[prec],
+                "traffic": traffic}
+    fl = profiled(prec, shape, "fp64_flops_per_node") if prec == "fp64" else None
+    ins = profiled(prec, shape, "fp64_instructions_per_node") if prec == "fp64" else None
+    if fl is not None and ins is not None:
+        # FP64 on GB300 is bound by the FP64 units, not by HBM
+        rate = nodes / per_launch_s
+        roofline = {"bound": "alu", "achieved": fl * rate / 1e12, "peak": 2 * FP64_INSTR_PEAK / 1e12,
+                    "unit": "TFLOP/s", "frac": fl * rate / (2 * FP64_INSTR_PEAK),
+                    "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2 flop",
+                    "fp64_flops_per_node": fl, "fp64_instructions_per_node": ins,
+                    "fp64_pipe_frac": ins * rate / FP64_INSTR_PEAK,
+                    "hbm_frac": achieved / peak, "traffic": traffic}
     out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
            "config": cfg,
-           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "peak_source": peak_kind,
-                        "frac_of_nominal_8tbs": achieved / 8000.0,
-                        "bytes_per_node": BYTES_PER_NODE[prec],
-                        "traffic": traffic},
+           "roofline": roofline,
            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
            "clocks": clk.summary()}
     if tot is not None:
