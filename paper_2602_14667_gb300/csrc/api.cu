@@ -3,6 +3,7 @@
 // the step loop, diagnostics, checkpointing and the launch-shape autotuner.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -44,6 +45,20 @@ bool finite_array(const double* a, long long n) {
     return true;
 }
 
+// Input check of mhd_set_fields on the device copies: bit 0 of *flags for a
+// non-finite field value, bit 1 for rho <= 0 (or non-finite rho).
+__global__ void check_fields_kernel(const double* ux, const double* uy, const double* bx, const double* by,
+                                    const double* rho, long long n, int* flags) {
+    int f = 0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        if (!(isfinite(ux[k]) && isfinite(uy[k]) && isfinite(bx[k]) && isfinite(by[k]))) f |= 1;
+        if (rho) f |= !isfinite(rho[k]) ? 1 : (rho[k] > 0 ? 0 : 2);
+    }
+    f = __reduce_or_sync(0xffffffffu, f);
+    if ((threadIdx.x & 31) == 0 && f) atomicOr(flags, f);
+}
+
 }  // namespace
 
 void mhd::set_last_error(const std::string& msg) { g_err = msg; }
@@ -69,6 +84,7 @@ struct mhd_lattice {
     double* partials = nullptr;
     double* totals_d = nullptr;
     double* totals_h = nullptr;  // pinned
+    int* flags_d = nullptr;      // device word of the input checks
     mhd_kernel_config cfg{1, 8};
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     void* closure_buf = nullptr;  // lattice-owned copy of the closure's inference parameters
@@ -254,6 +270,7 @@ mhd_status mhd_create(int nx, int ny, const mhd_params* p, void* stream, mhd_lat
         e = cudaMalloc(&l->partials, sizeof(double) * mhd::kDiagSlots * mhd::diag_blocks(l->L));
     if (e == cudaSuccess) e = cudaMalloc(&l->totals_d, sizeof(double) * mhd::kDiagSlots);
     if (e == cudaSuccess) e = cudaMallocHost(&l->totals_h, sizeof(double) * mhd::kDiagSlots);
+    if (e == cudaSuccess) e = cudaMalloc(&l->flags_d, 16);
     if (e != cudaSuccess) {
         cudaGetLastError();
         mhd_destroy(l);
@@ -284,6 +301,7 @@ mhd_status mhd_destroy(mhd_lattice* l) {
     if (l->partials) cudaFree(l->partials);
     if (l->totals_d) cudaFree(l->totals_d);
     if (l->totals_h) cudaFreeHost(l->totals_h);
+    if (l->flags_d) cudaFree(l->flags_d);
     if (l->cap) cudaStreamDestroy(l->cap);
     delete l;
     return MHD_OK;
@@ -293,11 +311,6 @@ mhd_status mhd_set_fields(mhd_lattice* l, const double* ux, const double* uy, co
                           const double* by, const double* rho) {
     if (!l || !ux || !uy || !bx || !by) return fail(MHD_EINVAL, "NULL argument");
     const long long n = l->n();
-    for (const double* a : {ux, uy, bx, by, rho})
-        if (a && !finite_array(a, n)) return fail(MHD_EINVAL, "non-finite input field");
-    if (rho)
-        for (long long k = 0; k < n; ++k)
-            if (!(rho[k] > 0)) return fail(MHD_EINVAL, "rho must be > 0");
     CK(cudaSetDevice(l->dev), "cudaSetDevice");
     mhd_status s = ensure_io(l);
     if (s != MHD_OK) return s;
@@ -306,6 +319,19 @@ mhd_status mhd_set_fields(mhd_lattice* l, const double* ux, const double* uy, co
     const double* h[5] = {ux, uy, bx, by, rho};
     for (int q = 0; q < 5; ++q)
         if (h[q]) CK(cudaMemcpyAsync(d[q], h[q], bytes, cudaMemcpyHostToDevice, l->stream), "H2D fields");
+    // the inputs are checked on the device copies, before the state is touched
+    {
+        int flags = 0;
+        CK(cudaMemsetAsync(l->flags_d, 0, sizeof(int), l->stream), "clear input flags");
+        const long long blocks = std::max(1LL, std::min((n + 255) / 256, 152LL * 8));
+        check_fields_kernel<<<(unsigned)blocks, 256, 0, l->stream>>>(d[0], d[1], d[2], d[3], rho ? d[4] : nullptr, n,
+                                                                      l->flags_d);
+        CK(cudaGetLastError(), "input check kernel");
+        CK(cudaMemcpyAsync(&flags, l->flags_d, sizeof(int), cudaMemcpyDeviceToHost, l->stream), "input flags");
+        CK(cudaStreamSynchronize(l->stream), "mhd_set_fields");
+        if (flags & 1) return fail(MHD_EINVAL, "non-finite input field");
+        if (flags & 2) return fail(MHD_EINVAL, "rho must be > 0");
+    }
     CK(mhd::launch_init(l->L, l->p.precision, l->buf[l->cur], rho ? d[4] : nullptr, d[0], d[1], d[2],
                         d[3], l->p.rho0, l->p.eq_variant, l->stream),
        "init kernel");

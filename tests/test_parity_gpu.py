@@ -324,6 +324,15 @@ def test_errors_are_reported():
         bad = z.copy(); bad[2, 3] = np.nan
         with pytest.raises(MhdError, match="EINVAL"):
             lat.set_fields(bad, z, z, z)
+        with pytest.raises(MhdError, match="ESTATE"):   # a rejected set leaves no fields
+            lat.advance(1)
+        lat.set_fields(z + 0.01, z, z, z)
+        lat.advance(3)
+        before = lat.get_state()
+        for rho in (z, z + np.inf, np.where(bad == bad, 1.0, np.nan)):
+            with pytest.raises(MhdError, match="EINVAL"):
+                lat.set_fields(z, z, z, z, rho=rho)
+        assert np.array_equal(lat.get_state(), before)  # ... and leaves the state alone
         with pytest.raises(MhdError, match="EINVAL"):
             lat.kernel_config = (3, 4)
         with pytest.raises(MhdError, match="EINVAL"):
