@@ -481,6 +481,20 @@ def run_ensemble(args):
         dist.destroy_process_group()
 
 
+def training_rate(res):
+    """Throughput of the GPU training (fit_normalisation excluded): samples
+    per second over all epochs, and the MLP's algorithmic tensor work --
+    forward 11,648 flop per sample, backward twice that (input and weight
+    gradients) -- against the measured dense BF16 peak."""
+    per_sample = 3 * 2 * (24 * 64 + 64 * 64 + 64 * 3)
+    rate = res["samples"] * res["epochs"] / res["train_s"]
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+        peak = float(json.load(fh)["bf16_tflops"])
+    tflops = rate * per_sample / 1e12
+    return {"samples_per_s": rate, "seconds": res["train_s"], "epochs": res["epochs"],
+            "flop_per_sample": per_sample, "tflops": tflops, "frac_of_bf16_peak": tflops / peak}
+
+
 def run_closure(args):
     """The learned-closure workload: 2048^2 fine runs (random-spectrum fields,
     rms 0.03) filtered 4x onto 512^2; MLP trained on the GPU on ~2 M samples
@@ -517,6 +531,7 @@ def run_closure(args):
            "closure": {str(k): res["closure"][k] for k in cfg.eval_coarse_steps} if "closure" in res else None,
            "spectrum_error": {"plain": sp, "closure": sc}, "current_error": {"plain": jp, "closure": jc},
            "s_per_coarse_step": {"plain": cost_p, "closure": cost_c},
+           "training": training_rate(res),
            "equal_gpu_time_note": "a plain run at the next finer grid the fine run can be filtered to "
                                   "(1024^2) costs 8x the plain 512^2 run",
            "wall_s": wall}

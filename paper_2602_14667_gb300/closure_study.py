@@ -256,12 +256,17 @@ def evaluate(cfg: StudyConfig, mlp=None, seed=None):
 def run(cfg: StudyConfig | None = None) -> dict:
     """Data from the training seeds, GPU training, a posteriori calibration
     on the first training seed, evaluation on the held-out seed."""
+    import torch
     cfg = cfg or StudyConfig()
     X, T = generate_data(cfg)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     mlp = train(cfg, X, T)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
     c, scores = calibrate(cfg, mlp)
     res = evaluate(cfg, mlp if c != 0.0 else None)
     res.update(samples=int(X.shape[0]), train_loss=mlp.last_loss, amplitude=c,
-               calibration_scores=scores)
+               calibration_scores=scores, train_s=train_s, epochs=cfg.epochs)
     mlp.close()
     return res

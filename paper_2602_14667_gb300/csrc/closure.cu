@@ -371,8 +371,15 @@ __global__ void loss_grad(const float* __restrict__ Y, const float* __restrict__
 }
 
 // Adam on the trainable part of the parameter blob.
-__global__ void adam_kernel(float* __restrict__ prm, const float* __restrict__ grad, float* __restrict__ m,
-                            float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
+// Adam on the FP32 master weights (the normalisation and output-scale
+// entries of the blob are not trained).  The step count t is read from
+// device memory (the training loop runs as a captured graph); tick_kernel
+// advances it.
+__global__ void adam_dev_kernel(float* __restrict__ prm, const float* __restrict__ grad, float* __restrict__ m,
+                                float* __restrict__ v, float lr, float b1, float b2, float eps,
+                                const long long* __restrict__ t) {
+    const float tn = (float)(*t + 1);
+    const float c1 = 1.f - powf(b1, tn), c2 = 1.f - powf(b2, tn);
     for (int i = kOffW1 + blockIdx.x * blockDim.x + threadIdx.x; i < kBlob; i += gridDim.x * blockDim.x) {
         const float gi = grad[i];
         const float mi = b1 * m[i] + (1.f - b1) * gi;
@@ -380,6 +387,16 @@ __global__ void adam_kernel(float* __restrict__ prm, const float* __restrict__ g
         m[i] = mi;
         v[i] = vi;
         prm[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// One thread: t += 1, and the batch's loss partials added in a fixed order.
+__global__ void tick_kernel(long long* t, const double* __restrict__ lossp, int nb, double* acc) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        *t += 1;
+        double s = *acc;
+        for (int b = 0; b < nb; ++b) s += lossp[b];
+        *acc = s;
     }
 }
 
@@ -788,10 +805,14 @@ cudaError_t launch_gather_batch(const float* X, const float* T, const int* idx, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_adam(float* prm, const float* grad, float* m, float* v, float lr, float b1, float b2, float eps,
-                        long long t, cudaStream_t st) {
-    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
-    adam_kernel<<<24, 256, 0, st>>>(prm, grad, m, v, lr, b1, b2, eps, c1, c2);
+cudaError_t launch_adam_dev(float* prm, const float* grad, float* m, float* v, float lr, float b1, float b2,
+                            float eps, const long long* t, cudaStream_t st) {
+    adam_dev_kernel<<<24, 256, 0, st>>>(prm, grad, m, v, lr, b1, b2, eps, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tick(long long* t, const double* lossp, int nb, double* acc, cudaStream_t st) {
+    tick_kernel<<<1, 32, 0, st>>>(t, lossp, nb, acc);
     return cudaGetLastError();
 }
 

@@ -51,6 +51,9 @@ struct mhd_mlp {
     float *prm = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
     double* lossp = nullptr;
     double* statp = nullptr;
+    long long* t_d = nullptr;    // Adam step count while a training graph runs
+    double* loss_acc = nullptr;  // the epoch's loss, summed on the device
+    cudaStream_t cap = nullptr;  // private stream for graph capture
     mhd::MlpDev d{};
     std::vector<void*> allocs;
     long long t = 0;
@@ -78,6 +81,8 @@ mhd_status mlp_buffers(mhd_mlp* m) {
     const size_t R = (size_t)m->max_rows;
     CALLOC(m->prm, kBlob); CALLOC(m->m, kBlob); CALLOC(m->v, kBlob); CALLOC(m->grad, kBlob);
     CALLOC(m->lossp, kLossBlocks);
+    CALLOC(m->t_d, 1);
+    CALLOC(m->loss_acc, 1);
     CALLOC(m->statp, (size_t)kStatBlocks * 2 * (kIn + kOut));
     MlpDev& d = m->d;
     CALLOC(d.Wt1, kHid * kInPad); CALLOC(d.W1, kInPad * kHid);
@@ -137,7 +142,8 @@ mhd_status mhd_mlp_create(unsigned long long seed, int max_batch, void* stream, 
     m->stream = static_cast<cudaStream_t>(stream);
     m->max_rows = rows_of(max_batch);
     cudaError_t e = cudaGetDevice(&m->dev);
-    mhd_status s = e == cudaSuccess ? mlp_buffers(m) : ccuda(e, "cudaGetDevice");
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking);
+    mhd_status s = e == cudaSuccess ? mlp_buffers(m) : ccuda(e, "mhd_mlp_create");
     if (s == MHD_OK) {
         std::vector<float> p = initial_params(seed);
         e = cudaMemcpy(m->prm, p.data(), sizeof(float) * p.size(), cudaMemcpyHostToDevice);
@@ -158,6 +164,7 @@ mhd_status mhd_mlp_destroy(mhd_mlp* m) {
     cudaSetDevice(m->dev);
     cudaStreamSynchronize(m->stream);
     for (void* p : m->allocs) cudaFree(p);
+    if (m->cap) cudaStreamDestroy(m->cap);
     delete m;
     return MHD_OK;
 }
@@ -213,6 +220,33 @@ mhd_status mhd_mlp_gradients(mhd_mlp* m, const float* X, const float* T, long lo
     return MHD_OK;
 }
 
+// One epoch's batches -- gather, forward, backward, Adam (step count on the
+// device), weight refresh, loss accumulation -- recorded once as a CUDA graph
+// and replayed every epoch after the new permutation is uploaded: the step
+// is some twenty small kernels, so launching them one by one cost more than
+// running them.
+static cudaError_t capture_epoch(mhd_mlp* m, const float* X, const float* T, const int* idx, long long n,
+                                 int batch, float lr, cudaGraphExec_t* exec) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(m->loss_acc, 0, sizeof(double), m->cap);
+    for (long long b0 = 0; b0 < n && e == cudaSuccess; b0 += batch) {
+        const int nb = (int)std::min<long long>(batch, n - b0), rows = rows_of(nb);
+        e = mhd::launch_gather_batch(X, T, idx + b0, nb, rows, m->prm, m->d, m->cap);
+        if (e == cudaSuccess)
+            e = mhd::mlp_forward_backward(m->d, m->prm, rows, nb, true, m->grad, m->lossp, kLossBlocks, m->cap);
+        if (e == cudaSuccess) e = mhd::launch_adam_dev(m->prm, m->grad, m->m, m->v, lr, 0.9f, 0.999f, 1e-8f, m->t_d, m->cap);
+        if (e == cudaSuccess) e = mhd::launch_refresh(m->prm, m->d, m->cap);
+        if (e == cudaSuccess) e = mhd::launch_tick(m->t_d, m->lossp, kLossBlocks, m->loss_acc, m->cap);
+    }
+    const cudaError_t ee = cudaStreamEndCapture(m->cap, &g);
+    if (e == cudaSuccess) e = ee;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
+
 mhd_status mhd_mlp_train(mhd_mlp* m, const float* X, const float* T, long long n, int epochs, int batch,
                          float lr, unsigned long long seed, double* last_epoch_loss) {
     if (!m || !X || !T) return cfail(MHD_EINVAL, "NULL argument");
@@ -225,37 +259,31 @@ mhd_status mhd_mlp_train(mhd_mlp* m, const float* X, const float* T, long long n
     std::vector<int> perm((size_t)n);
     for (long long i = 0; i < n; ++i) perm[(size_t)i] = (int)i;
     unsigned long long s = seed;
-    double epoch_loss = 0;
-    mhd_status st = MHD_OK;
-    for (int ep = 0; ep < epochs && st == MHD_OK; ++ep) {
-        for (long long i = n - 1; i > 0; --i) {  // Fisher-Yates
+    // the work so far on the caller's stream comes first; the step count
+    // continues from the host copy
+    cudaError_t e = cudaStreamSynchronize(m->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(m->t_d, &m->t, sizeof(long long), cudaMemcpyHostToDevice);
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = capture_epoch(m, X, T, idx, n, batch, lr, &exec);
+    for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
+        for (long long i = n - 1; i > 0; --i) {  // Fisher-Yates (while the previous epoch runs)
             const long long j = (long long)(uniform01(s) * (double)(i + 1));
             std::swap(perm[(size_t)i], perm[(size_t)std::min(j, i)]);
         }
-        cudaError_t e = cudaMemcpyAsync(idx, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, m->stream);
-        double sum = 0;
-        for (long long b0 = 0; b0 < n && e == cudaSuccess; b0 += batch) {
-            const int nb = (int)std::min<long long>(batch, n - b0), rows = rows_of(nb);
-            e = mhd::launch_gather_batch(X, T, idx + b0, nb, rows, m->prm, m->d, m->stream);
-            if (e == cudaSuccess)
-                e = mhd::mlp_forward_backward(m->d, m->prm, rows, nb, true, m->grad, m->lossp, kLossBlocks,
-                                              m->stream);
-            if (e == cudaSuccess) e = mhd::launch_adam(m->prm, m->grad, m->m, m->v, lr, 0.9f, 0.999f, 1e-8f, ++m->t, m->stream);
-            if (e == cudaSuccess) e = mhd::launch_refresh(m->prm, m->d, m->stream);
-            if (e == cudaSuccess && ep == epochs - 1) {
-                double lp[kLossBlocks];
-                e = cudaMemcpyAsync(lp, m->lossp, sizeof lp, cudaMemcpyDeviceToHost, m->stream);
-                if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
-                for (double v : lp) sum += v;
-            }
-        }
-        if (e != cudaSuccess) st = ccuda(e, "mhd_mlp_train");
-        epoch_loss = sum / (double)(n * mhd::kOut);
+        e = cudaMemcpyAsync(idx, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, m->stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(exec, m->stream);
     }
-    cudaError_t e2 = cudaStreamSynchronize(m->stream);
+    double acc = 0;
+    long long t = m->t;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&acc, m->loss_acc, sizeof(double), cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&t, m->t_d, sizeof(long long), cudaMemcpyDeviceToHost, m->stream);
+    const cudaError_t e2 = cudaStreamSynchronize(m->stream);
+    if (exec) cudaGraphExecDestroy(exec);
     cudaFree(idx);
-    if (st != MHD_OK) return st;
+    if (e != cudaSuccess) return ccuda(e, "mhd_mlp_train");
     if (e2 != cudaSuccess) return ccuda(e2, "mhd_mlp_train");
+    m->t = t;
+    const double epoch_loss = acc / (double)(n * mhd::kOut);
     if (last_epoch_loss) *last_epoch_loss = epoch_loss;
     if (!std::isfinite(epoch_loss)) return cfail(MHD_EUNSTABLE, "training loss is not finite");
     return MHD_OK;

@@ -52,9 +52,12 @@ cudaError_t mlp_forward_backward(const MlpDev& d, const float* prm, int rows, in
                                  float* grad, double* lossp, int lossblocks, cudaStream_t st);
 cudaError_t launch_gather_batch(const float* X, const float* T, const int* idx, int nreal, int rows,
                                 const float* prm, const MlpDev& d, cudaStream_t st);
-cudaError_t launch_adam(float* prm, const float* grad, float* m, float* v, float lr, float b1, float b2,
-                        float eps, long long t, cudaStream_t st);
 cudaError_t launch_refresh(const float* prm, const MlpDev& d, cudaStream_t st);
+// Adam with the step count in device memory; then t += 1 and the batch's
+// loss partials added to *acc (one thread, fixed order)
+cudaError_t launch_adam_dev(float* prm, const float* grad, float* m, float* v, float lr, float b1, float b2,
+                            float eps, const long long* t, cudaStream_t st);
+cudaError_t launch_tick(long long* t, const double* lossp, int nb, double* acc, cudaStream_t st);
 cudaError_t launch_stats(const float* X, const float* T, long long n, double* P, int nblocks, float* prm,
                          cudaStream_t st);
 cudaError_t launch_mlp_predict(const MlpDev& d, int rows, int nreal, const float* prm, float* Yraw,
