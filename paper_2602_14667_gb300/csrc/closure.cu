@@ -741,7 +741,7 @@ cudaError_t launch_targets(const float* sT, const float* sT1, int nx, int ny, do
 }
 
 // ---- training driver pieces ------------------------------------------------------
-constexpr int kRowsPerWgradBlock = 1024;
+
 
 __global__ void assemble_grad(const MlpDev d, float* __restrict__ grad);
 
@@ -753,23 +753,27 @@ cudaError_t mlp_forward_backward(const MlpDev& d, const float* prm, int rows, in
     mlp_fwd<kHid, kOutPad, false><<<fwd_blocks, 256, 0, st>>>(d.H2, d.Wt3, d.b3, rows, d.Y, nullptr);
     loss_grad<<<lossblocks, 256, 0, st>>>(d.Y, d.tb, nreal, rows, prm, d.dYf, d.dYb, lossp);
     if (!backward) return cudaGetLastError();
-    const int wb = (rows + kRowsPerWgradBlock - 1) / kRowsPerWgradBlock;
+    // weight gradients: at least 128 rows per block, at most kMaxWgradBlocks
+    // per-block partials (reduced in a fixed order)
+    const int per = (rows + kMaxWgradBlocks - 1) / kMaxWgradBlocks;
+    const int rpb = std::max(128, (per + 15) / 16 * 16);
+    const int wb = (rows + rpb - 1) / rpb;
     // layer 3
-    mlp_wgrad<kHid, kOutPadK><<<wb, 256, 0, st>>>(d.H2, d.dYb, rows, kRowsPerWgradBlock, d.part);
+    mlp_wgrad<kHid, kOutPadK><<<wb, 256, 0, st>>>(d.H2, d.dYb, rows, rpb, d.part);
     reduce_partials<<<8, 256, 0, st>>>(d.part, wb, kHid * kOutPadK, d.gW3);
-    col_partials<kOutPad><<<wb, 32, 0, st>>>(d.dYf, rows, kRowsPerWgradBlock, d.part);
+    col_partials<kOutPad><<<wb, 32, 0, st>>>(d.dYf, rows, rpb, d.part);
     reduce_partials<<<1, 32, 0, st>>>(d.part, wb, kOutPad, d.gb3);
     mlp_bwd_data<kOutPadK, kHid><<<fwd_blocks, 256, 0, st>>>(d.dYb, d.W3, d.Z2, rows, d.dH2f, d.dH2b);
     // layer 2
-    mlp_wgrad<kHid, kHid><<<wb, 256, 0, st>>>(d.H1, d.dH2b, rows, kRowsPerWgradBlock, d.part);
+    mlp_wgrad<kHid, kHid><<<wb, 256, 0, st>>>(d.H1, d.dH2b, rows, rpb, d.part);
     reduce_partials<<<16, 256, 0, st>>>(d.part, wb, kHid * kHid, d.gW2);
-    col_partials<kHid><<<wb, 64, 0, st>>>(d.dH2f, rows, kRowsPerWgradBlock, d.part);
+    col_partials<kHid><<<wb, 64, 0, st>>>(d.dH2f, rows, rpb, d.part);
     reduce_partials<<<1, 64, 0, st>>>(d.part, wb, kHid, d.gb2);
     mlp_bwd_data<kHid, kHid><<<fwd_blocks, 256, 0, st>>>(d.dH2b, d.W2, d.Z1, rows, d.dH1f, d.dH1b);
     // layer 1
-    mlp_wgrad<kInPad, kHid><<<wb, 256, 0, st>>>(d.xb, d.dH1b, rows, kRowsPerWgradBlock, d.part);
+    mlp_wgrad<kInPad, kHid><<<wb, 256, 0, st>>>(d.xb, d.dH1b, rows, rpb, d.part);
     reduce_partials<<<8, 256, 0, st>>>(d.part, wb, kInPad * kHid, d.gW1);
-    col_partials<kHid><<<wb, 64, 0, st>>>(d.dH1f, rows, kRowsPerWgradBlock, d.part);
+    col_partials<kHid><<<wb, 64, 0, st>>>(d.dH1f, rows, rpb, d.part);
     reduce_partials<<<1, 64, 0, st>>>(d.part, wb, kHid, d.gb1);
     // assemble the blob-layout gradient
     assemble_grad<<<(kBlob + 255) / 256, 256, 0, st>>>(d, grad);

@@ -95,7 +95,7 @@ mhd_status mlp_buffers(mhd_mlp* m) {
     CALLOC(d.Y, R * kOutPad); CALLOC(d.dYf, R * kOutPad); CALLOC(d.dYb, R * kOutPadK);
     CALLOC(d.dH2f, R * kHid); CALLOC(d.dH2b, R * kHid);
     CALLOC(d.dH1f, R * kHid); CALLOC(d.dH1b, R * kHid);
-    CALLOC(d.part, ((R + 1023) / 1024 + 1) * (size_t)kHid * kHid);
+    CALLOC(d.part, (size_t)(mhd::kMaxWgradBlocks + 1) * kHid * kHid);
     CALLOC(d.gW1, kInPad * kHid); CALLOC(d.gb1, kHid);
     CALLOC(d.gW2, kHid * kHid); CALLOC(d.gb2, kHid);
     CALLOC(d.gW3, kHid * kOutPadK); CALLOC(d.gb3, kOutPad);

@@ -10,6 +10,7 @@
 namespace mhd {
 
 constexpr int kIn = 24, kInPad = 32, kHid = 64, kOut = 3, kOutPad = 8, kOutPadK = 16;
+constexpr int kMaxWgradBlocks = 256;  // per-block partials of a weight gradient
 // Flat FP32 parameter blob: mean[24] scale[24] out_scale[3] W1[24][64] b1[64]
 // W2[64][64] b2[64] W3[64][3] b3[3]  (weights input-major, W[in][out]).
 constexpr int kOffMean = 0, kOffScale = kOffMean + kIn, kOffOutScale = kOffScale + kIn;
