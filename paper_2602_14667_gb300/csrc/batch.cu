@@ -37,7 +37,8 @@ struct BatchTile {
     int lat, xblock, y0, pad;
 };
 
-template <int V>
+// Off: int offsets when every lattice's state has fewer than 2^31 elements.
+template <int V, typename Off>
 __global__ void __launch_bounds__(512) batch_step(const BatchLattice* __restrict__ lats,
                                                   const BatchTile* __restrict__ tiles, int ntiles,
                                                   const float* __restrict__ src, float* __restrict__ dst) {
@@ -46,8 +47,8 @@ __global__ void __launch_bounds__(512) batch_step(const BatchLattice* __restrict
         const BatchLattice L = lats[tile.lat];
         const int y = tile.y0 + threadIdx.y;
         if (y < L.ny)  // uniform over the warp
-            step_row<1, V, false>(src + L.offset, dst + L.offset, L.nx, L.ny, L.pitch, L.plane,
-                                  L.np, tile.xblock, y, threadIdx.x);
+            step_row<1, V, false, Off>(src + L.offset, dst + L.offset, L.nx, L.ny, L.pitch, L.plane,
+                                       L.np, tile.xblock, y, threadIdx.x);
     }
 }
 
@@ -85,6 +86,7 @@ struct mhd_batch {
     std::vector<char> prev_valid; // the spare buffer holds the state the last step read
     std::vector<char> is_eq;      // lattice i holds an equilibrium state (no step since set)
     long long total_elems = 0, nodes = 0;
+    bool wide = false;            // some lattice's state has 2^31 elements or more
     float* buf[2] = {nullptr, nullptr};
     int cur = 0;
     long long step = 0;
@@ -119,16 +121,24 @@ bool batch_shape_ok(const mhd_batch* b, const mhd_kernel_config& c) {
     return true;
 }
 
+using BatchKernel = void (*)(const mhd::BatchLattice*, const mhd::BatchTile*, int, const float*, float*);
+
+BatchKernel batch_kernel(bool wide, int V) {
+    switch (V) {
+    case 1: return wide ? mhd::batch_step<1, long long> : mhd::batch_step<1, int>;
+    case 2: return wide ? mhd::batch_step<2, long long> : mhd::batch_step<2, int>;
+    case 4: return wide ? mhd::batch_step<4, long long> : mhd::batch_step<4, int>;
+    }
+    return nullptr;
+}
+
 cudaError_t launch_batch(const mhd_batch* b, int from, int V, cudaStream_t st) {
     dim3 block(32, b->cfg.rows_per_block);
     const float* src = b->buf[from];
     float* dst = b->buf[from ^ 1];
-    switch (V) {
-    case 1: mhd::batch_step<1><<<b->grid, block, 0, st>>>(b->d_lats, b->d_tiles, b->ntiles, src, dst); break;
-    case 2: mhd::batch_step<2><<<b->grid, block, 0, st>>>(b->d_lats, b->d_tiles, b->ntiles, src, dst); break;
-    case 4: mhd::batch_step<4><<<b->grid, block, 0, st>>>(b->d_lats, b->d_tiles, b->ntiles, src, dst); break;
-    default: return cudaErrorInvalidValue;
-    }
+    const BatchKernel k = batch_kernel(b->wide, V);
+    if (!k) return cudaErrorInvalidValue;
+    k<<<b->grid, block, 0, st>>>(b->d_lats, b->d_tiles, b->ntiles, src, dst);
     return cudaGetLastError();
 }
 
@@ -150,13 +160,9 @@ mhd_status batch_configure(mhd_batch* b, const mhd_kernel_config& c) {
     b->ntiles = (int)tiles.size();
     int per_sm = 0, sms = 0;
     const int threads = 32 * rows;
-    cudaError_t e;
-    switch (c.nodes_per_thread) {
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mhd::batch_step<1>, threads, 0); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mhd::batch_step<2>, threads, 0); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mhd::batch_step<4>, threads, 0); break;
-    }
-    BCK(e, "occupancy");
+    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(b->wide, c.nodes_per_thread),
+                                                      threads, 0),
+        "occupancy");
     BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev), "SM count");
     b->grid = std::max(1, std::min(b->ntiles, std::max(1, per_sm) * sms));
     batch_drop_graphs(b);
@@ -228,6 +234,7 @@ mhd_status mhd_batch_create(int count, const int* nx, const int* ny, const mhd_p
         lats[i].np.collision = params[i].collision;
         lats[i].np.mag_collision = params[i].mag_collision;
         b->total_elems += (long long)mhd::kStatePlanes * L.plane;
+        if ((long long)mhd::kStatePlanes * L.plane >= (1LL << 31)) b->wide = true;
         b->nodes += (long long)nx[i] * ny[i];
         maxn = std::max(maxn, (long long)nx[i] * ny[i]);
     }

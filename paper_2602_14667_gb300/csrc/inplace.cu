@@ -7,33 +7,34 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "inplace.h"
 #include "inplace_row.cuh"
 
 namespace mhd {
 
-template <int PREC, int V, bool WALLY>
+template <int PREC, int V, bool WALLY, typename Off>
 __global__ void __launch_bounds__(512) aa_step_a(const StepArgs<typename Prec<PREC>::C> a, int nxb,
                                                  int ntiles) {
     using S = typename Prec<PREC>::S;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int y = (t / nxb) * blockDim.y + threadIdx.y;
         if (y < a.ny)  // whole warp
-            aa_row_a<PREC, V, WALLY>(static_cast<S*>(a.dst), a.nx, a.ny, a.pitch, a.plane, a.np,
-                                     t % nxb, y, threadIdx.x);
+            aa_row_a<PREC, V, WALLY, Off>(static_cast<S*>(a.dst), a.nx, a.ny, a.pitch, a.plane, a.np,
+                                          t % nxb, y, threadIdx.x);
     }
 }
 
-template <int PREC, int V>
+template <int PREC, int V, typename Off>
 __global__ void __launch_bounds__(512) aa_step_b(const StepArgs<typename Prec<PREC>::C> a, int nxb,
                                                  int ntiles) {
     using S = typename Prec<PREC>::S;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int y = (t / nxb) * blockDim.y + threadIdx.y;
         if (y < a.ny)
-            aa_row_b<PREC, V>(static_cast<S*>(a.dst), a.nx, a.pitch, a.plane, a.np, t % nxb, y,
-                              threadIdx.x);
+            aa_row_b<PREC, V, Off>(static_cast<S*>(a.dst), a.nx, a.pitch, a.plane, a.np, t % nxb, y,
+                                   threadIdx.x);
     }
 }
 
@@ -102,12 +103,20 @@ static cudaError_t launch_aa_t(const StepLaunch& s, int phase, cudaStream_t st) 
         if (phase == 1) return go(b);
         return s.wall_y ? go(a_wall) : go(a_periodic);
     };
+    // 32-bit element offsets while the state has fewer than 2^31 elements
+    const bool small = (long long)kPlanes * s.L.plane < (1LL << 31);
+    auto pick_v = [&](auto v) -> cudaError_t {
+        constexpr int V = decltype(v)::value;
+        if (small)
+            return pick(aa_step_a<PREC, V, false, int>, aa_step_a<PREC, V, true, int>, aa_step_b<PREC, V, int>);
+        return pick(aa_step_a<PREC, V, false, long long>, aa_step_a<PREC, V, true, long long>,
+                    aa_step_b<PREC, V, long long>);
+    };
     switch (s.V) {
-    case 1: return pick(aa_step_a<PREC, 1, false>, aa_step_a<PREC, 1, true>, aa_step_b<PREC, 1>);
-    case 2: return pick(aa_step_a<PREC, 2, false>, aa_step_a<PREC, 2, true>, aa_step_b<PREC, 2>);
+    case 1: return pick_v(std::integral_constant<int, 1>{});
+    case 2: return pick_v(std::integral_constant<int, 2>{});
     case 4:
-        if constexpr (PREC != 0)
-            return pick(aa_step_a<PREC, 4, false>, aa_step_a<PREC, 4, true>, aa_step_b<PREC, 4>);
+        if constexpr (PREC != 0) return pick_v(std::integral_constant<int, 4>{});
         return cudaErrorInvalidValue;
     }
     return cudaErrorInvalidValue;

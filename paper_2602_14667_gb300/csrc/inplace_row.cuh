@@ -59,8 +59,9 @@ __device__ __forceinline__ float step_store_one(float c, float) { return c; }
 __device__ __forceinline__ __half step_store_one(float c, __half) { return __float2half_rn(c); }
 
 // Phase A for one warp: 32*V consecutive nodes of row y (requires nx % V
-// == 0, all 32 lanes present, y < ny; periodic in x).
-template <int PREC, int V, bool WALLY>
+// == 0, all 32 lanes present, y < ny; periodic in x).  Off: the element
+// offset type (int when the state has fewer than 2^31 elements).
+template <int PREC, int V, bool WALLY, typename Off = long long>
 __device__ __forceinline__ void aa_row_a(typename Prec<PREC>::S* buf, int nx, int ny,
                                          long long pitch, long long plane,
                                          const NodeParams<typename Prec<PREC>::C>& np, int xblock,
@@ -83,15 +84,15 @@ __device__ __forceinline__ void aa_row_a(typename Prec<PREC>::S* buf, int nx, in
     const int xl = (x0 == 0) ? nx - 1 : x0 - 1;
     const int xr = (x0 + V >= nx) ? x0 + V - nx : x0 + V;
     const bool right_by_shfl = (lane < 31) && (x0 + V < nx);
-    const long long rowy = (long long)y * pitch;
+    const Off pl = (Off)plane, pt = (Off)pitch;
+    const Off o_m = (Off)ym * pt, o_0 = (Off)y * pt, o_p = (Off)yp * pt;
 
-    auto slot_row = [&](int p) -> S* {  // the cells slot p reads and writes
+    auto slot_off = [&](int p) -> Off {  // offset of the cells slot p reads and writes
         const int cy = pcy(p);
         const bool bounce = WALLY && (cy > 0 ? bm : (cy < 0 ? bp : false));
-        const int sy = cy > 0 ? ym : (cy < 0 ? yp : y);
-        return bounce ? buf + (long long)popp(p) * plane + rowy
-                      : buf + (long long)p * plane + (long long)sy * pitch;
+        return bounce ? (Off)popp(p) * pl + o_0 : (Off)p * pl + (cy > 0 ? o_m : (cy < 0 ? o_p : o_0));
     };
+    auto slot_row = [&](int p) -> S* { return buf + slot_off(p); };
     auto slot_bounce = [&](int p) -> bool {
         const int cy = pcy(p);
         return WALLY && (cy > 0 ? bm : (cy < 0 ? bp : false));
@@ -156,13 +157,7 @@ __device__ __forceinline__ void aa_row_a(typename Prec<PREC>::S* buf, int nx, in
     // slot addresses here instead of keeping them live across the collision.
     S* wbuf;
     asm volatile("mov.b64 %0, %1;" : "=l"(wbuf) : "l"(buf));
-    auto wslot_row = [&](int p) -> S* {
-        const int cy = pcy(p);
-        const bool bounce = WALLY && (cy > 0 ? bm : (cy < 0 ? bp : false));
-        const int sy = cy > 0 ? ym : (cy < 0 ? yp : y);
-        return bounce ? wbuf + (long long)popp(p) * plane + rowy
-                      : wbuf + (long long)p * plane + (long long)sy * pitch;
-    };
+    auto wslot_row = [&](int p) -> S* { return wbuf + slot_off(p); };
 #pragma unroll
     for (int p = 0; p < kPlanes; ++p) {
         const int cx = pcx(p);
@@ -198,7 +193,7 @@ __device__ __forceinline__ void aa_row_a(typename Prec<PREC>::S* buf, int nx, in
 }
 
 // Phase B for one thread: V consecutive nodes of row y, all accesses local.
-template <int PREC, int V>
+template <int PREC, int V, typename Off = long long>
 __device__ __forceinline__ void aa_row_b(typename Prec<PREC>::S* buf, int nx, long long pitch,
                                          long long plane,
                                          const NodeParams<typename Prec<PREC>::C>& np, int xblock,
@@ -209,10 +204,11 @@ __device__ __forceinline__ void aa_row_b(typename Prec<PREC>::S* buf, int nx, lo
     using Codec = StepCodec<S, V>;
     const int x0 = (xblock * 32 + lane) * V;
     if (x0 >= nx) return;
-    S* base = buf + (long long)y * pitch + x0;
+    const Off pl = (Off)plane;
+    S* base = buf + ((Off)y * (Off)pitch + x0);
     S r[kPlanes][V];
 #pragma unroll
-    for (int p = 0; p < kPlanes; ++p) VecRW<S, V>::load(base + (long long)p * plane, r[p]);
+    for (int p = 0; p < kPlanes; ++p) VecRW<S, V>::load(base + (Off)p * pl, r[p]);
     C v[kPlanes][V];  // v[q]: population q, read from plane opp(q)
 #pragma unroll
     for (int p = 0; p < kPlanes; ++p) Codec::to_compute(r[p], v[popp(p)]);
@@ -233,7 +229,7 @@ __device__ __forceinline__ void aa_row_b(typename Prec<PREC>::S* buf, int nx, lo
     for (int p = 0; p < kPlanes; ++p) {
         S w[V];
         Codec::to_storage(v[p], w);
-        VecRW<S, V>::store(base + (long long)p * plane, w, false, false);
+        VecRW<S, V>::store(base + (Off)p * pl, w, false, false);
     }
 }
 

@@ -28,15 +28,16 @@ namespace mhd {
 // once and each block walks the tiles (rows_per_block rows x 32*V columns)
 // with a fixed stride, so warps of one SM drift apart and the loads of one
 // tile overlap the arithmetic of another.
-template <int PREC, int V, bool WALLY>
+// Off: int offsets when the state has fewer than 2^31 elements per buffer.
+template <int PREC, int V, bool WALLY, typename Off>
 __global__ void __launch_bounds__(512) step_vec(const StepArgs<typename Prec<PREC>::C> a, int nxb,
                                                 int ntiles) {
     using S = typename Prec<PREC>::S;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int y = (t / nxb) * blockDim.y + threadIdx.y;
         if (y < a.ny)  // whole warp (one row per warp)
-            step_row<PREC, V, WALLY>(static_cast<const S*>(a.src), static_cast<S*>(a.dst), a.nx,
-                                     a.ny, a.pitch, a.plane, a.np, t % nxb, y, threadIdx.x);
+            step_row<PREC, V, WALLY, Off>(static_cast<const S*>(a.src), static_cast<S*>(a.dst), a.nx,
+                                          a.ny, a.pitch, a.plane, a.np, t % nxb, y, threadIdx.x);
     }
 }
 
@@ -95,11 +96,19 @@ static cudaError_t launch_step_t(const StepLaunch& s, cudaStream_t st) {
         kernel<<<blocks, block, 0, st>>>(a, nxb, ntiles);
         return cudaGetLastError();
     };
+    const bool small = (long long)kPlanes * s.L.plane < (1LL << 31);
+    auto pick = [&](auto k32, auto k64) -> cudaError_t { return small ? go(k32) : go(k64); };
     switch (s.V) {
-    case 1: return s.wall_y ? go(step_vec<PREC, 1, true>) : go(step_vec<PREC, 1, false>);
-    case 2: return s.wall_y ? go(step_vec<PREC, 2, true>) : go(step_vec<PREC, 2, false>);
+    case 1:
+        return s.wall_y ? pick(step_vec<PREC, 1, true, int>, step_vec<PREC, 1, true, long long>)
+                        : pick(step_vec<PREC, 1, false, int>, step_vec<PREC, 1, false, long long>);
+    case 2:
+        return s.wall_y ? pick(step_vec<PREC, 2, true, int>, step_vec<PREC, 2, true, long long>)
+                        : pick(step_vec<PREC, 2, false, int>, step_vec<PREC, 2, false, long long>);
     case 4:
-        if constexpr (PREC != 0) return s.wall_y ? go(step_vec<PREC, 4, true>) : go(step_vec<PREC, 4, false>);
+        if constexpr (PREC != 0)
+            return s.wall_y ? pick(step_vec<PREC, 4, true, int>, step_vec<PREC, 4, true, long long>)
+                            : pick(step_vec<PREC, 4, false, int>, step_vec<PREC, 4, false, long long>);
         return cudaErrorInvalidValue;
     }
     return cudaErrorInvalidValue;

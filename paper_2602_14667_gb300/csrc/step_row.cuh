@@ -27,7 +27,10 @@ template <typename C> struct StepArgs {
 // Requires nx % V == 0, all 32 lanes of the warp present, y < ny.  WALLY:
 // half-way bounce-back walls below row 0 and above row ny-1 (compile-time,
 // so that the periodic kernel has no branch between its 19 plane loads).
-template <int PREC, int V, bool WALLY>
+// Off: the type of element offsets into the state; int when the 19 planes
+// hold fewer than 2^31 elements (fewer address instructions per plane),
+// long long otherwise.
+template <int PREC, int V, bool WALLY, typename Off = long long>
 __device__ __forceinline__ void step_row(const typename Prec<PREC>::S* __restrict__ src,
                                          typename Prec<PREC>::S* __restrict__ dst, int nx, int ny,
                                          long long pitch, long long plane,
@@ -50,7 +53,8 @@ __device__ __forceinline__ void step_row(const typename Prec<PREC>::S* __restric
     const int xl = (x0 == 0) ? nx - 1 : x0 - 1;          // source column for c_x = +1 at x0
     const int xr = (x0 + V >= nx) ? x0 + V - nx : x0 + V;  // source column for c_x = -1 at x0+V-1
     const bool right_by_shfl = (lane < 31) && (x0 + V < nx);
-    const long long rowy = (long long)y * pitch;
+    const Off pl = (Off)plane, pt = (Off)pitch;
+    const Off o_m = (Off)ym * pt, o_0 = (Off)y * pt, o_p = (Off)yp * pt;
 
     // Phase 1: issue every load of the 19 planes (aligned vectors, plus the
     // edge element for the lanes at a warp / lattice edge) before any
@@ -61,9 +65,8 @@ __device__ __forceinline__ void step_row(const typename Prec<PREC>::S* __restric
     for (int p = 0; p < kPlanes; ++p) {
         const int cx = pcx(p), cy = pcy(p);
         const bool bounce = WALLY && (cy > 0 ? bm : (cy < 0 ? bp : false));  // warp-uniform
-        const int sy = cy > 0 ? ym : (cy < 0 ? yp : y);
-        const S* row = bounce ? src + (long long)popp(p) * plane + rowy
-                              : src + (long long)p * plane + (long long)sy * pitch;
+        const S* row = src + (bounce ? (Off)popp(p) * pl + o_0
+                                     : (Off)p * pl + (cy > 0 ? o_m : (cy < 0 ? o_p : o_0)));
 #pragma unroll
         for (int k = 0; k < V; ++k) r[p][k] = S(0);
         edge[p] = S(0);
@@ -117,7 +120,7 @@ __device__ __forceinline__ void step_row(const typename Prec<PREC>::S* __restric
     for (int p = 0; p < kPlanes; ++p) {
         S r[V];
         Codec::to_storage(v[p], r);
-        VecIO<S, V>::store(dst + (long long)p * plane + rowy + x0, r);
+        VecIO<S, V>::store(dst + ((Off)p * pl + o_0 + x0), r);
     }
 }
 
