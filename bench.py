@@ -82,7 +82,7 @@ def measured_peaks():
 
 
 # The translation unit of the step kernels (kernels.cu) and what it includes.
-STEP_KERNEL_SOURCES = ("internal.h", "kernels.cu", "lbm_device.cuh", "step_row.cuh")
+STEP_KERNEL_SOURCES = ("f32x2.cuh", "internal.h", "kernels.cu", "lbm_device.cuh", "step_row.cuh")
 
 
 def kernel_source_hash():

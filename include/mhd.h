@@ -121,7 +121,7 @@ typedef struct {
  * updates with vector loads and stores: 1, 2 or 4 (at most 2 for MHD_FP64);
  * it must divide nx and must be 1 when the x axis has walls.
  * rows_per_block: warps per block, one row of 32*nodes_per_thread nodes
- * each: 1..16 (1..8 for MHD_FP64). */
+ * each: 1..16 (1..8 for MHD_FP64 and for MHD_FP16S with MHD_IN_PLACE). */
 typedef struct {
     int nodes_per_thread;
     int rows_per_block;

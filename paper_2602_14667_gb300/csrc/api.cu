@@ -170,6 +170,8 @@ mhd_kernel_config default_config(const mhd::Layout& L, int prec, int wall_x) {
 
 bool config_ok(const mhd_lattice* l, const mhd_kernel_config& c) {
     if (l->p.precision == 0 && c.rows_per_block > 8) return false;
+    // the FP16S in-place phase A kernel takes blocks of at most 256 threads
+    if (l->in_place && l->p.precision == MHD_FP16S && c.rows_per_block > 8) return false;
     return mhd::step_shape_ok(l->L, l->p.precision, l->p.bc_x == MHD_WALL, c.nodes_per_thread,
                               c.rows_per_block);
 }

@@ -14,8 +14,13 @@
 
 namespace mhd {
 
+// FP16S phase A (node pairs on FP32x2 beside the x-shift logic of both the
+// gather and the write-back) needs about 150 registers to run without
+// spilling: blocks of at most 256 threads.
+constexpr int aa_a_max_threads(int prec) { return prec == 2 ? 256 : 512; }
+
 template <int PREC, int V, bool WALLY, typename Off>
-__global__ void __launch_bounds__(512) aa_step_a(const StepArgs<typename Prec<PREC>::C> a, int nxb,
+__global__ void __launch_bounds__(aa_a_max_threads(PREC)) aa_step_a(const StepArgs<typename Prec<PREC>::C> a, int nxb,
                                                  int ntiles) {
     using S = typename Prec<PREC>::S;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -125,6 +130,7 @@ static cudaError_t launch_aa_t(const StepLaunch& s, int phase, cudaStream_t st) 
 cudaError_t launch_aa_step(const StepLaunch& s, int phase, cudaStream_t st) {
     if (s.wall_x || s.src != s.dst || (phase != 0 && phase != 1)) return cudaErrorInvalidValue;
     if (!step_shape_ok(s.L, s.prec, 0, s.V, s.BY)) return cudaErrorInvalidValue;
+    if (32 * s.BY > aa_a_max_threads(s.prec)) return cudaErrorInvalidValue;
     switch (s.prec) {
     case 0: return launch_aa_t<0>(s, phase, st);
     case 1: return launch_aa_t<1>(s, phase, st);

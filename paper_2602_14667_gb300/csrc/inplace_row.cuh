@@ -69,6 +69,8 @@ __device__ __forceinline__ void aa_row_a(typename Prec<PREC>::S* buf, int nx, in
     using S = typename Prec<PREC>::S;
     using C = typename Prec<PREC>::C;
     constexpr bool kScaled = PREC == 2;
+    // FP16S: node pairs on FP32x2, as in the two-buffer step (same bits)
+    constexpr int kMode = PREC == 2 ? kPairs : kNative;
     using Codec = StepCodec<S, V>;
     const int x0 = (xblock * 32 + lane) * V;
     const bool active = x0 < nx;
@@ -139,19 +141,7 @@ __device__ __forceinline__ void aa_row_a(typename Prec<PREC>::S* buf, int nx, in
     }
     // collide (inactive lanes hold zero deviations: a harmless rest state;
     // they stay in the warp for the shuffles below)
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-        C f[9], g[10];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = v[i][k];
-#pragma unroll
-        for (int q = 0; q < 10; ++q) g[q] = v[9 + q][k];
-        collide_impl<false, C, kScaled>(f, g, np, nullptr);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) v[i][k] = f[i];
-#pragma unroll
-        for (int q = 0; q < 10; ++q) v[9 + q][k] = g[q];
-    }
+    collide_nodes<C, V, kScaled, kMode>(v, np);
     // write back: slot p's cells receive f*_opp(p) of the nodes that read them.
     // A fresh copy of the base pointer makes the compiler recompute the 19
     // slot addresses here instead of keeping them live across the collision.
@@ -201,6 +191,8 @@ __device__ __forceinline__ void aa_row_b(typename Prec<PREC>::S* buf, int nx, lo
     using S = typename Prec<PREC>::S;
     using C = typename Prec<PREC>::C;
     constexpr bool kScaled = PREC == 2;
+    // FP16S: node pairs on FP32x2
+    constexpr int kMode = PREC == 2 ? kPairs : kNative;
     using Codec = StepCodec<S, V>;
     const int x0 = (xblock * 32 + lane) * V;
     if (x0 >= nx) return;
@@ -212,19 +204,7 @@ __device__ __forceinline__ void aa_row_b(typename Prec<PREC>::S* buf, int nx, lo
     C v[kPlanes][V];  // v[q]: population q, read from plane opp(q)
 #pragma unroll
     for (int p = 0; p < kPlanes; ++p) Codec::to_compute(r[p], v[popp(p)]);
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-        C f[9], g[10];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = v[i][k];
-#pragma unroll
-        for (int q = 0; q < 10; ++q) g[q] = v[9 + q][k];
-        collide_impl<false, C, kScaled>(f, g, np, nullptr);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) v[i][k] = f[i];
-#pragma unroll
-        for (int q = 0; q < 10; ++q) v[9 + q][k] = g[q];
-    }
+    collide_nodes<C, V, kScaled, kMode>(v, np);
 #pragma unroll
     for (int p = 0; p < kPlanes; ++p) {
         S w[V];

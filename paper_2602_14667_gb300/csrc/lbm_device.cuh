@@ -22,6 +22,10 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
+#include "f32x2.cuh"
+
 namespace mhd {
 
 constexpr int kQ = 9;        // D2Q9
@@ -348,6 +352,88 @@ __device__ __forceinline__ void collide_impl(C (&f)[9], C (&g)[10], const NodePa
     // = 1 + 6e-8 in FP32 would otherwise grow b by ~1e-7 per step)
     g[0] = Bx - ((g[2] + g[4]) + (g[6] + g[8]));
     g[1] = By - ((g[3] + g[5]) + (g[7] + g[9]));
+}
+
+// How collide_nodes evaluates the collision of a thread's V nodes.
+enum CollideMode {
+    kNative = 0,    // C as given, products fused where the compiler chooses
+    kPairs = 1,     // FP32: nodes (k, k+1) as one F2 on the packed FP32x2 instructions
+    kExplicit = 2,  // FP32: one node at a time as F1, bitwise equal to kPairs
+};
+
+// Tasks 2-5 for the V nodes of one thread, held as v[plane][k].  kPairs
+// does the arithmetic of two nodes in one instruction stream (about half
+// the FP32 instructions, more registers live); it pays where the step is
+// issue-bound (FP16S storage: half the bytes per node).  kExplicit is its
+// one-node form (used for odd V), so that every FP16S kernel produces the
+// same bits whatever its launch shape.
+template <typename C, int V, bool SCALED, int MODE>
+__device__ __forceinline__ void collide_nodes(C (&v)[kPlanes][V], const NodeParams<C>& np) {
+    if constexpr (MODE == kNative) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            C f[9], g[10];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = v[i][k];
+#pragma unroll
+            for (int q = 0; q < 10; ++q) g[q] = v[9 + q][k];
+            collide_impl<false, C, SCALED>(f, g, np, nullptr);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) v[i][k] = f[i];
+#pragma unroll
+            for (int q = 0; q < 10; ++q) v[9 + q][k] = g[q];
+        }
+    } else if constexpr (MODE == kPairs && V % 2 == 0) {
+        static_assert(std::is_same<C, float>::value, "packed pairs are FP32");
+        NodeParams<F2> p2;
+        p2.omega = F2(np.omega);
+        p2.omega_m = F2(np.omega_m);
+        p2.rho0 = F2(np.rho0);
+        p2.variant = np.variant;
+        p2.collision = np.collision;
+        p2.mag_collision = np.mag_collision;
+#pragma unroll
+        for (int k = 0; k < V; k += 2) {
+            F2 f[9], g[10];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = F2(v[i][k], v[i][k + 1]);
+#pragma unroll
+            for (int q = 0; q < 10; ++q) g[q] = F2(v[9 + q][k], v[9 + q][k + 1]);
+            collide_impl<false, F2, SCALED>(f, g, p2, nullptr);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                v[i][k] = f[i].v.x;
+                v[i][k + 1] = f[i].v.y;
+            }
+#pragma unroll
+            for (int q = 0; q < 10; ++q) {
+                v[9 + q][k] = g[q].v.x;
+                v[9 + q][k + 1] = g[q].v.y;
+            }
+        }
+    } else {
+        static_assert(std::is_same<C, float>::value, "explicit fusion is FP32");
+        NodeParams<F1> p1;
+        p1.omega = F1(np.omega);
+        p1.omega_m = F1(np.omega_m);
+        p1.rho0 = F1(np.rho0);
+        p1.variant = np.variant;
+        p1.collision = np.collision;
+        p1.mag_collision = np.mag_collision;
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            F1 f[9], g[10];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = F1(v[i][k]);
+#pragma unroll
+            for (int q = 0; q < 10; ++q) g[q] = F1(v[9 + q][k]);
+            collide_impl<false, F1, SCALED>(f, g, p1, nullptr);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) v[i][k] = f[i].v;
+#pragma unroll
+            for (int q = 0; q < 10; ++q) v[9 + q][k] = g[q].v;
+        }
+    }
 }
 
 // Equilibrium deviations for given fields (initial state; a1 = 0).

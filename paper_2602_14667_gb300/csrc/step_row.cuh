@@ -77,6 +77,8 @@ __device__ __forceinline__ void step_row(const typename Prec<PREC>::S* __restric
     // Phase 2: decode and apply the +-1 x shift of the moving populations
     // (FP16S values stay in storage units: the collision below runs in them).
     constexpr bool kScaled = PREC == 2;
+    // FP16S: node pairs on FP32x2
+    constexpr int kMode = PREC == 2 ? kPairs : kNative;
     using Codec = StepCodec<S, V>;
     C v[kPlanes][V];
 #pragma unroll
@@ -103,19 +105,7 @@ __device__ __forceinline__ void step_row(const typename Prec<PREC>::S* __restric
         }
     }
     if (!active) return;
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-        C f[9], g[10];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = v[i][k];
-#pragma unroll
-        for (int q = 0; q < 10; ++q) g[q] = v[9 + q][k];
-        collide_impl<false, C, kScaled>(f, g, np, nullptr);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) v[i][k] = f[i];
-#pragma unroll
-        for (int q = 0; q < 10; ++q) v[9 + q][k] = g[q];
-    }
+    collide_nodes<C, V, kScaled, kMode>(v, np);
 #pragma unroll
     for (int p = 0; p < kPlanes; ++p) {
         S r[V];

@@ -55,3 +55,32 @@ def test_reduced_precision_against_fp64(n, tau, amp, steps):
         print(f"  {prec}: rel L2 vs FP64 " + " ".join(f"{k}={v:.2e}" for k, v in errs.items())
               + f"; energy drift {de:+.3e}; cross-helicity drift {s1['cross_hel'] - s0['cross_hel']:+.3e}")
         assert max(errs.values()) < bound
+
+
+@pytest.mark.parametrize("wall_y", [False, True])
+def test_fp16s_launch_shapes_give_the_same_bits(wall_y):
+    """FP16S collides two nodes at once on the packed FP32x2 instructions
+    where a thread holds an even number of nodes, and one node at a time
+    (same fusion of products, same rounding) otherwise and in the in-place
+    phase that pulls.  Every launch shape, two buffers or one, must
+    therefore produce the same state bit for bit."""
+    import mhd_inputs
+    from paper_2602_14667_gb300 import Lattice, MhdError
+    nx, ny = 264, 40
+    f = mhd_inputs.random_spectrum(nx, ny, 7, 0.04, 0.04, kmax=6)
+    states = {}
+    shapes = {False: [(1, 4), (2, 8), (4, 2), (4, 16)],
+              True: [(1, 4), (2, 8), (4, 2), (4, 8)]}    # in place: at most 8 rows per block
+    for in_place in (False, True):
+        for shape in shapes[in_place]:
+            with Lattice(nx, ny, 0.53, 0.62, precision="fp16s", wall_y=wall_y, in_place=in_place) as lat:
+                lat.kernel_config = shape
+                lat.set_fields(*f)
+                lat.advance(75)
+                states[(in_place, shape)] = lat.get_state()
+    ref = states[(False, (1, 4))]
+    for k, s in states.items():
+        assert np.array_equal(s, ref), k
+    with Lattice(nx, ny, 0.53, 0.62, precision="fp16s", in_place=True) as lat:
+        with pytest.raises(MhdError):
+            lat.kernel_config = (4, 16)
