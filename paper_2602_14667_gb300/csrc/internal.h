@@ -55,9 +55,11 @@ cudaError_t launch_plane_in(const Layout& L, int prec, void* buf, int p, double 
 
 // Diagnostics.  mode 0: gather the pre-collision state from `prev` (the
 // buffer the last step read); mode 1: use `cur` in place, with the
-// magnetic non-equilibrium scaled by neq_scale.  Writes kDiagSlots doubles
-// per block into `partials`, then reduces them in a fixed order into
-// `totals` (kDiagSlots doubles).
+// magnetic non-equilibrium scaled by neq_scale.  A persistent grid of at
+// most diag_blocks(L) blocks walks the 32 x 8 node tiles; each block writes
+// kDiagSlots doubles into `partials`, then they are reduced in a fixed order
+// into `totals` (kDiagSlots doubles).  diag_blocks(L) (the tile count) is
+// the room `partials` must have.
 constexpr int kDiagSlots = 13;
 struct DiagLaunch {
     Layout L;
