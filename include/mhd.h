@@ -308,9 +308,10 @@ mhd_status mhd_mlp_fit_normalisation(mhd_mlp* m, const float* X, const float* T,
 mhd_status mhd_mlp_gradients(mhd_mlp* m, const float* X, const float* T, long long n, float* grad_host,
                              double* loss);
 /* Mini-batch Adam (beta1 0.9, beta2 0.999, eps 1e-8) over `epochs`
- * passes of a SplitMix64(seed)-shuffled data set; *last_epoch_loss (may be
- * NULL) is the mean batch loss of the last pass.  MHD_EUNSTABLE if it is
- * not finite. */
+ * passes of the data set, each in a different pseudo-random order (a
+ * bijection of the sample indices computed on the GPU, keyed by seed and
+ * the Adam step count); *last_epoch_loss (may be NULL) is the mean batch
+ * loss of the last pass.  MHD_EUNSTABLE if it is not finite. */
 mhd_status mhd_mlp_train(mhd_mlp* m, const float* X, const float* T, long long n, int epochs, int batch,
                          float lr, unsigned long long seed, double* last_epoch_loss);
 /* Y (n x 3, device) = dA predicted for the features X (n x 24, device). */

@@ -221,106 +221,6 @@ __global__ void mlp_fwd(const bf16* __restrict__ A, const bf16* __restrict__ Wt,
     }
 }
 
-// dH = (dZ (M x NO) * W^T) masked by relu'(Zprev), W stored input-major
-// (KI x NO).  Writes FP32 and BF16 copies.
-template <int NO, int KI>
-__global__ void mlp_bwd_data(const bf16* __restrict__ dZ, const bf16* __restrict__ W,
-                             const float* __restrict__ Zprev, int M, float* __restrict__ dH,
-                             bf16* __restrict__ dHb) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int mt = warp; mt * 16 < M; mt += nwarps) {
-        const int m0 = mt * 16;
-        uint32_t a[NO / 16][4];
-#pragma unroll
-        for (int c = 0; c < NO / 16; ++c) {
-            a[c][0] = ld2(dZ + (long long)(m0 + g) * NO + 16 * c + 2 * t);
-            a[c][1] = ld2(dZ + (long long)(m0 + g + 8) * NO + 16 * c + 2 * t);
-            a[c][2] = ld2(dZ + (long long)(m0 + g) * NO + 16 * c + 2 * t + 8);
-            a[c][3] = ld2(dZ + (long long)(m0 + g + 8) * NO + 16 * c + 2 * t + 8);
-        }
-#pragma unroll
-        for (int j = 0; j < KI / 8; ++j) {
-            float d[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int c = 0; c < NO / 16; ++c) {
-                const uint32_t b[2] = {ld2(W + (8 * j + g) * NO + 16 * c + 2 * t),
-                                       ld2(W + (8 * j + g) * NO + 16 * c + 2 * t + 8)};
-                mma16816(d, a[c], b);
-            }
-            const long long r0 = (long long)(m0 + g) * KI + 8 * j + 2 * t, r1 = r0 + 8LL * KI;
-            const float v0 = Zprev[r0] > 0.f ? d[0] : 0.f, v1 = Zprev[r0 + 1] > 0.f ? d[1] : 0.f;
-            const float v2 = Zprev[r1] > 0.f ? d[2] : 0.f, v3 = Zprev[r1 + 1] > 0.f ? d[3] : 0.f;
-            dH[r0] = v0; dH[r0 + 1] = v1; dH[r1] = v2; dH[r1 + 1] = v3;
-            *reinterpret_cast<uint32_t*>(dHb + r0) = pack2(v0, v1);
-            *reinterpret_cast<uint32_t*>(dHb + r1) = pack2(v2, v3);
-        }
-    }
-}
-
-// Weight gradient partials: P[block][k][n] = sum over the block's rows m of
-// Act[m][k] * dZ[m][n] (KI x NO), as A = Act^T (rows k, columns m) times
-// B = dZ (rows m, columns n).  8 warps; warp w owns output tiles w, w+8, ...
-constexpr int kWgradWarps = 8;
-template <int KI, int NO>
-__global__ void __launch_bounds__(256) mlp_wgrad(const bf16* __restrict__ Act, const bf16* __restrict__ dZ,
-                                                 int M, int rows_per_block, float* __restrict__ P) {
-    constexpr int KT = KI / 16, NT = NO / 8, TILES = KT * NT;
-    constexpr int PER = (TILES + kWgradWarps - 1) / kWgradWarps;
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, w = threadIdx.x >> 5;
-    float acc[PER][4];
-#pragma unroll
-    for (int u = 0; u < PER; ++u) acc[u][0] = acc[u][1] = acc[u][2] = acc[u][3] = 0.f;
-    const int mb = blockIdx.x * rows_per_block, me = min(M, mb + rows_per_block);
-    for (int m0 = mb; m0 < me; m0 += 16) {
-#pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            const int tile = w + u * kWgradWarps;
-            if (tile >= TILES) break;
-            const int kt = tile / NT, nt = tile % NT;
-            const bf16* a0 = Act + (long long)(m0 + 2 * t) * KI + 16 * kt + g;
-            const uint32_t a[4] = {ld11(a0, a0 + KI), ld11(a0 + 8, a0 + KI + 8),
-                                   ld11(a0 + 8LL * KI, a0 + 9LL * KI),
-                                   ld11(a0 + 8LL * KI + 8, a0 + 9LL * KI + 8)};
-            const bf16* b0 = dZ + (long long)(m0 + 2 * t) * NO + 8 * nt + g;
-            const uint32_t b[2] = {ld11(b0, b0 + NO), ld11(b0 + 8LL * NO, b0 + 9LL * NO)};
-            mma16816(acc[u], a, b);
-        }
-    }
-    float* out = P + (long long)blockIdx.x * KI * NO;
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int tile = w + u * kWgradWarps;
-        if (tile >= TILES) break;
-        const int kt = tile / NT, nt = tile % NT;
-        const int r = 16 * kt + g, c = 8 * nt + 2 * t;
-        out[r * NO + c] = acc[u][0];
-        out[r * NO + c + 1] = acc[u][1];
-        out[(r + 8) * NO + c] = acc[u][2];
-        out[(r + 8) * NO + c + 1] = acc[u][3];
-    }
-}
-
-// Column sums of an FP32 (M x NO) matrix into per-block partials P[block][NO].
-template <int NO>
-__global__ void col_partials(const float* __restrict__ dZ, int M, int rows_per_block, float* __restrict__ P) {
-    const int mb = blockIdx.x * rows_per_block, me = min(M, mb + rows_per_block);
-    for (int c = threadIdx.x; c < NO; c += blockDim.x) {
-        float s = 0.f;
-        for (int m = mb; m < me; ++m) s += dZ[(long long)m * NO + c];
-        P[(long long)blockIdx.x * NO + c] = s;
-    }
-}
-
-// out[i] = sum_b P[b][i] in block order (deterministic).
-__global__ void reduce_partials(const float* __restrict__ P, int nblocks, int width, float* __restrict__ out) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < width; i += gridDim.x * blockDim.x) {
-        float s = 0.f;
-        for (int b = 0; b < nblocks; ++b) s += P[(long long)b * width + i];
-        out[i] = s;
-    }
-}
-
 // Batch assembly: rows idx[r] of X (n x 24, raw) -> xb (rows x 32, bf16,
 // normalised, zero padded), T (n x 3) -> tb (rows x 3); rows beyond nreal zero.
 __global__ void gather_batch(const float* __restrict__ X, const float* __restrict__ T, const int* __restrict__ idx,
@@ -337,66 +237,6 @@ __global__ void gather_batch(const float* __restrict__ X, const float* __restric
         }
 #pragma unroll
         for (int c = 0; c < kOut; ++c) tb[(long long)r * kOut + c] = (ok && T) ? T[s * kOut + c] : 0.f;
-    }
-}
-
-// Loss gradient in scaled output units: dY = 2 (yn - t / out_scale) / (nreal * 3)
-// for real rows / columns (0 elsewhere); loss partial sums per block.
-__global__ void loss_grad(const float* __restrict__ Y, const float* __restrict__ tb, int nreal, int rows,
-                          const float* __restrict__ prm, float* __restrict__ dYf, bf16* __restrict__ dYb,
-                          double* __restrict__ lossp) {
-    __shared__ double red[256];
-    double acc = 0.0;
-    const float inv = 2.0f / (float)(nreal * kOut);
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
-#pragma unroll
-        for (int c = 0; c < kOutPadK; ++c) {
-            float gr = 0.f;
-            if (r < nreal && c < kOut) {
-                const float d = Y[(long long)r * kOutPad + c] - tb[(long long)r * kOut + c] / prm[kOffOutScale + c];
-                acc += (double)d * (double)d;
-                gr = inv * d;
-            }
-            if (c < kOutPad) dYf[(long long)r * kOutPad + c] = gr;
-            dYb[(long long)r * kOutPadK + c] = __float2bfloat16_rn(gr);
-        }
-    }
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) lossp[blockIdx.x] = red[0];
-}
-
-// Adam on the trainable part of the parameter blob.
-// Adam on the FP32 master weights (the normalisation and output-scale
-// entries of the blob are not trained).  The step count t is read from
-// device memory (the training loop runs as a captured graph); tick_kernel
-// advances it.
-__global__ void adam_dev_kernel(float* __restrict__ prm, const float* __restrict__ grad, float* __restrict__ m,
-                                float* __restrict__ v, float lr, float b1, float b2, float eps,
-                                const long long* __restrict__ t) {
-    const float tn = (float)(*t + 1);
-    const float c1 = 1.f - powf(b1, tn), c2 = 1.f - powf(b2, tn);
-    for (int i = kOffW1 + blockIdx.x * blockDim.x + threadIdx.x; i < kBlob; i += gridDim.x * blockDim.x) {
-        const float gi = grad[i];
-        const float mi = b1 * m[i] + (1.f - b1) * gi;
-        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        prm[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-    }
-}
-
-// One thread: t += 1, and the batch's loss partials added in a fixed order.
-__global__ void tick_kernel(long long* t, const double* __restrict__ lossp, int nb, double* acc) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        *t += 1;
-        double s = *acc;
-        for (int b = 0; b < nb; ++b) s += lossp[b];
-        *acc = s;
     }
 }
 
@@ -743,80 +583,11 @@ cudaError_t launch_targets(const float* sT, const float* sT1, int nx, int ny, do
 // ---- training driver pieces ------------------------------------------------------
 
 
-__global__ void assemble_grad(const MlpDev d, float* __restrict__ grad);
-
-cudaError_t mlp_forward_backward(const MlpDev& d, const float* prm, int rows, int nreal, bool backward,
-                                 float* grad, double* lossp, int lossblocks, cudaStream_t st) {
-    const int fwd_blocks = std::max(1, std::min((rows / 16 + 7) / 8, 152 * 8));
-    mlp_fwd<kInPad, kHid, true><<<fwd_blocks, 256, 0, st>>>(d.xb, d.Wt1, d.b1, rows, d.Z1, d.H1);
-    mlp_fwd<kHid, kHid, true><<<fwd_blocks, 256, 0, st>>>(d.H1, d.Wt2, d.b2, rows, d.Z2, d.H2);
-    mlp_fwd<kHid, kOutPad, false><<<fwd_blocks, 256, 0, st>>>(d.H2, d.Wt3, d.b3, rows, d.Y, nullptr);
-    loss_grad<<<lossblocks, 256, 0, st>>>(d.Y, d.tb, nreal, rows, prm, d.dYf, d.dYb, lossp);
-    if (!backward) return cudaGetLastError();
-    // weight gradients: at least 128 rows per block, at most kMaxWgradBlocks
-    // per-block partials (reduced in a fixed order)
-    const int per = (rows + kMaxWgradBlocks - 1) / kMaxWgradBlocks;
-    const int rpb = std::max(128, (per + 15) / 16 * 16);
-    const int wb = (rows + rpb - 1) / rpb;
-    // layer 3
-    mlp_wgrad<kHid, kOutPadK><<<wb, 256, 0, st>>>(d.H2, d.dYb, rows, rpb, d.part);
-    reduce_partials<<<8, 256, 0, st>>>(d.part, wb, kHid * kOutPadK, d.gW3);
-    col_partials<kOutPad><<<wb, 32, 0, st>>>(d.dYf, rows, rpb, d.part);
-    reduce_partials<<<1, 32, 0, st>>>(d.part, wb, kOutPad, d.gb3);
-    mlp_bwd_data<kOutPadK, kHid><<<fwd_blocks, 256, 0, st>>>(d.dYb, d.W3, d.Z2, rows, d.dH2f, d.dH2b);
-    // layer 2
-    mlp_wgrad<kHid, kHid><<<wb, 256, 0, st>>>(d.H1, d.dH2b, rows, rpb, d.part);
-    reduce_partials<<<16, 256, 0, st>>>(d.part, wb, kHid * kHid, d.gW2);
-    col_partials<kHid><<<wb, 64, 0, st>>>(d.dH2f, rows, rpb, d.part);
-    reduce_partials<<<1, 64, 0, st>>>(d.part, wb, kHid, d.gb2);
-    mlp_bwd_data<kHid, kHid><<<fwd_blocks, 256, 0, st>>>(d.dH2b, d.W2, d.Z1, rows, d.dH1f, d.dH1b);
-    // layer 1
-    mlp_wgrad<kInPad, kHid><<<wb, 256, 0, st>>>(d.xb, d.dH1b, rows, rpb, d.part);
-    reduce_partials<<<8, 256, 0, st>>>(d.part, wb, kInPad * kHid, d.gW1);
-    col_partials<kHid><<<wb, 64, 0, st>>>(d.dH1f, rows, rpb, d.part);
-    reduce_partials<<<1, 64, 0, st>>>(d.part, wb, kHid, d.gb1);
-    // assemble the blob-layout gradient
-    assemble_grad<<<(kBlob + 255) / 256, 256, 0, st>>>(d, grad);
-    return cudaGetLastError();
-}
-
-__global__ void assemble_grad(const MlpDev d, float* __restrict__ grad) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= kBlob) return;
-    float v = 0.f;
-    if (i >= kOffW1 && i < kOffB1) {
-        const int k = (i - kOffW1) / kHid, o = (i - kOffW1) % kHid;
-        v = d.gW1[k * kHid + o];
-    } else if (i >= kOffB1 && i < kOffW2) {
-        v = d.gb1[i - kOffB1];
-    } else if (i >= kOffW2 && i < kOffB2) {
-        v = d.gW2[i - kOffW2];
-    } else if (i >= kOffB2 && i < kOffW3) {
-        v = d.gb2[i - kOffB2];
-    } else if (i >= kOffW3 && i < kOffB3) {
-        const int k = (i - kOffW3) / kOut, o = (i - kOffW3) % kOut;
-        v = d.gW3[k * kOutPadK + o];
-    } else if (i >= kOffB3) {
-        v = d.gb3[i - kOffB3];
-    }
-    grad[i] = v;
-}
 
 cudaError_t launch_gather_batch(const float* X, const float* T, const int* idx, int nreal, int rows,
                                 const float* prm, const MlpDev& d, cudaStream_t st) {
     const int blocks = std::max(1, std::min((rows + 255) / 256, 152 * 8));
     gather_batch<<<blocks, 256, 0, st>>>(X, T, idx, nreal, rows, prm, d.xb, d.tb);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_adam_dev(float* prm, const float* grad, float* m, float* v, float lr, float b1, float b2,
-                            float eps, const long long* t, cudaStream_t st) {
-    adam_dev_kernel<<<24, 256, 0, st>>>(prm, grad, m, v, lr, b1, b2, eps, t);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_tick(long long* t, const double* lossp, int nb, double* acc, cudaStream_t st) {
-    tick_kernel<<<1, 32, 0, st>>>(t, lossp, nb, acc);
     return cudaGetLastError();
 }
 

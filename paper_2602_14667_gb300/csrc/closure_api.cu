@@ -39,7 +39,6 @@ unsigned long long splitmix(unsigned long long& s) {
 }
 double uniform01(unsigned long long& s) { return (double)(splitmix(s) >> 11) * (1.0 / 9007199254740992.0); }
 
-constexpr int kLossBlocks = 64;
 constexpr int kStatBlocks = 256;
 
 }  // namespace
@@ -49,8 +48,9 @@ struct mhd_mlp {
     cudaStream_t stream = nullptr;
     int max_rows = 0;
     float *prm = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
-    double* lossp = nullptr;
     double* statp = nullptr;
+    float* tpart = nullptr;      // per-block gradient partials of a training step
+    double* tlossp = nullptr;    // per-block loss sums of a training step
     long long* t_d = nullptr;    // Adam step count while a training graph runs
     double* loss_acc = nullptr;  // the epoch's loss, summed on the device
     cudaStream_t cap = nullptr;  // private stream for graph capture
@@ -80,10 +80,11 @@ mhd_status mlp_buffers(mhd_mlp* m) {
     using namespace mhd;
     const size_t R = (size_t)m->max_rows;
     CALLOC(m->prm, kBlob); CALLOC(m->m, kBlob); CALLOC(m->v, kBlob); CALLOC(m->grad, kBlob);
-    CALLOC(m->lossp, kLossBlocks);
     CALLOC(m->t_d, 1);
     CALLOC(m->loss_acc, 1);
     CALLOC(m->statp, (size_t)kStatBlocks * 2 * (kIn + kOut));
+    CALLOC(m->tpart, (size_t)train_blocks(m->max_rows) * kBlob);
+    CALLOC(m->tlossp, (size_t)train_blocks(m->max_rows));
     MlpDev& d = m->d;
     CALLOC(d.Wt1, kHid * kInPad); CALLOC(d.W1, kInPad * kHid);
     CALLOC(d.Wt2, kHid * kHid); CALLOC(d.W2, kHid * kHid);
@@ -92,13 +93,7 @@ mhd_status mlp_buffers(mhd_mlp* m) {
     CALLOC(d.xb, R * kInPad); CALLOC(d.tb, R * kOut);
     CALLOC(d.Z1, R * kHid); CALLOC(d.H1, R * kHid);
     CALLOC(d.Z2, R * kHid); CALLOC(d.H2, R * kHid);
-    CALLOC(d.Y, R * kOutPad); CALLOC(d.dYf, R * kOutPad); CALLOC(d.dYb, R * kOutPadK);
-    CALLOC(d.dH2f, R * kHid); CALLOC(d.dH2b, R * kHid);
-    CALLOC(d.dH1f, R * kHid); CALLOC(d.dH1b, R * kHid);
-    CALLOC(d.part, (size_t)(mhd::kMaxWgradBlocks + 1) * kHid * kHid);
-    CALLOC(d.gW1, kInPad * kHid); CALLOC(d.gb1, kHid);
-    CALLOC(d.gW2, kHid * kHid); CALLOC(d.gb2, kHid);
-    CALLOC(d.gW3, kHid * kOutPadK); CALLOC(d.gb3, kOutPad);
+    CALLOC(d.Y, R * kOutPad);
     return MHD_OK;
 }
 
@@ -143,6 +138,7 @@ mhd_status mhd_mlp_create(unsigned long long seed, int max_batch, void* stream, 
     m->max_rows = rows_of(max_batch);
     cudaError_t e = cudaGetDevice(&m->dev);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = mhd::prepare_train_kernels();
     mhd_status s = e == cudaSuccess ? mlp_buffers(m) : ccuda(e, "mhd_mlp_create");
     if (s == MHD_OK) {
         std::vector<float> p = initial_params(seed);
@@ -206,13 +202,13 @@ mhd_status mhd_mlp_gradients(mhd_mlp* m, const float* X, const float* T, long lo
     if (!m || !X || !T || !grad_host) return cfail(MHD_EINVAL, "NULL argument");
     if (n < 1 || n > m->max_rows) return cfail(MHD_EINVAL, "n must be in [1, max_batch]");
     CCK(cudaSetDevice(m->dev), "cudaSetDevice");
-    const int rows = rows_of(n);
-    CCK(mhd::launch_gather_batch(X, T, nullptr, (int)n, rows, m->prm, m->d, m->stream), "gather");
-    CCK(mhd::mlp_forward_backward(m->d, m->prm, rows, (int)n, true, m->grad, m->lossp, kLossBlocks, m->stream),
+    const int rows = rows_of(n), nblk = mhd::train_blocks(rows);
+    CCK(mhd::launch_train_step(X, T, nullptr, (int)n, rows, m->prm, m->d, m->tpart, m->tlossp, nullptr, m->grad,
+                               m->m, m->v, 0.f, nullptr, false, m->stream),
         "forward / backward");
     CCK(cudaMemcpyAsync(grad_host, m->grad, sizeof(float) * mhd::kBlob, cudaMemcpyDeviceToHost, m->stream), "D2H");
-    double lp[kLossBlocks];
-    CCK(cudaMemcpyAsync(lp, m->lossp, sizeof lp, cudaMemcpyDeviceToHost, m->stream), "D2H loss");
+    std::vector<double> lp((size_t)nblk);
+    CCK(cudaMemcpyAsync(lp.data(), m->tlossp, sizeof(double) * nblk, cudaMemcpyDeviceToHost, m->stream), "D2H loss");
     CCK(cudaStreamSynchronize(m->stream), "mhd_mlp_gradients");
     double s = 0;
     for (double v : lp) s += v;
@@ -220,25 +216,22 @@ mhd_status mhd_mlp_gradients(mhd_mlp* m, const float* X, const float* T, long lo
     return MHD_OK;
 }
 
-// One epoch's batches -- gather, forward, backward, Adam (step count on the
-// device), weight refresh, loss accumulation -- recorded once as a CUDA graph
-// and replayed every epoch after the new permutation is uploaded: the step
-// is some twenty small kernels, so launching them one by one cost more than
-// running them.
-static cudaError_t capture_epoch(mhd_mlp* m, const float* X, const float* T, const int* idx, long long n,
-                                 int batch, float lr, cudaGraphExec_t* exec) {
+// One epoch -- the sample order (a keyed permutation computed on the GPU),
+// then two kernels per batch: the fused forward / backward / weight-gradient
+// pass and the Adam update with the weight refresh and the loss
+// accumulation (step count on the device) -- recorded once as a CUDA graph
+// and replayed every epoch.
+static cudaError_t capture_epoch(mhd_mlp* m, const float* X, const float* T, int* idx, long long n, int batch,
+                                 float lr, unsigned long long seed, cudaGraphExec_t* exec) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(m->loss_acc, 0, sizeof(double), m->cap);
+    if (e == cudaSuccess) e = mhd::launch_epoch_permutation(idx, n, seed, m->t_d, m->cap);
     for (long long b0 = 0; b0 < n && e == cudaSuccess; b0 += batch) {
         const int nb = (int)std::min<long long>(batch, n - b0), rows = rows_of(nb);
-        e = mhd::launch_gather_batch(X, T, idx + b0, nb, rows, m->prm, m->d, m->cap);
-        if (e == cudaSuccess)
-            e = mhd::mlp_forward_backward(m->d, m->prm, rows, nb, true, m->grad, m->lossp, kLossBlocks, m->cap);
-        if (e == cudaSuccess) e = mhd::launch_adam_dev(m->prm, m->grad, m->m, m->v, lr, 0.9f, 0.999f, 1e-8f, m->t_d, m->cap);
-        if (e == cudaSuccess) e = mhd::launch_refresh(m->prm, m->d, m->cap);
-        if (e == cudaSuccess) e = mhd::launch_tick(m->t_d, m->lossp, kLossBlocks, m->loss_acc, m->cap);
+        e = mhd::launch_train_step(X, T, idx + b0, nb, rows, m->prm, m->d, m->tpart, m->tlossp, m->t_d, m->grad,
+                                   m->m, m->v, lr, m->loss_acc, true, m->cap);
     }
     const cudaError_t ee = cudaStreamEndCapture(m->cap, &g);
     if (e == cudaSuccess) e = ee;
@@ -256,23 +249,13 @@ mhd_status mhd_mlp_train(mhd_mlp* m, const float* X, const float* T, long long n
     CCK(cudaSetDevice(m->dev), "cudaSetDevice");
     int* idx = nullptr;
     CCK(cudaMalloc(&idx, sizeof(int) * n), "cudaMalloc(index)");
-    std::vector<int> perm((size_t)n);
-    for (long long i = 0; i < n; ++i) perm[(size_t)i] = (int)i;
-    unsigned long long s = seed;
     // the work so far on the caller's stream comes first; the step count
     // continues from the host copy
     cudaError_t e = cudaStreamSynchronize(m->stream);
     if (e == cudaSuccess) e = cudaMemcpy(m->t_d, &m->t, sizeof(long long), cudaMemcpyHostToDevice);
     cudaGraphExec_t exec = nullptr;
-    if (e == cudaSuccess) e = capture_epoch(m, X, T, idx, n, batch, lr, &exec);
-    for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
-        for (long long i = n - 1; i > 0; --i) {  // Fisher-Yates (while the previous epoch runs)
-            const long long j = (long long)(uniform01(s) * (double)(i + 1));
-            std::swap(perm[(size_t)i], perm[(size_t)std::min(j, i)]);
-        }
-        e = cudaMemcpyAsync(idx, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, m->stream);
-        if (e == cudaSuccess) e = cudaGraphLaunch(exec, m->stream);
-    }
+    if (e == cudaSuccess) e = capture_epoch(m, X, T, idx, n, batch, lr, seed, &exec);
+    for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) e = cudaGraphLaunch(exec, m->stream);
     double acc = 0;
     long long t = m->t;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&acc, m->loss_acc, sizeof(double), cudaMemcpyDeviceToHost, m->stream);

@@ -10,7 +10,6 @@
 namespace mhd {
 
 constexpr int kIn = 24, kInPad = 32, kHid = 64, kOut = 3, kOutPad = 8, kOutPadK = 16;
-constexpr int kMaxWgradBlocks = 256;  // per-block partials of a weight gradient
 // Flat FP32 parameter blob: mean[24] scale[24] out_scale[3] W1[24][64] b1[64]
 // W2[64][64] b2[64] W3[64][3] b3[3]  (weights input-major, W[in][out]).
 constexpr int kOffMean = 0, kOffScale = kOffMean + kIn, kOffOutScale = kOffScale + kIn;
@@ -27,9 +26,8 @@ struct MlpDev {
     float *b1, *b2, *b3;
     __nv_bfloat16* xb;
     float* tb;
-    float *Z1, *Z2, *Y, *dYf, *dH2f, *dH1f;
-    __nv_bfloat16 *H1, *H2, *dYb, *dH2b, *dH1b;
-    float *part, *gW1, *gb1, *gW2, *gb2, *gW3, *gb3;
+    float *Z1, *Z2, *Y;
+    __nv_bfloat16 *H1, *H2;
 };
 
 // What the closure step reads (a lattice-owned copy).
@@ -49,19 +47,29 @@ cudaError_t launch_sgs(const Layout& L, int prec, const void* prev, int r, doubl
 cudaError_t launch_features(const float* state, int nx, int ny, float rho0, float* X, cudaStream_t st);
 cudaError_t launch_targets(const float* sT, const float* sT1, int nx, int ny, double rho0, double omega,
                            float* out, cudaStream_t st);
-cudaError_t mlp_forward_backward(const MlpDev& d, const float* prm, int rows, int nreal, bool backward,
-                                 float* grad, double* lossp, int lossblocks, cudaStream_t st);
 cudaError_t launch_gather_batch(const float* X, const float* T, const int* idx, int nreal, int rows,
                                 const float* prm, const MlpDev& d, cudaStream_t st);
 cudaError_t launch_refresh(const float* prm, const MlpDev& d, cudaStream_t st);
-// Adam with the step count in device memory; then t += 1 and the batch's
-// loss partials added to *acc (one thread, fixed order)
-cudaError_t launch_adam_dev(float* prm, const float* grad, float* m, float* v, float lr, float b1, float b2,
-                            float eps, const long long* t, cudaStream_t st);
-cudaError_t launch_tick(long long* t, const double* lossp, int nb, double* acc, cudaStream_t st);
 cudaError_t launch_stats(const float* X, const float* T, long long n, double* P, int nblocks, float* prm,
                          cudaStream_t st);
 cudaError_t launch_mlp_predict(const MlpDev& d, int rows, int nreal, const float* prm, float* Yraw,
                                cudaStream_t st);
+
+// One training step (mlp_train.cu): a fused forward / backward / weight-
+// gradient kernel over blocks of 128 rows writing per-block partials
+// (train_blocks(rows) x kBlob floats in `part`, one loss sum per block in
+// `lossp`), then a per-parameter kernel that sums them in block order and
+// either applies Adam (adam: step += 1 first; the batch loss is added to
+// *loss_acc) or stores the gradient in `grad`.  prepare_train_kernels sets
+// the fused kernel's shared-memory size once per device.
+int train_blocks(int rows);
+// idx[0..n) = this epoch's order of the samples: a bijection of [0, n)
+// keyed by seed and *step (the Adam step count when the epoch starts).
+cudaError_t launch_epoch_permutation(int* idx, long long n, unsigned long long seed, const long long* step,
+                                     cudaStream_t st);
+cudaError_t prepare_train_kernels();
+cudaError_t launch_train_step(const float* X, const float* T, const int* idx, int nreal, int rows, float* prm,
+                              const MlpDev& d, float* part, double* lossp, long long* step, float* grad, float* m,
+                              float* v, float lr, double* loss_acc, bool adam, cudaStream_t st);
 
 }  // namespace mhd

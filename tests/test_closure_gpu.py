@@ -194,6 +194,31 @@ def test_training_reduces_the_loss():
     assert loss < 0.05 * loss0, (loss0, loss)
 
 
+@pytest.mark.parametrize("n,batch", [(3000, 256), (4096, 1024), (17, 16), (1000, 1000)])
+def test_each_epoch_visits_every_sample_once(n, batch):
+    """The epoch's sample order is a permutation computed on the GPU.  With a
+    learning rate far below the FP32 resolution of the weights, the epoch
+    loss (the batch losses summed over the epoch) must equal the loss of the
+    whole data set in one batch: a repeated or skipped sample would change
+    it.  Sizes cover the cycle-walk (n not a power of four), a power of four,
+    a tiny set and a ragged last batch."""
+    import torch
+
+    from paper_2602_14667_gb300 import _abi
+    X, T = _data(n, 7)
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    Td = torch.tensor(T, dtype=torch.float32, device="cuda")
+    with _abi.MLP(seed=3, max_batch=max(n, batch)) as m:
+        m.fit_normalisation(Xd, Td)
+        ref, _ = m.gradients(Xd, Td)
+        p0 = m.get_params()
+        for ep in (1, 2):
+            loss = m.train(Xd, Td, epochs=ep, batch=batch, lr=1e-30, seed=11)
+            assert abs(loss / ref - 1) < 1e-5, (ep, loss, ref)
+        # (biases that start at zero move by ~1e-29: still nothing at FP32 scale)
+        np.testing.assert_allclose(m.get_params(), p0, rtol=1e-6, atol=1e-20)
+
+
 KINDS = pytest.mark.parametrize("kind", [0, 1], ids=["warp_mma", "tcgen05"])
 
 
