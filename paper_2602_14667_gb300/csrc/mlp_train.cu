@@ -47,6 +47,13 @@ struct TrainShared {
     bf16 dh1[kTR][kSH];
     float bg[kTW][kBG];
     double loss[kTW];
+    // the weights and biases, staged once per block (rows padded as above)
+    bf16 wt1[kHid][kSX];      // W1^T, output-major (forward)
+    bf16 wt2[kHid][kSH];      // W2^T
+    bf16 wt3[kOutPad][kSH];   // W3^T
+    bf16 w3[kHid][kSY];       // W3, input-major (backward)
+    bf16 w2[kHid][kSH];       // W2
+    float b1[kHid], b2[kHid], b3[kOutPad];
 };
 
 __device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const bf16* p) {
@@ -74,13 +81,12 @@ __device__ __forceinline__ float rows_sum(float v) {
 }
 
 // One hidden layer on a 16-row tile: Z = A W^T + b (A as operand fragments
-// over K, W^T output-major in global memory), H = relu(Z) as the next
+// over K, W^T output-major in shared memory), H = relu(Z) as the next
 // layer's operand fragments and in shared memory, mask bit 4j+e = Z > 0.
-template <int KC>
-__device__ __forceinline__ void hidden_layer(const uint32_t (&a)[KC][4], const bf16* __restrict__ Wt,
-                                             const float* __restrict__ bias, int g, int t, bf16 (*sh)[kSH],
+template <int KC, int LD>
+__device__ __forceinline__ void hidden_layer(const uint32_t (&a)[KC][4], const bf16 (*Wt)[LD],
+                                             const float* bias, int g, int t, bf16 (*sh)[kSH],
                                              int r0, uint32_t (&h)[4][4], uint32_t& mask) {
-    constexpr int K = 16 * KC;
     float d[8][4];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -88,8 +94,7 @@ __device__ __forceinline__ void hidden_layer(const uint32_t (&a)[KC][4], const b
         d[j][0] = b0; d[j][1] = b1; d[j][2] = b0; d[j][3] = b1;
 #pragma unroll
         for (int c = 0; c < KC; ++c) {
-            const uint32_t b[2] = {ld2(Wt + (8 * j + g) * K + 16 * c + 2 * t),
-                                   ld2(Wt + (8 * j + g) * K + 16 * c + 2 * t + 8)};
+            const uint32_t b[2] = {ld2(&Wt[8 * j + g][16 * c + 2 * t]), ld2(&Wt[8 * j + g][16 * c + 2 * t + 8])};
             mma16816(d[j], a[c], b);
         }
     }
@@ -112,21 +117,19 @@ __device__ __forceinline__ void hidden_layer(const uint32_t (&a)[KC][4], const b
 }
 
 // Back through a hidden layer: dH = (dZ W^T) masked by the layer's ReLU
-// (W input-major in global memory, dZ as operand fragments over KC chunks);
+// (W input-major in shared memory, dZ as operand fragments over KC chunks);
 // writes BF16 dH to shared memory, its fragments for the layer below, and
 // the column sums of the FP32 dH (bias gradient) to bg.
-template <int KC>
-__device__ __forceinline__ void hidden_back(const uint32_t (&a)[KC][4], const bf16* __restrict__ W, uint32_t mask,
+template <int KC, int LD>
+__device__ __forceinline__ void hidden_back(const uint32_t (&a)[KC][4], const bf16 (*W)[LD], uint32_t mask,
                                             int g, int t, bf16 (*sh)[kSH], int r0, float* bg,
                                             uint32_t (&dh)[4][4]) {
-    constexpr int NO = 16 * KC;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         float d[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int c = 0; c < KC; ++c) {
-            const uint32_t b[2] = {ld2(W + (8 * j + g) * NO + 16 * c + 2 * t),
-                                   ld2(W + (8 * j + g) * NO + 16 * c + 2 * t + 8)};
+            const uint32_t b[2] = {ld2(&W[8 * j + g][16 * c + 2 * t]), ld2(&W[8 * j + g][16 * c + 2 * t + 8])};
             mma16816(d, a[c], b);
         }
 #pragma unroll
@@ -172,35 +175,79 @@ __global__ void __launch_bounds__(kTW * 32) train_block(const float* __restrict_
     const int nrows = min(kTR, rows - blk_row);  // a multiple of 16
     if (step && blockIdx.x == 0 && threadIdx.x == 0) *step += 1;  // Adam's step count
 
+    // stage the weights and biases (16-byte asynchronous copies) while the
+    // rows' inputs are fetched
+    {
+        auto stage = [&](bf16* dst, int dld, const bf16* src, int nrow, int k) {
+            const int chunks = k / 8;  // 8 bf16 per 16 bytes
+            for (int q = threadIdx.x; q < nrow * chunks; q += blockDim.x)
+                cp_async16(dst + (q / chunks) * dld + 8 * (q % chunks), src + (q / chunks) * k + 8 * (q % chunks));
+        };
+        stage(&S.wt1[0][0], kSX, d.Wt1, kHid, kInPad);
+        stage(&S.wt2[0][0], kSH, d.Wt2, kHid, kHid);
+        stage(&S.wt3[0][0], kSH, d.Wt3, kOutPad, kHid);
+        stage(&S.w3[0][0], kSY, d.W3, kHid, kOutPadK);
+        stage(&S.w2[0][0], kSH, d.W2, kHid, kHid);
+        if (threadIdx.x < kHid / 4) {
+            cp_async16(&S.b1[4 * threadIdx.x], d.b1 + 4 * threadIdx.x);
+            cp_async16(&S.b2[4 * threadIdx.x], d.b2 + 4 * threadIdx.x);
+        }
+        if (threadIdx.x < kOutPad / 4) cp_async16(&S.b3[4 * threadIdx.x], d.b3 + 4 * threadIdx.x);
+        cp_async_commit();
+    }
+    // sample index of each of the warp's 16 rows (lane r holds row r's),
+    // then every load of the rows' inputs and targets issued together
+    int my_s = 0;
+    if (lane < 16 && m0 + lane < nreal) my_s = idx ? idx[m0 + lane] : m0 + lane;
+    const int c = 2 * (lane & 15);  // this lane's column pair
+    float xv[8][2];
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+        const int rr = 2 * it + (lane >> 4);
+        const long long sidx = __shfl_sync(kFull, my_s, rr);
+        xv[it][0] = xv[it][1] = 0.f;
+        if (m0 + rr < nreal && c < kIn) {
+            xv[it][0] = X[sidx * kIn + c];
+            xv[it][1] = X[sidx * kIn + c + 1];  // kIn is even
+        }
+    }
+    float tv[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int rr = g + ((e >> 1) << 3), col = 2 * t + (e & 1);
+        const long long sidx = __shfl_sync(kFull, my_s, rr);
+        tv[e] = (m0 + rr < nreal && col < kOut) ? T[sidx * kOut + col] : 0.f;
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+
     double loss = 0.0;
     float* bg = S.bg[w];
     if (m0 < rows) {
-        // gather and normalise the warp's 16 rows (padded columns zero)
-        for (int q = lane; q < 16 * (kInPad / 2); q += 32) {
-            const int rr = q / (kInPad / 2), c = 2 * (q % (kInPad / 2));
-            const int gr = m0 + rr;
-            float v0 = 0.f, v1 = 0.f;
-            if (gr < nreal) {
-                const long long s = idx ? idx[gr] : gr;
-                if (c < kIn) v0 = (X[s * kIn + c] - prm[kOffMean + c]) * prm[kOffScale + c];
-                if (c + 1 < kIn) v1 = (X[s * kIn + c + 1] - prm[kOffMean + c + 1]) * prm[kOffScale + c + 1];
-            }
+        // normalise (padded columns and rows zero)
+        const float mu0 = c < kIn ? prm[kOffMean + c] : 0.f, mu1 = c < kIn ? prm[kOffMean + c + 1] : 0.f;
+        const float sc0 = c < kIn ? prm[kOffScale + c] : 0.f, sc1 = c < kIn ? prm[kOffScale + c + 1] : 0.f;
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            const int rr = 2 * it + (lane >> 4);
+            const bool ok = m0 + rr < nreal && c < kIn;
+            const float v0 = ok ? (xv[it][0] - mu0) * sc0 : 0.f, v1 = ok ? (xv[it][1] - mu1) * sc1 : 0.f;
             *reinterpret_cast<uint32_t*>(&S.x[r0 + rr][c]) = pack2(v0, v1);
         }
         __syncwarp();
         uint32_t a1[2][4];
 #pragma unroll
-        for (int c = 0; c < 2; ++c)
-            ldsm_x4(a1[c], &S.x[r0 + (lane & 7) + (((lane >> 3) & 1) << 3)][16 * c + ((lane >> 4) << 3)]);
+        for (int kc = 0; kc < 2; ++kc)
+            ldsm_x4(a1[kc], &S.x[r0 + (lane & 7) + (((lane >> 3) & 1) << 3)][16 * kc + ((lane >> 4) << 3)]);
         uint32_t h1[4][4], h2[4][4], mask1, mask2;
-        hidden_layer<2>(a1, d.Wt1, d.b1, g, t, S.h1, r0, h1, mask1);
-        hidden_layer<4>(h1, d.Wt2, d.b2, g, t, S.h2, r0, h2, mask2);
+        hidden_layer<2, kSX>(a1, S.wt1, S.b1, g, t, S.h1, r0, h1, mask1);
+        hidden_layer<4, kSH>(h1, S.wt2, S.b2, g, t, S.h2, r0, h2, mask2);
         // output layer and loss gradient (columns 2t, 2t+1 of rows g, g+8)
-        float y[4] = {d.b3[2 * t], d.b3[2 * t + 1], d.b3[2 * t], d.b3[2 * t + 1]};
+        float y[4] = {S.b3[2 * t], S.b3[2 * t + 1], S.b3[2 * t], S.b3[2 * t + 1]};
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const uint32_t b[2] = {ld2(d.Wt3 + g * kHid + 16 * c + 2 * t), ld2(d.Wt3 + g * kHid + 16 * c + 2 * t + 8)};
-            mma16816(y, h2[c], b);
+        for (int cc = 0; cc < 4; ++cc) {
+            const uint32_t b[2] = {ld2(&S.wt3[g][16 * cc + 2 * t]), ld2(&S.wt3[g][16 * cc + 2 * t + 8])};
+            mma16816(y, h2[cc], b);
         }
         const float inv = 2.0f / (float)(nreal * kOut);
 #pragma unroll
@@ -208,8 +255,7 @@ __global__ void __launch_bounds__(kTW * 32) train_block(const float* __restrict_
             const int gr = m0 + g + ((e >> 1) << 3), col = 2 * t + (e & 1);
             float gy = 0.f;
             if (gr < nreal && col < kOut) {
-                const long long s = idx ? idx[gr] : gr;
-                const float dd = y[e] - T[s * kOut + col] / prm[kOffOutScale + col];
+                const float dd = y[e] - tv[e] / prm[kOffOutScale + col];
                 loss += (double)dd * (double)dd;
                 gy = inv * dd;
             }
@@ -228,8 +274,8 @@ __global__ void __launch_bounds__(kTW * 32) train_block(const float* __restrict_
         // back through layer 2 (dZ = dY, 8 real of 16 operand columns) and layer 1
         const uint32_t ady[1][4] = {{dy_lo, dy_hi, 0u, 0u}};
         uint32_t dh2[4][4], dh1[4][4];
-        hidden_back<1>(ady, d.W3, mask2, g, t, S.dh2, r0, bg + kHid, dh2);
-        hidden_back<4>(dh2, d.W2, mask1, g, t, S.dh1, r0, bg, dh1);
+        hidden_back<1, kSY>(ady, S.w3, mask2, g, t, S.dh2, r0, bg + kHid, dh2);
+        hidden_back<4, kSH>(dh2, S.w2, mask1, g, t, S.dh1, r0, bg, dh1);
     } else {
         for (int c = lane; c < kBG; c += 32) bg[c] = 0.f;
     }
@@ -281,25 +327,39 @@ __global__ void __launch_bounds__(kTW * 32) train_block(const float* __restrict_
 
 // Sum of the block partials per parameter; ADAM: update the master weight
 // and its BF16 / bias copies and add the batch loss to *loss_acc; else
-// store the gradient (zero for the untrained normalisation entries).
+// store the gradient (zero for the untrained normalisation entries).  A
+// block takes 32 parameters; warp w sums the partials of blocks w, w + 8,
+// ... and the eight warp sums are added in warp order (a fixed order).
 template <bool ADAM>
-__global__ void train_update(const float* __restrict__ part, int nblk, float* __restrict__ prm,
-                             float* __restrict__ grad, float* __restrict__ m, float* __restrict__ v, float lr,
-                             const long long* __restrict__ step, const double* __restrict__ lossp,
-                             double* __restrict__ loss_acc, const MlpDev d) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ADAM && i == 0) {
+__global__ void __launch_bounds__(256) train_update(const float* __restrict__ part, int nblk, float* __restrict__ prm,
+                                                    float* __restrict__ grad, float* __restrict__ m,
+                                                    float* __restrict__ v, float lr,
+                                                    const long long* __restrict__ step,
+                                                    const double* __restrict__ lossp, double* __restrict__ loss_acc,
+                                                    const MlpDev d) {
+    __shared__ float red[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    if (ADAM && blockIdx.x == 0 && threadIdx.x == 0) {
         double s = *loss_acc;
         for (int b = 0; b < nblk; ++b) s += lossp[b];
         *loss_acc = s;
     }
-    if (i >= kBlob) return;
+    float part_sum = 0.f;
+    if (i >= kOffW1 && i < kBlob) {
+#pragma unroll 4
+        for (int b = w; b < nblk; b += 8) part_sum += part[(long long)b * kBlob + i];
+    }
+    red[w][lane] = part_sum;
+    __syncthreads();
+    if (w != 0 || i >= kBlob) return;
     if (i < kOffW1) {
         if (!ADAM) grad[i] = 0.f;
         return;
     }
-    float gi = 0.f;
-    for (int b = 0; b < nblk; ++b) gi += part[(long long)b * kBlob + i];
+    float gi = red[0][lane];
+#pragma unroll
+    for (int ww = 1; ww < 8; ++ww) gi += red[ww][lane];
     if (!ADAM) {
         grad[i] = gi;
         return;
@@ -404,7 +464,7 @@ cudaError_t launch_train_step(const float* X, const float* T, const int* idx, in
     const int nblk = train_blocks(rows);
     train_block<<<nblk, kTW * 32, sizeof(TrainShared), st>>>(X, T, idx, nreal, rows, prm, d, part, lossp,
                                                              adam ? step : nullptr);
-    const int ub = (kBlob + 255) / 256;
+    const int ub = (kBlob + 31) / 32;
     if (adam)
         train_update<true><<<ub, 256, 0, st>>>(part, nblk, prm, grad, m, v, lr, step, lossp, loss_acc, d);
     else
