@@ -21,6 +21,11 @@ Prints ONE JSON line (rank 0):
 has) on a bounded sample of the same workload.
 Multi-GPU (torchrun): every rank advances its own replica (weak scaling, no
 data-path collective).
+
+Other rows of the path have their own line (--workload): ensemble (512
+lattices in one persistent launch per step), closure (the learned-closure
+study), closure_step (the closure step's cost), diagnostics (the global
+totals) and training (the closure MLP's training).
 """
 from __future__ import annotations
 
@@ -53,9 +58,11 @@ def parse():
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="ot4096", choices=["ot4096", "ensemble", "closure", "closure_step"],
+    ap.add_argument("--workload", default="ot4096", choices=["ot4096", "ensemble", "closure", "closure_step", "diagnostics", "training"],
                     help="ot4096: the headline single lattice; ensemble: 512 random-spectrum "
-                         "lattices in one persistent launch per step")
+                         "lattices in one persistent launch per step; closure: the learned-closure "
+                         "study; closure_step: the closure step's cost; diagnostics: the global "
+                         "totals; training: the closure MLP's training")
     ap.add_argument("--retune", action="store_true",
                     help="time every launch shape instead of using the autotuner's cache")
     ap.add_argument("--shape", default=None,
@@ -83,23 +90,24 @@ def measured_peaks():
 
 # The translation unit of the step kernels (kernels.cu) and what it includes.
 STEP_KERNEL_SOURCES = ("f32x2.cuh", "internal.h", "kernels.cu", "lbm_device.cuh", "step_row.cuh")
+DIAG_KERNEL_SOURCES = ("diag.cu", "f32x2.cuh", "internal.h", "lbm_device.cuh", "step_row.cuh")
 
 
-def kernel_source_hash():
-    """Hash of the step kernel's sources: a profile summary taken from other
+def kernel_source_hash(sources=STEP_KERNEL_SOURCES):
+    """Hash of a kernel's sources: a profile summary taken from other
     sources no longer describes the timed kernel."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2602_14667_gb300", "csrc")
-    for name in STEP_KERNEL_SOURCES:
+    for name in sources:
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled(prec, shape, key):
+def profiled(prec, shape, key, name=None, sources=STEP_KERNEL_SOURCES):
     """A per-node figure from a committed ncu summary, if it was taken from
     the current kernel sources with the same launch shape (else None)."""
-    path = os.path.join(ROOT, "profiles", f"rr_step_{prec}_ncu.md")
+    path = os.path.join(ROOT, "profiles", name or f"rr_step_{prec}_ncu.md")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -108,9 +116,9 @@ def profiled(prec, shape, key):
             if ":" in line and line.startswith("- "):
                 k, v = line[2:].split(":", 1)
                 vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_sha") != kernel_source_hash():
+    if vals.get("kernel_source_sha") != kernel_source_hash(sources):
         return None
-    if vals.get("shape") != f"{shape[0]},{shape[1]}":
+    if shape is not None and vals.get("shape") != f"{shape[0]},{shape[1]}":
         return None
     try:
         return float(vals[key])
@@ -596,6 +604,106 @@ def run_closure_step(args):
     print(json.dumps(res), flush=True)
 
 
+def run_training(args):
+    """Throughput of the closure MLP's training alone: 2,097,152 synthetic
+    samples (24 normal features with a smooth 3-output teacher: the size of
+    the closure study's training set), 8,192-row batches, Adam; one warm-up
+    epoch, then CUDA events around `steps` Adam steps (whole epochs).  Algorithmic work: forward 11,648 flop per sample and the
+    backward pass twice that, against the measured dense BF16 peak.  Each
+    train call records its epoch graph once, so at least 8 epochs are
+    timed."""
+    import torch
+
+    from paper_2602_14667_gb300 import _abi
+    torch.cuda.set_device(0)
+    n, batch = 2097152, 8192
+    per_epoch = (n + batch - 1) // batch
+    epochs = max(8, round(args.steps / per_epoch))  # the per-call set-up is amortised over 8+ epochs
+    g = torch.Generator(device="cuda").manual_seed(0)
+    X = torch.randn((n, 24), device="cuda", generator=g)
+    T = torch.tanh(X @ torch.randn((24, 3), device="cuda", generator=g) * 0.3).contiguous()
+    stream = torch.cuda.current_stream()
+    with _abi.MLP(seed=0, max_batch=batch) as m:
+        m.fit_normalisation(X, T)
+        m.train(X, T, epochs=1, batch=batch, lr=1e-3, seed=1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        with ClockSampler(0) as clk:
+            e0.record(stream)
+            loss = m.train(X, T, epochs=epochs, batch=batch, lr=1e-3, seed=2)
+            e1.record(stream)
+            e1.synchronize()
+        s = e0.elapsed_time(e1) * 1e-3
+    rate = n * epochs / s
+    per_sample = 3 * 2 * (24 * 64 + 64 * 64 + 64 * 3)
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+        peak = float(json.load(fh)["bf16_tflops"])
+    tflops = rate * per_sample / 1e12
+    out = {"metric": "closure MLP training throughput", "value": rate / 1e6, "unit": "M samples/s",
+           "higher_is_better": True, "n_gpus": 1, "steps": epochs * per_epoch, "warmup": per_epoch,
+           "us_per_adam_step": s / (epochs * per_epoch) * 1e6, "dtype": "bf16 (f32 accumulate, f32 Adam)",
+           "data": "synthetic",
+           "config": {"workload": "closure_mlp_training_24_64_64_3", "samples": n, "batch": batch,
+                      "epochs": epochs, "final_epoch_loss": loss},
+           "clocks": clk.summary(), "gpu_launches": epochs * (1 + 2 * per_epoch),
+           "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                        "frac": tflops / peak, "peak_source": "measured bf16 dense (burst)",
+                        "flops_per_sample": per_sample, "traffic": None}}
+    print(json.dumps(out), flush=True)
+
+
+def run_diagnostics(args):
+    """Cost of the global diagnostics (mass, momentum, energies, cross
+    helicity, sum b, div b rms / max, current-density and vorticity maxima):
+    the Orszag-Tang lattice (4096^2 FP32 by default) after `warmup` steps,
+    CUDA events on the lattice's stream around `steps` calls of the totals
+    (each: one persistent kernel over the lattice, the fixed-order final
+    reduction, the copy of the 13 values to the host and the host's wait).
+    The kernel is bound by the FP64 units (FP64 per-node contributions), so
+    the roofline is the FP64 instruction rate."""
+    import torch
+
+    import mhd_inputs
+    from paper_2602_14667_gb300 import Lattice
+    torch.cuda.set_device(0)
+    n, prec = args.n, args.precision
+    stream = torch.cuda.Stream()
+    nodes = n * n
+    with Lattice(n, n, 0.50006, 0.50006, precision=prec, stream=stream.cuda_stream) as lat:
+        lat.set_fields(*mhd_inputs.orszag_tang(n, 0.04, 0.04))
+        lat.advance(max(args.warmup, 1))
+        for _ in range(3):
+            lat.get_totals()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                tot = lat.get_totals()
+            e1.record(stream)
+            e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+    ins = profiled(prec, None, "fp64_instructions_per_node", name=f"diag_kernel_{prec}_ncu.md",
+                   sources=DIAG_KERNEL_SOURCES)
+    roofline = None
+    if ins is not None:
+        rate = ins * nodes / (ms * 1e-3)
+        roofline = {"bound": "alu", "achieved": rate / 1e9, "peak": FP64_INSTR_PEAK / 1e9,
+                    "unit": "G FP64 instructions/s", "frac": rate / FP64_INSTR_PEAK,
+                    "peak_source": "derived: 2 FP64 instructions/clk/SM x 152 SMs x 2.07 GHz",
+                    "fp64_instructions_per_node": ins, "traffic": None,
+                    "note": "per call, including the final reduction, the D2H copy and the host wait"}
+    out = {"metric": "global diagnostics rate", "value": nodes / (ms * 1e-3) / 1e6, "unit": "Mnodes/s",
+           "ms_per_call": ms, "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "dtype": DTYPE[prec] + " (f64 sums)", "data": "synthetic",
+           "config": {"workload": f"diagnostics_orszag_tang_{n}x{n}_{prec}", "nx": n, "ny": n,
+                      "calls": args.steps, "l2": "no flush: the state is far above the 129 MB L2"},
+           "totals_sample": {"mass": tot["mass"], "divb_max": tot["divb_max"], "jz_max": tot["jz_max"]},
+           "clocks": clk.summary(), "gpu_launches": 2 * args.steps, "roofline": roofline}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -606,6 +714,10 @@ def main():
         run_closure(args)
     elif args.workload == "closure_step":
         run_closure_step(args)
+    elif args.workload == "diagnostics":
+        run_diagnostics(args)
+    elif args.workload == "training":
+        run_training(args)
     else:
         run_gb300(args)
 
