@@ -61,9 +61,9 @@ def test_reduced_precision_against_fp64(n, tau, amp, steps):
 def test_fp16s_launch_shapes_give_the_same_bits(wall_y):
     """FP16S collides two nodes at once on the packed FP32x2 instructions
     where a thread holds an even number of nodes, and one node at a time
-    (same fusion of products, same rounding) otherwise and in the in-place
-    phase that pulls.  Every launch shape, two buffers or one, must
-    therefore produce the same state bit for bit."""
+    (same fusion of products, same rounding) where it holds one.  Every
+    launch shape, two buffers or one, must therefore produce the same state
+    bit for bit."""
     import mhd_inputs
     from paper_2602_14667_gb300 import Lattice, MhdError
     nx, ny = 264, 40
