@@ -162,8 +162,10 @@ def test_in_place_rejections():
             _abi.closure_filter(lat, 4, out)
 
 
-def test_in_place_orszag_tang_4096_bitwise_at_the_bench_shape():
-    """The benchmark's workload and launch shape, an odd step count."""
+@pytest.mark.parametrize("prec,code", [("fp32", 1), ("fp16s", 2)])
+def test_in_place_orszag_tang_4096_bitwise_at_the_bench_shapes(prec, code):
+    """The benchmark's workload, an odd step count, in the launch shape the
+    in-place benchmark line times (cached by the autotuner)."""
     import json
     import os
 
@@ -171,12 +173,13 @@ def test_in_place_orszag_tang_4096_bitwise_at_the_bench_shape():
     from paper_2602_14667_gb300 import Lattice
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     with open(os.path.join(root, "paper_2602_14667_gb300", "tune_cache.json")) as fh:
-        shape = tuple(json.load(fh)["NVIDIA GB300|p1|4096x4096|bc00"])
+        cache = json.load(fh)
+    shape = tuple(cache[f"NVIDIA GB300|p{code}|4096x4096|bc00|inplace"])
     n = 4096
     f = mhd_inputs.orszag_tang(n, 0.04, 0.04)
     states = []
     for in_place in (False, True):
-        with Lattice(n, n, 0.50006, 0.50006, precision="fp32", in_place=in_place) as lat:
+        with Lattice(n, n, 0.50006, 0.50006, precision=prec, in_place=in_place) as lat:
             lat.kernel_config = shape
             lat.set_fields(*f)
             lat.advance(601)

@@ -140,6 +140,23 @@ def test_fp64_totals_with_walls(orc):
     _check_totals(got, ref, nx * ny)
 
 
+@pytest.mark.parametrize("wall_y", [False, True])
+def test_fp64_totals_with_many_tiles_per_block(orc, wall_y):
+    """The diagnostics grid holds only the resident blocks, each walking
+    several 32 x 8 tiles: 1000 x 250 nodes is 1024 tiles (ragged in x and
+    y), more than the blocks resident at once."""
+    nx, ny = 1000, 250
+    p = orc.Params(nx, ny, 0.56, 0.71, wall_y=wall_y)
+    fields = _ot(nx, ny)
+    f, g = _oracle_state(orc, p, fields, 10)
+    ref = orc.totals(p, f, g)
+    with _lat(nx, ny, "fp64", 0.56, 0.71, wall_y=wall_y) as lat:
+        lat.set_fields(*fields)
+        lat.advance(10)
+        got = lat.get_totals()
+    _check_totals(got, ref, nx * ny)
+
+
 def test_totals_after_restore_use_the_stored_state(orc):
     """Right after mhd_set_populations the pre-collision g is recovered from
     the stored post-collision one, (g* - g_eq)/(1 - omega_m)."""
