@@ -93,14 +93,20 @@ static cudaError_t launch_aa_t(const StepLaunch& s, int phase, cudaStream_t st) 
     const dim3 block(32, s.BY);
     const int nxb = (s.L.nx + 32 * s.V - 1) / (32 * s.V);
     const int ntiles = nxb * ((s.L.ny + s.BY - 1) / s.BY);
-    // persistent grid: as many blocks as are resident at once
+    // persistent grid: as many blocks as are resident at once, with the
+    // resident warps capped as for the pull step (about 4 KB of every plane
+    // in flight per SM; FP64 uncapped)
+    using S = typename Prec<PREC>::S;
+    const int max_warps = PREC == 0 ? 64 : std::max(1, 4096 / (32 * s.V * (int)sizeof(S)));
+    const int warp_cap = std::max(1, max_warps / s.BY);
     auto go = [&](auto kernel) -> cudaError_t {
         int per_sm = 0, sms = 0, dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * s.BY, 0);
         if (e != cudaSuccess) return e;
-        const int blocks = std::max(1, std::min(ntiles, std::max(1, per_sm) * sms));
+        per_sm = std::min(std::max(1, per_sm), warp_cap);
+        const int blocks = std::max(1, std::min(ntiles, per_sm * sms));
         kernel<<<blocks, block, 0, st>>>(a, nxb, ntiles);
         return cudaGetLastError();
     };

@@ -86,13 +86,22 @@ static cudaError_t launch_step_t(const StepLaunch& s, cudaStream_t st) {
         return cudaGetLastError();
     }
     const int nxb = grid.x, ntiles = grid.x * grid.y;
+    // Resident warps per SM: the DRAM throughput of the storage-bound
+    // kernels peaks with about 4 KB of every plane in flight per SM (warps x
+    // 32 lanes x V elements); more concurrent row streams lose bandwidth
+    // (FP32: 8 warps at V = 4 or 16 at V = 2; FP16S: 16 at V = 4).  FP64 is
+    // bound by its arithmetic and keeps every resident block.
+    using S = typename Prec<PREC>::S;
+    const int max_warps = PREC == 0 ? 64 : std::max(1, 4096 / (32 * s.V * (int)sizeof(S)));
+    const int warp_cap = std::max(1, max_warps / s.BY);
     auto go = [&](auto kernel) -> cudaError_t {
         int per_sm = 0, sms = 0, dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * s.BY, 0);
         if (e != cudaSuccess) return e;
-        const int blocks = std::max(1, std::min(ntiles, std::max(1, per_sm) * sms));
+        per_sm = std::min(std::max(1, per_sm), warp_cap);
+        const int blocks = std::max(1, std::min(ntiles, per_sm * sms));
         kernel<<<blocks, block, 0, st>>>(a, nxb, ntiles);
         return cudaGetLastError();
     };
