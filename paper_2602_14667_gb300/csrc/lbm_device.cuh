@@ -303,14 +303,19 @@ __device__ __forceinline__ void collide_impl(C (&f)[9], C (&g)[10], const NodePa
     // carry a systematic relative bias of ~1e-8 (FP32) in their mass and
     // momentum; left alone it accumulates step after step.  Fold the
     // (algebraically zero) residuals back: x / y momentum into the axis pairs
-    // (2, 6) / (4, 8), mass into the rest population.
-    const C rx = m.mx - ((f[5] + f[6] + f[7]) - (f[1] + f[2] + f[3]));
-    f[6] += C(0.5) * rx;
-    f[2] -= C(0.5) * rx;
-    const C ry = m.my - ((f[1] + f[7] + f[8]) - (f[3] + f[4] + f[5]));
-    f[8] += C(0.5) * ry;
-    f[4] -= C(0.5) * ry;
-    f[0] = m.drho - (((f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8])));
+    // (2, 6) / (4, 8), mass into the rest population.  In FP64 the residual
+    // is ~1e-16 and the fold (about 20 FP64 instructions on units that bound
+    // the FP64 step) is left out.
+    constexpr bool kFold = !std::is_same<C, double>::value;
+    if constexpr (kFold) {
+        const C rx = m.mx - ((f[5] + f[6] + f[7]) - (f[1] + f[2] + f[3]));
+        f[6] += C(0.5) * rx;
+        f[2] -= C(0.5) * rx;
+        const C ry = m.my - ((f[1] + f[7] + f[8]) - (f[3] + f[4] + f[5]));
+        f[8] += C(0.5) * ry;
+        f[4] -= C(0.5) * ry;
+        f[0] = m.drho - (((f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8])));
+    }
     // magnetic BGK (Eq. collide_g): g* = omega_m g_eq + (1 - omega_m) g,
     // g_eq_{j,a} = psi_j [b_a + 3 e_{j,c} (u_c b_a - u_a b_c)], E = ux by - uy bx
     // (linear in b: evaluated in the units of g)
@@ -349,9 +354,22 @@ __device__ __forceinline__ void collide_impl(C (&f)[9], C (&g)[10], const NodePa
         g[9] = gby + omm1 * h24y;
     }
     // rest population by difference: sum_j g*_j = b exactly (psi_0 + 4 psi_1
-    // = 1 + 6e-8 in FP32 would otherwise grow b by ~1e-7 per step)
-    g[0] = Bx - ((g[2] + g[4]) + (g[6] + g[8]));
-    g[1] = By - ((g[3] + g[5]) + (g[7] + g[9]));
+    // = 1 + 6e-8 in FP32 would otherwise grow b by ~1e-7 per step); FP64
+    // relaxes it directly (psi_0 = 1/3; no non-equilibrium kept at j = 0
+    // by the regularised collision)
+    if constexpr (kFold) {
+        g[0] = Bx - ((g[2] + g[4]) + (g[6] + g[8]));
+        g[1] = By - ((g[3] + g[5]) + (g[7] + g[9]));
+    } else {
+        const C q0 = C(1.0 / 3.0);
+        if (p.mag_collision == 0) {
+            g[0] = om * (q0 * Bx) + omm1 * g[0];
+            g[1] = om * (q0 * By) + omm1 * g[1];
+        } else {
+            g[0] = q0 * Bx;
+            g[1] = q0 * By;
+        }
+    }
 }
 
 // How collide_nodes evaluates the collision of a thread's V nodes.
