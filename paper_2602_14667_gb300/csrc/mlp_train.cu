@@ -1,16 +1,17 @@
 // mlp_train.cu -- one training step of the closure MLP (24 -> 64 -> 64 -> 3,
 // ReLU, BF16 operands, FP32 accumulation) as two kernels.
 //
-// train_block: each block takes 128 rows of the batch (one 16-row tile per
-// warp).  A warp gathers and normalises its rows, runs the three layers on
+// train_block: a block takes 128-row slices of the batch (one 16-row tile
+// per warp), one slice per block up to one block per SM, several beyond.  A warp gathers and normalises its rows, runs the three layers on
 // mma.sync fragments with the activations kept in registers (the
 // accumulator fragment of one layer is the operand fragment of the next),
 // forms the loss gradient, and back-propagates through the two hidden
 // layers the same way, the ReLU masks kept as bits.  The activations and
 // gradients of the block's rows are left in shared memory, from which the
-// block computes its share of the three weight gradients (Act^T dZ, loaded
-// transposed by ldmatrix) and writes them, with the bias-gradient column
-// sums and the loss, as one partial per block.
+// block adds the slice's share of the three weight gradients (Act^T dZ,
+// loaded transposed by ldmatrix) to accumulators kept in registers, and at
+// the end writes them, with the bias-gradient column sums and the loss, as
+// one partial per block.
 //
 // train_update: every parameter sums the block partials in block order
 // (deterministic), then either stores the gradient or applies Adam to the
@@ -119,7 +120,7 @@ __device__ __forceinline__ void hidden_layer(const uint32_t (&a)[KC][4], const b
 // Back through a hidden layer: dH = (dZ W^T) masked by the layer's ReLU
 // (W input-major in shared memory, dZ as operand fragments over KC chunks);
 // writes BF16 dH to shared memory, its fragments for the layer below, and
-// the column sums of the FP32 dH (bias gradient) to bg.
+// adds the column sums of the FP32 dH (bias gradient) to bg.
 template <int KC, int LD>
 __device__ __forceinline__ void hidden_back(const uint32_t (&a)[KC][4], const bf16 (*W)[LD], uint32_t mask,
                                             int g, int t, bf16 (*sh)[kSH], int r0, float* bg,
@@ -142,8 +143,8 @@ __device__ __forceinline__ void hidden_back(const uint32_t (&a)[KC][4], const bf
         dh[j >> 1][(j & 1) * 2 + 1] = hi;
         const float s0 = rows_sum(d[0] + d[2]), s1 = rows_sum(d[1] + d[3]);
         if (g == 0) {
-            bg[8 * j + 2 * t] = s0;
-            bg[8 * j + 2 * t + 1] = s1;
+            bg[8 * j + 2 * t] += s0;
+            bg[8 * j + 2 * t + 1] += s1;
         }
     }
 }
@@ -163,7 +164,7 @@ __device__ __forceinline__ void wgrad_tile(const bf16 (*act)[SA], const bf16 (*d
     }
 }
 
-__global__ void __launch_bounds__(kTW * 32) train_block(const float* __restrict__ X, const float* __restrict__ T,
+__global__ void __launch_bounds__(kTW * 32, 1) train_block(const float* __restrict__ X, const float* __restrict__ T,
                                                         const int* __restrict__ idx, int nreal, int rows,
                                                         const float* __restrict__ prm, const MlpDev d,
                                                         float* __restrict__ part, double* __restrict__ lossp,
@@ -171,12 +172,12 @@ __global__ void __launch_bounds__(kTW * 32) train_block(const float* __restrict_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TrainShared& S = *reinterpret_cast<TrainShared*>(smem_raw);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-    const int blk_row = blockIdx.x * kTR, r0 = 16 * w, m0 = blk_row + r0;
-    const int nrows = min(kTR, rows - blk_row);  // a multiple of 16
+    const int r0 = 16 * w;
+    const int nslices = (rows + kTR - 1) / kTR;
     if (step && blockIdx.x == 0 && threadIdx.x == 0) *step += 1;  // Adam's step count
 
-    // stage the weights and biases (16-byte asynchronous copies) while the
-    // rows' inputs are fetched
+    // stage the weights and biases once (16-byte asynchronous copies, waited
+    // for with the first slice's inputs in flight)
     {
         auto stage = [&](bf16* dst, int dld, const bf16* src, int nrow, int k) {
             const int chunks = k / 8;  // 8 bf16 per 16 bytes
@@ -195,122 +196,142 @@ __global__ void __launch_bounds__(kTW * 32) train_block(const float* __restrict_
         if (threadIdx.x < kOutPad / 4) cp_async16(&S.b3[4 * threadIdx.x], d.b3 + 4 * threadIdx.x);
         cp_async_commit();
     }
-    // sample index of each of the warp's 16 rows (lane r holds row r's),
-    // then every load of the rows' inputs and targets issued together
-    int my_s = 0;
-    if (lane < 16 && m0 + lane < nreal) my_s = idx ? idx[m0 + lane] : m0 + lane;
-    const int c = 2 * (lane & 15);  // this lane's column pair
-    float xv[8][2];
+    float* bg = S.bg[w];  // this warp's bias-gradient sums over the block's slices
+    for (int c = lane; c < kBG; c += 32) bg[c] = 0.f;
+    // this warp's weight-gradient tiles (tile w + 8 i), summed over the slices
+    constexpr int kTilesPerWarp = (52 + kTW - 1) / kTW;
+    float wacc[kTilesPerWarp][4];
 #pragma unroll
-    for (int it = 0; it < 8; ++it) {
-        const int rr = 2 * it + (lane >> 4);
-        const long long sidx = __shfl_sync(kFull, my_s, rr);
-        xv[it][0] = xv[it][1] = 0.f;
-        if (m0 + rr < nreal && c < kIn) {
-            xv[it][0] = X[sidx * kIn + c];
-            xv[it][1] = X[sidx * kIn + c + 1];  // kIn is even
-        }
-    }
-    float tv[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const int rr = g + ((e >> 1) << 3), col = 2 * t + (e & 1);
-        const long long sidx = __shfl_sync(kFull, my_s, rr);
-        tv[e] = (m0 + rr < nreal && col < kOut) ? T[sidx * kOut + col] : 0.f;
-    }
-    cp_async_wait<0>();
-    __syncthreads();
-
+    for (int i = 0; i < kTilesPerWarp; ++i) wacc[i][0] = wacc[i][1] = wacc[i][2] = wacc[i][3] = 0.f;
     double loss = 0.0;
-    float* bg = S.bg[w];
-    if (m0 < rows) {
-        // normalise (padded columns and rows zero)
-        const float mu0 = c < kIn ? prm[kOffMean + c] : 0.f, mu1 = c < kIn ? prm[kOffMean + c + 1] : 0.f;
-        const float sc0 = c < kIn ? prm[kOffScale + c] : 0.f, sc1 = c < kIn ? prm[kOffScale + c + 1] : 0.f;
+
+    // a block walks the batch's 128-row slices (grid: at most one block per
+    // SM, so the partials stay few whatever the batch size)
+    for (int slice = blockIdx.x; slice < nslices; slice += gridDim.x) {
+        const int blk_row = slice * kTR, m0 = blk_row + r0;
+        const int nrows = min(kTR, rows - blk_row);  // a multiple of 16
+        // sample index of each of the warp's 16 rows (lane r holds row r's),
+        // then every load of the rows' inputs and targets issued together
+        int my_s = 0;
+        if (lane < 16 && m0 + lane < nreal) my_s = idx ? idx[m0 + lane] : m0 + lane;
+        const int c = 2 * (lane & 15);  // this lane's column pair
+        float xv[8][2];
 #pragma unroll
         for (int it = 0; it < 8; ++it) {
             const int rr = 2 * it + (lane >> 4);
-            const bool ok = m0 + rr < nreal && c < kIn;
-            const float v0 = ok ? (xv[it][0] - mu0) * sc0 : 0.f, v1 = ok ? (xv[it][1] - mu1) * sc1 : 0.f;
-            *reinterpret_cast<uint32_t*>(&S.x[r0 + rr][c]) = pack2(v0, v1);
+            const long long sidx = __shfl_sync(kFull, my_s, rr);
+            xv[it][0] = xv[it][1] = 0.f;
+            if (m0 + rr < nreal && c < kIn) {
+                xv[it][0] = X[sidx * kIn + c];
+                xv[it][1] = X[sidx * kIn + c + 1];  // kIn is even
+            }
         }
-        __syncwarp();
-        uint32_t a1[2][4];
-#pragma unroll
-        for (int kc = 0; kc < 2; ++kc)
-            ldsm_x4(a1[kc], &S.x[r0 + (lane & 7) + (((lane >> 3) & 1) << 3)][16 * kc + ((lane >> 4) << 3)]);
-        uint32_t h1[4][4], h2[4][4], mask1, mask2;
-        hidden_layer<2, kSX>(a1, S.wt1, S.b1, g, t, S.h1, r0, h1, mask1);
-        hidden_layer<4, kSH>(h1, S.wt2, S.b2, g, t, S.h2, r0, h2, mask2);
-        // output layer and loss gradient (columns 2t, 2t+1 of rows g, g+8)
-        float y[4] = {S.b3[2 * t], S.b3[2 * t + 1], S.b3[2 * t], S.b3[2 * t + 1]};
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-            const uint32_t b[2] = {ld2(&S.wt3[g][16 * cc + 2 * t]), ld2(&S.wt3[g][16 * cc + 2 * t + 8])};
-            mma16816(y, h2[cc], b);
-        }
-        const float inv = 2.0f / (float)(nreal * kOut);
+        float tv[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const int gr = m0 + g + ((e >> 1) << 3), col = 2 * t + (e & 1);
-            float gy = 0.f;
-            if (gr < nreal && col < kOut) {
-                const float dd = y[e] - tv[e] / prm[kOffOutScale + col];
-                loss += (double)dd * (double)dd;
-                gy = inv * dd;
-            }
-            y[e] = gy;
+            const int rr = g + ((e >> 1) << 3), col = 2 * t + (e & 1);
+            const long long sidx = __shfl_sync(kFull, my_s, rr);
+            tv[e] = (m0 + rr < nreal && col < kOut) ? T[sidx * kOut + col] : 0.f;
         }
-        const uint32_t dy_lo = pack2(y[0], y[1]), dy_hi = pack2(y[2], y[3]);
-        *reinterpret_cast<uint32_t*>(&S.dy[r0 + g][2 * t]) = dy_lo;
-        *reinterpret_cast<uint32_t*>(&S.dy[r0 + g + 8][2 * t]) = dy_hi;
-        {
-            const float s0 = rows_sum(y[0] + y[2]), s1 = rows_sum(y[1] + y[3]);
-            if (g == 0) {
-                bg[2 * kHid + 2 * t] = s0;
-                bg[2 * kHid + 2 * t + 1] = s1;
+        cp_async_wait<0>();
+        __syncthreads();
+
+        if (m0 < rows) {
+            // normalise (padded columns and rows zero)
+            const float mu0 = c < kIn ? prm[kOffMean + c] : 0.f, mu1 = c < kIn ? prm[kOffMean + c + 1] : 0.f;
+            const float sc0 = c < kIn ? prm[kOffScale + c] : 0.f, sc1 = c < kIn ? prm[kOffScale + c + 1] : 0.f;
+#pragma unroll
+            for (int it = 0; it < 8; ++it) {
+                const int rr = 2 * it + (lane >> 4);
+                const bool ok = m0 + rr < nreal && c < kIn;
+                const float v0 = ok ? (xv[it][0] - mu0) * sc0 : 0.f, v1 = ok ? (xv[it][1] - mu1) * sc1 : 0.f;
+                *reinterpret_cast<uint32_t*>(&S.x[r0 + rr][c]) = pack2(v0, v1);
             }
+            __syncwarp();
+            uint32_t a1[2][4];
+#pragma unroll
+            for (int kc = 0; kc < 2; ++kc)
+                ldsm_x4(a1[kc], &S.x[r0 + (lane & 7) + (((lane >> 3) & 1) << 3)][16 * kc + ((lane >> 4) << 3)]);
+            uint32_t h1[4][4], h2[4][4], mask1, mask2;
+            hidden_layer<2, kSX>(a1, S.wt1, S.b1, g, t, S.h1, r0, h1, mask1);
+            hidden_layer<4, kSH>(h1, S.wt2, S.b2, g, t, S.h2, r0, h2, mask2);
+            // output layer and loss gradient (columns 2t, 2t+1 of rows g, g+8)
+            float y[4] = {S.b3[2 * t], S.b3[2 * t + 1], S.b3[2 * t], S.b3[2 * t + 1]};
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+                const uint32_t b[2] = {ld2(&S.wt3[g][16 * cc + 2 * t]), ld2(&S.wt3[g][16 * cc + 2 * t + 8])};
+                mma16816(y, h2[cc], b);
+            }
+            const float inv = 2.0f / (float)(nreal * kOut);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int gr = m0 + g + ((e >> 1) << 3), col = 2 * t + (e & 1);
+                float gy = 0.f;
+                if (gr < nreal && col < kOut) {
+                    const float dd = y[e] - tv[e] / prm[kOffOutScale + col];
+                    loss += (double)dd * (double)dd;
+                    gy = inv * dd;
+                }
+                y[e] = gy;
+            }
+            const uint32_t dy_lo = pack2(y[0], y[1]), dy_hi = pack2(y[2], y[3]);
+            *reinterpret_cast<uint32_t*>(&S.dy[r0 + g][2 * t]) = dy_lo;
+            *reinterpret_cast<uint32_t*>(&S.dy[r0 + g + 8][2 * t]) = dy_hi;
+            {
+                const float s0 = rows_sum(y[0] + y[2]), s1 = rows_sum(y[1] + y[3]);
+                if (g == 0) {
+                    bg[2 * kHid + 2 * t] += s0;
+                    bg[2 * kHid + 2 * t + 1] += s1;
+                }
+            }
+            // back through layer 2 (dZ = dY, 8 real of 16 operand columns) and layer 1
+            const uint32_t ady[1][4] = {{dy_lo, dy_hi, 0u, 0u}};
+            uint32_t dh2[4][4], dh1[4][4];
+            hidden_back<1, kSY>(ady, S.w3, mask2, g, t, S.dh2, r0, bg + kHid, dh2);
+            hidden_back<4, kSH>(dh2, S.w2, mask1, g, t, S.dh1, r0, bg, dh1);
         }
-        // back through layer 2 (dZ = dY, 8 real of 16 operand columns) and layer 1
-        const uint32_t ady[1][4] = {{dy_lo, dy_hi, 0u, 0u}};
-        uint32_t dh2[4][4], dh1[4][4];
-        hidden_back<1, kSY>(ady, S.w3, mask2, g, t, S.dh2, r0, bg + kHid, dh2);
-        hidden_back<4, kSH>(dh2, S.w2, mask1, g, t, S.dh1, r0, bg, dh1);
-    } else {
-        for (int c = lane; c < kBG; c += 32) bg[c] = 0.f;
+        __syncthreads();
+
+        // weight gradients of the slice: 16 tiles of W1 (32 x 64), 32 of W2
+        // (64 x 64), 4 of W3 (64 x 8); warp w takes tiles w, w + 8, ...
+#pragma unroll
+        for (int i = 0; i < kTilesPerWarp; ++i) {
+            const int tile = w + kTW * i;
+            if (tile < 16)
+                wgrad_tile<kSX, kSH>(S.x, S.dh1, 16 * (tile >> 3), 8 * (tile & 7), nrows, lane, wacc[i]);
+            else if (tile < 48)
+                wgrad_tile<kSH, kSH>(S.h1, S.dh2, 16 * ((tile - 16) >> 3), 8 * ((tile - 16) & 7), nrows, lane,
+                                     wacc[i]);
+            else if (tile < 52)
+                wgrad_tile<kSH, kSY>(S.h2, S.dy, 16 * (tile - 48), 0, nrows, lane, wacc[i]);
+        }
+        __syncthreads();  // the next slice overwrites the shared rows
+    }
+
+    // the block's partial: weight-gradient tiles, bias sums (warps in order), loss
+    float* out = part + (long long)blockIdx.x * kBlob;
+#pragma unroll
+    for (int i = 0; i < kTilesPerWarp; ++i) {
+        const int tile = w + kTW * i;
+        if (tile >= 52) break;
+        int h0, n0, off, ld, kmax, nmax;
+        if (tile < 16) {
+            h0 = 16 * (tile >> 3); n0 = 8 * (tile & 7); off = kOffW1; ld = kHid; kmax = kIn; nmax = kHid;
+        } else if (tile < 48) {
+            h0 = 16 * ((tile - 16) >> 3); n0 = 8 * ((tile - 16) & 7); off = kOffW2; ld = kHid; kmax = kHid; nmax = kHid;
+        } else {
+            h0 = 16 * (tile - 48); n0 = 0; off = kOffW3; ld = kOut; kmax = kHid; nmax = kOut;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int k = h0 + g + ((e >> 1) << 3), n = n0 + 2 * t + (e & 1);
+            if (k < kmax && n < nmax) out[off + k * ld + n] = wacc[i][e];
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) loss += __shfl_down_sync(kFull, loss, o);
     if (lane == 0) S.loss[w] = loss;
     __syncthreads();
-
-    // weight gradients of the block: 16 tiles of W1 (32 x 64), 32 of W2
-    // (64 x 64), 4 of W3 (64 x 8); warp w takes tiles w, w + 8, ...
-    float* out = part + (long long)blockIdx.x * kBlob;
-    for (int tile = w; tile < 52; tile += kTW) {
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        int h0, n0, off, ld, kmax, nmax;
-        if (tile < 16) {
-            h0 = 16 * (tile >> 3); n0 = 8 * (tile & 7);
-            wgrad_tile<kSX, kSH>(S.x, S.dh1, h0, n0, nrows, lane, acc);
-            off = kOffW1; ld = kHid; kmax = kIn; nmax = kHid;
-        } else if (tile < 48) {
-            const int u = tile - 16;
-            h0 = 16 * (u >> 3); n0 = 8 * (u & 7);
-            wgrad_tile<kSH, kSH>(S.h1, S.dh2, h0, n0, nrows, lane, acc);
-            off = kOffW2; ld = kHid; kmax = kHid; nmax = kHid;
-        } else {
-            h0 = 16 * (tile - 48); n0 = 0;
-            wgrad_tile<kSH, kSY>(S.h2, S.dy, h0, n0, nrows, lane, acc);
-            off = kOffW3; ld = kOut; kmax = kHid; nmax = kOut;
-        }
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int k = h0 + g + ((e >> 1) << 3), n = n0 + 2 * t + (e & 1);
-            if (k < kmax && n < nmax) out[off + k * ld + n] = acc[e];
-        }
-    }
-    // bias gradients (warp partials in warp order) and the loss
     for (int c = threadIdx.x; c < kBG; c += blockDim.x) {
         float s = 0.f;
         for (int ww = 0; ww < kTW; ++ww) s += S.bg[ww][c];
@@ -452,7 +473,13 @@ cudaError_t launch_epoch_permutation(int* idx, long long n, unsigned long long s
     return cudaGetLastError();
 }
 
-int train_blocks(int rows) { return (rows + kTR - 1) / kTR; }
+// Blocks of the fused kernel: one per 128-row slice, at most one per SM
+// (it holds 120 KB of shared memory); each block writes one partial.
+int train_blocks(int rows) {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return std::max(1, std::min((rows + kTR - 1) / kTR, sms));
+}
 
 cudaError_t prepare_train_kernels() {
     return cudaFuncSetAttribute(train_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainShared));

@@ -194,7 +194,7 @@ def test_training_reduces_the_loss():
     assert loss < 0.05 * loss0, (loss0, loss)
 
 
-@pytest.mark.parametrize("n,batch", [(3000, 256), (4096, 1024), (17, 16), (1000, 1000)])
+@pytest.mark.parametrize("n,batch", [(3000, 256), (4096, 1024), (17, 16), (1000, 1000), (40000, 32768)])
 def test_each_epoch_visits_every_sample_once(n, batch):
     """The epoch's sample order is a permutation computed on the GPU.  With a
     learning rate far below the FP32 resolution of the weights, the epoch
@@ -217,6 +217,29 @@ def test_each_epoch_visits_every_sample_once(n, batch):
             assert abs(loss / ref - 1) < 1e-5, (ep, loss, ref)
         # (biases that start at zero move by ~1e-29: still nothing at FP32 scale)
         np.testing.assert_allclose(m.get_params(), p0, rtol=1e-6, atol=1e-20)
+
+
+def test_gradients_over_many_slices_per_block():
+    """The fused kernel gives each block one 128-row slice until there are
+    more slices than SMs; then a block walks several and sums them.  The
+    gradient of 40,000 samples (313 slices) must equal the size-weighted
+    combination of the gradients of its two halves (157 and 156 slices at
+    most one per block), up to FP32 summation order."""
+    import torch
+
+    from paper_2602_14667_gb300 import _abi
+    n, n1 = 40000, 20000
+    X, T = _data(n, 11)
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    Td = torch.tensor(T, dtype=torch.float32, device="cuda")
+    with _abi.MLP(seed=4, max_batch=n) as m:
+        m.fit_normalisation(Xd, Td)
+        loss, g = m.gradients(Xd, Td)
+        la, ga = m.gradients(Xd[:n1], Td[:n1])
+        lb, gb = m.gradients(Xd[n1:], Td[n1:])
+    ref = (n1 * ga.astype(np.float64) + (n - n1) * gb.astype(np.float64)) / n
+    assert abs(loss - (n1 * la + (n - n1) * lb) / n) <= 1e-9 * abs(loss)
+    assert np.linalg.norm(g - ref) <= 1e-5 * np.linalg.norm(ref)
 
 
 KINDS = pytest.mark.parametrize("kind", [0, 1], ids=["warp_mma", "tcgen05"])
