@@ -130,3 +130,52 @@ def test_ensemble_draws():
     assert e == mhd_inputs.ensemble(512)
     nodes = sum(d["n"] ** 2 for d in e)
     assert 2.0e7 < nodes < 6.0e7
+
+
+def test_tune_cache_holds_only_valid_launch_shapes():
+    """The autotuner's committed cache (read by mhd_create / mhd_autotune and
+    by the benchmark) may only name shapes the library accepts: 1, 2 or 4
+    nodes per thread dividing nx (at most 2 for FP64), 1..16 rows per block
+    (at most 8 for FP64 and for FP16S in place)."""
+    import json
+    with open(os.path.join(ROOT, "paper_2602_14667_gb300", "tune_cache.json")) as fh:
+        cache = json.load(fh)
+    assert cache
+    for key, (V, BY) in cache.items():
+        gpu, prec, size, bc, *rest = key.split("|")
+        nx = int(size.split("x")[0])
+        p = int(prec[1:])
+        in_place = rest == ["inplace"]
+        assert rest in ([], ["inplace"]) and bc == "bc00", key
+        assert V in (1, 2, 4) and nx % V == 0, key
+        assert 1 <= BY <= 16, key
+        if p == 0:
+            assert V <= 2 and BY <= 8, key
+        if p == 2 and in_place:
+            assert BY <= 8, key
+
+
+def test_bench_reads_profile_keys_only_for_matching_sources_and_shapes():
+    """bench.py reports a kernel's measured DRAM traffic (and the FP64 and
+    diagnostics instruction counts) from the committed ncu summaries only
+    while their recorded source hash and launch shape match."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    h = bench.kernel_source_hash()
+    assert len(h) == 16 and h != bench.kernel_source_hash(bench.DIAG_KERNEL_SOURCES)
+    # a summary with the current hash and shape is read; another shape or hash is not
+    tmp = os.path.join(ROOT, "profiles", f"rr_step_testonly{os.getpid()}_ncu.md")
+    try:
+        with open(tmp, "w") as fh:
+            fh.write(f"- kernel_source_sha: `{h}`\n- shape: `4,1`\n- dram_bytes_per_node: `150.5`\n")
+        name = f"testonly{os.getpid()}"
+        assert bench.profiled(name, (4, 1), "dram_bytes_per_node") == 150.5
+        assert bench.profiled(name, (2, 16), "dram_bytes_per_node") is None
+        assert bench.profiled(name, (4, 1), "missing_key") is None
+        assert bench.profiled(name, (4, 1), "dram_bytes_per_node", sources=bench.DIAG_KERNEL_SOURCES) is None
+        assert bench.profiled_traffic(name, 4096, (4, 1)) == 150.5 * 4096 * 4096
+    finally:
+        os.remove(tmp)
+    assert bench.profiled("nonexistent", (4, 1), "dram_bytes_per_node") is None
