@@ -186,9 +186,21 @@ class MLP:
         yn = h2 @ q(P["W3"]) + P["b3"]
         return yn * P["out_scale"], (a0, z1, h1, z2, h2, yn)
 
-    def loss_and_grads(self, X, T, bf16_like_gpu: bool = False):
+    def loss_and_grads(self, X, T, bf16_like_gpu: bool = False, bf16_backward: bool = False,
+                       scales: bool = False):
         """MSE over all n*3 entries in scaled output units,
-        L = mean((yn - T / out_scale)^2), and its gradients w.r.t. TRAINABLE."""
+        L = mean((yn - T / out_scale)^2), and its gradients w.r.t. TRAINABLE.
+
+        bf16_backward (with bf16_like_gpu) also rounds the back-propagated
+        gradients dY, dH2, dH1 to bfloat16 where they enter a product (the
+        weight gradients Act^T dZ and the next layer's dZ W^T), as the
+        tensor-core kernels do; the bias gradients sum the unrounded values.
+        With scales=True a third dict holds, per parameter, the magnitude
+        every element is a sum of: sum_n |Act_ni| D_nj for a weight and
+        sum_n D_nj for a bias, where D is the gradient propagated with
+        absolute values (|dY|, then (D |W|^T) under the ReLU mask).  A
+        relative rounding of eps in any operand moves an element by at most
+        eps times that magnitude."""
         P = self.p
         _, (a0, z1, h1, z2, h2, yn) = self.forward(X, bf16_like_gpu)
         tn = np.asarray(T, dtype=np.float64) / P["out_scale"]
@@ -197,14 +209,24 @@ class MLP:
         loss = float(np.mean(d * d))
         dy = 2.0 * d / (n * N_OUT)
         q = bf16 if bf16_like_gpu else (lambda a: a)
-        g = {"W3": h2.T @ dy, "b3": dy.sum(axis=0)}
-        dh2 = (dy @ q(P["W3"]).T) * (z2 > 0)
-        g["W2"] = h1.T @ dh2
+        qb = bf16 if (bf16_like_gpu and bf16_backward) else (lambda a: a)
+        dyq = qb(dy)
+        g = {"W3": h2.T @ dyq, "b3": dy.sum(axis=0)}
+        dh2 = (dyq @ q(P["W3"]).T) * (z2 > 0)
+        dh2q = qb(dh2)
+        g["W2"] = h1.T @ dh2q
         g["b2"] = dh2.sum(axis=0)
-        dh1 = (dh2 @ q(P["W2"]).T) * (z1 > 0)
-        g["W1"] = a0.T @ dh1
+        dh1 = (dh2q @ q(P["W2"]).T) * (z1 > 0)
+        g["W1"] = a0.T @ qb(dh1)
         g["b1"] = dh1.sum(axis=0)
-        return loss, g
+        if not scales:
+            return loss, g
+        D3 = np.abs(dy)
+        D2 = (D3 @ np.abs(q(P["W3"])).T) * (z2 > 0)
+        D1 = (D2 @ np.abs(q(P["W2"])).T) * (z1 > 0)
+        s = {"W3": np.abs(h2).T @ D3, "b3": D3.sum(axis=0), "W2": np.abs(h1).T @ D2,
+             "b2": D2.sum(axis=0), "W1": np.abs(a0).T @ D1, "b1": D1.sum(axis=0)}
+        return loss, g, s
 
 
 class Adam:

@@ -155,3 +155,65 @@ def test_sgs_target_trace_is_the_weighted_velocity_variance(orc, clo):
     var = avg(rho * (ux ** 2 + uy ** 2)) - (avg(rho * ux) ** 2 + avg(rho * uy) ** 2) / avg(rho)
     np.testing.assert_allclose(t[:, 0] + t[:, 2], var, rtol=1e-9, atol=1e-15)
     assert (var > 0).all()
+
+
+def test_sgs_target_of_fields_linear_inside_each_block(orc, clo):
+    """Inside each r x r block let the fields be linear in the in-block
+    offsets (i, j), with rho = 1:  u = (alpha j, delta j) + U_B and
+    b = (beta i, gamma i) + B_B, where U_B, B_B are random per-block
+    constants.  Over a block i and j are independent and uniform on
+    {0, ..., r-1} with variance V = (r^2 - 1)/12, so the filtered fluxes
+    minus the fluxes of the filtered fields are the covariances:
+      <uu> - u_bar u_bar = V [[a^2, a d], [a d, d^2]],
+      <M> - M(b_bar) = (1/2) tr(C) I - C,  C = V [[b^2, b g], [b g, g^2]],
+    so tau_xx = V (a^2 + (g^2 - b^2)/2), tau_xy = V (a d - b g),
+    tau_yy = V (d^2 + (b^2 - g^2)/2), and the target is tau / (1 - 1/tau_c).
+    The off-diagonal Maxwell term enters with the sign opposite to the
+    Reynolds term, and the Maxwell diagonal is traceless: a sign or a
+    transposition in either part fails here."""
+    n, r, tau_c = 16, 4, 0.515
+    al, de, be, ga = 0.011, -0.007, 0.013, 0.005
+    p = orc.Params(n, n, 0.6, 0.6)
+    rng = np.random.default_rng(10)
+    X, Y = np.meshgrid(np.arange(n), np.arange(n))
+    i, j = X % r, Y % r
+    const = [np.kron(rng.uniform(-0.02, 0.02, (n // r, n // r)), np.ones((r, r))) for _ in range(4)]
+    f, g = orc.init(p, al * j + const[0], de * j + const[1], be * i + const[2], ga * i + const[3])
+    got = clo.sgs_targets(p, f, g, r, tau_c)
+    V = (r * r - 1) / 12.0
+    want = np.array([V * (al * al + (ga * ga - be * be) / 2), V * (al * de - be * ga),
+                     V * (de * de + (be * be - ga * ga) / 2)]) / (1 - 1 / tau_c)
+    assert abs(want[1]) > 0.5 * np.abs(want).max()
+    np.testing.assert_allclose(got, np.broadcast_to(want, got.shape), rtol=1e-9, atol=1e-16)
+
+
+def test_gradient_scales_bound_the_gradients_and_the_bf16_backward_rounding(clo):
+    """The scales of loss_and_grads are sums of absolute values of the terms
+    each gradient element sums, so |grad| <= scale, with equality when every
+    term has one sign (nonnegative weights and activations and a target
+    below every output make all of them nonnegative).  Rounding the
+    back-propagated operands to bfloat16 (at most 2^-9 relative each, and a
+    weight gradient meets at most three such roundings along its chain)
+    moves every element by less than 3 * 2^-9 of its scale."""
+    rng = np.random.default_rng(12)
+    X = rng.normal(size=(300, clo.N_IN))
+    net = clo.MLP(seed=5)
+    for k in ("W1", "W2", "W3"):
+        net.p[k] = np.abs(net.p[k])
+    net.p["b1"][:] = 0.1
+    net.p["b2"][:] = 0.1
+    Xp = np.abs(X)
+    T = np.full((300, clo.N_OUT), -50.0)
+    _, g, s = net.loss_and_grads(Xp, T, bf16_like_gpu=True, scales=True)
+    for k in clo.TRAINABLE:
+        np.testing.assert_allclose(np.abs(g[k]), s[k], rtol=1e-12, atol=0)
+    net2 = clo.MLP(seed=6)
+    T2 = rng.normal(size=(300, clo.N_OUT))
+    _, g0, s0 = net2.loss_and_grads(X, T2, bf16_like_gpu=True, scales=True)
+    _, gb = net2.loss_and_grads(X, T2, bf16_like_gpu=True, bf16_backward=True)
+    moved = False
+    for k in clo.TRAINABLE:
+        assert (np.abs(g0[k]) <= s0[k] * (1 + 1e-12)).all(), k
+        assert (np.abs(gb[k] - g0[k]) <= 3 * 2.0 ** -9 * s0[k]).all(), k
+        moved |= bool(np.any(gb[k] != g0[k]))
+    assert moved
