@@ -464,7 +464,7 @@ mhd_status mhd_get_totals(mhd_lattice* l, mhd_totals* out) {
     d.neq_scale = d.mode == 0 ? 1.0 : ((l->state_is_eq || std::fabs(om1) < 1e-12) ? 0.0 : 1.0 / om1);
     d.wall_x = l->p.bc_x == MHD_WALL;
     d.wall_y = l->p.bc_y == MHD_WALL;
-    CK(mhd::launch_diag(d, l->partials, l->totals_d, l->stream), "diagnostics kernel");
+    CK(mhd::launch_diag(d, l->partials, mhd::diag_blocks(l->L), l->totals_d, l->stream), "diagnostics kernel");
     CK(cudaMemcpyAsync(l->totals_h, l->totals_d, sizeof(double) * mhd::kDiagSlots,
                        cudaMemcpyDeviceToHost, l->stream),
        "D2H totals");

@@ -406,7 +406,7 @@ mhd_status mhd_batch_get_totals(mhd_batch* b, int index, mhd_totals* out) {
     const double om1 = 1.0 - d.omega_m;
     d.neq_scale = d.mode == 0 ? 1.0 : ((b->is_eq[index] || std::fabs(om1) < 1e-12) ? 0.0 : 1.0 / om1);
     d.wall_x = d.wall_y = 0;
-    BCK(mhd::launch_diag(d, b->partials, b->totals_d, b->stream), "diagnostics kernel");
+    BCK(mhd::launch_diag(d, b->partials, mhd::diag_blocks(L), b->totals_d, b->stream), "diagnostics kernel");
     BCK(cudaMemcpyAsync(b->totals_h, b->totals_d, sizeof(double) * mhd::kDiagSlots, cudaMemcpyDeviceToHost,
                         b->stream),
         "D2H totals");

@@ -2,10 +2,17 @@
 // and magnetic energy, cross helicity, sum of b, div b (rms and max) and the
 // maxima of the current density and the vorticity, reduced on the device in
 // a fixed order.
+//
+// Definitions: the moments of task 1 of the "Algorithm of computation";
+// j_z of Eq. current; the isotropic lattice gradient, the vorticity and the
+// energies E_k = mean |u|^2/2, E_m = mean |b|^2/2 of the Orszag-Tang
+// section.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
+#include <cstdint>
 
 #include "internal.h"
 #include "lbm_device.cuh"
@@ -13,31 +20,92 @@
 
 namespace mhd {
 
-// ---- diagnostics ----------------------------------------------------------
-// Persistent grid (the blocks resident at once, at most one per tile); each
-// block walks 32 x 8 node tiles with a fixed stride.  The moments of a tile
-// plus a one-node halo are staged in shared memory for the isotropic
-// gradient stencil.  Per-node contributions are accumulated in FP64 in
-// registers over all the block's tiles, then reduced once with warp
-// shuffles and across warps in shared memory into kDiagSlots partials per
-// block:
-//   0 mass, 1 mom_x, 2 mom_y, 3 sum |u|^2/2, 4 sum |b|^2/2, 5 sum u.b,
-//   6 sum b_x, 7 sum b_y, 8 sum (div b)^2, 9 #gradient nodes,
+// ---- tiles ------------------------------------------------------------------
+// One warp walks one tile: a strip of 30 V output columns and up to H
+// output rows [y0, y1) (H picked by the launcher so that the tiles are
+// about as many as the resident warps).  Lane l holds the V nodes starting at
+// x0s + l V with x0s = strip * 30 V - V: lanes 1..30 are the tile's own
+// columns, lanes 0 and 31 the one-vector halo on either side, so the x
+// neighbours of every output node arrive by warp shuffles and every load
+// is an aligned vector (periodic x wraps the halo lanes around).  The warp
+// forms the moments of rows y0 - 1 .. y1 one after the other (downwards
+// in even row segments, upwards in odd ones) from the row's 19 planes --
+// read with vector loads, and for the state the last step read with the
+// step's pull gather -- adds the point sums of its output nodes, and keeps
+// u and b of the last three rows in registers; once a row is formed the
+// isotropic gradient stencil of the row before it is evaluated.  Each node
+// is read by one tile, apart from the halo lanes and the two halo rows of
+// each tile, which the neighbouring tiles read at about the same time.  No
+// shared memory and no barrier is needed until the block's final
+// reduction.
+//
+// Arithmetic: FP64 storage keeps every per-node quantity in FP64.  FP32 and
+// FP16S storage form the per-node quantities in FP32; each lane adds them
+// into an FP32 sum with an FP32 compensation term (Knuth's TwoSum recovers
+// the rounding error of every addition exactly), and FP64 enters only in
+// the warp, block and final reductions.  Mass is rho0 times the node count
+// plus the sum of the density deviations, and the momentum is the sum of
+// the first moments sum_i f_i c_i themselves.
+//
+// Per-block partials (kDiagSlots doubles):
+//   0 sum (rho - rho0), 1 mom_x, 2 mom_y, 3 sum |u|^2/2, 4 sum |b|^2/2,
+//   5 sum u.b, 6 sum b_x, 7 sum b_y, 8 sum (div b)^2, 9 #gradient nodes,
 //   10 max |div b|, 11 max |j_z|, 12 max |omega_z|.
-// The FP64 units are the bound (two FP64 instructions per clock per SM), so
-// the count is kept as an integer and the three maxima, all of
-// non-negative values, are taken on the bit patterns of the doubles with
+// The maxima of non-negative values are taken on their bit patterns with
 // integer instructions (a NaN, whose pattern is above every finite value's,
 // reaches the totals).
-constexpr int kDTX = 32, kDTY = 8, kDHX = kDTX + 2, kDHY = kDTY + 2;
+constexpr int kDWarps = 8;                 // warps per block (independent tiles)
+constexpr int kDiagMaxBlocks = 4096;       // upper bound of any grid the launcher picks
 
 template <typename C> struct DiagArgs {
-    const void* prev;
-    const void* cur;
+    const void* src;   // mode 0: the buffer the last step read (gathered); mode 1: the stored state
     int nx, ny;
     long long pitch, plane;
     C omega_m, rho0, neq_scale;
     int wall_x, wall_y;
+    int strips;        // tiles along x (30 V output columns each)
+    int rows;          // output rows per tile (H)
+    int ntiles;
+};
+
+// ---- accumulation helpers -------------------------------------------------
+template <typename C> struct LaneSum {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double take() {
+        const double v = s;
+        s = 0.0;
+        return v;
+    }
+};
+template <> struct LaneSum<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = s + x;
+        const float bv = t - s;
+        const float e = (s - (t - bv)) + (x - bv);
+        s = t;
+        c += e;
+    }
+    __device__ __forceinline__ double take() {
+        const double v = (double)s + (double)c;
+        s = c = 0.f;
+        return v;
+    }
+};
+
+template <typename C> struct AbsBits;
+template <> struct AbsBits<double> {
+    using T = unsigned long long;
+    __device__ __forceinline__ static T of(double v) {
+        return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+    }
+    __device__ __forceinline__ static double value(T b) { return __longlong_as_double((long long)b); }
+};
+template <> struct AbsBits<float> {
+    using T = unsigned int;
+    __device__ __forceinline__ static T of(float v) { return __float_as_uint(v) & 0x7fffffffu; }
+    __device__ __forceinline__ static double value(T b) { return (double)__uint_as_float(b); }
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -53,114 +121,315 @@ __device__ __forceinline__ unsigned long long warp_max_bits(unsigned long long v
     }
     return v;
 }
-__device__ __forceinline__ unsigned long long abs_bits(double v) {
+__device__ __forceinline__ unsigned long long dbits(double v) {
     return (unsigned long long)__double_as_longlong(fabs(v));
 }
 __device__ __forceinline__ unsigned long long max_bits(unsigned long long a, unsigned long long b) {
     return a > b ? a : b;
 }
 
+// ---- one node's moments -----------------------------------------------------
+template <typename C> struct NodeMom {
+    C drho, mx, my, bx, by, ux, uy;
+    C dg;  // (g_3y - g_1y) - (g_4x - g_2x): the e-weighted antisymmetric part entering j_z
+};
+
+// From populations in `unit`s of the deviation (FP16S storage units: 2^-12).
+template <typename C>
+__device__ __forceinline__ NodeMom<C> node_moments(const C (&f)[9], const C (&g)[10], C unit, C rho0) {
+    Moments<C> m;
+    moment_sums(f, g, m);
+    NodeMom<C> n;
+    n.drho = m.drho * unit;
+    n.mx = m.mx * unit;
+    n.my = m.my * unit;
+    n.bx = m.bx * unit;
+    n.by = m.by * unit;
+    const C inv = C(1) / (rho0 + n.drho);
+    n.ux = n.mx * inv;
+    n.uy = n.my * inv;
+    n.dg = ((g[7] - g[3]) - (g[8] - g[4])) * unit;
+    return n;
+}
+
+// Eq. current with g_eq of the node substituted: for D2Q5,
+// sum_j (e_jx g_neq_jy - e_jy g_neq_jx) = dg - 2 (u_x b_y - u_y b_x).
+template <typename C>
+__device__ __forceinline__ C node_current(const NodeMom<C>& n, C omega_m, C neq_scale) {
+    return -C(3) * omega_m * neq_scale * (n.dg - C(2) * (n.ux * n.by - n.uy * n.bx));
+}
+
+// u, b of one node (x, y) inside the lattice, one population at a time:
+// mode 0 gathers the pre-collision state, mode 1 reads the stored one.
 template <int PREC, int MODE>
-__global__ void __launch_bounds__(256) diag_kernel(const DiagArgs<typename Prec<PREC>::C> a, int tiles_x,
-                                                   int ntiles, double* __restrict__ partials) {
+__device__ __forceinline__ NodeMom<typename Prec<PREC>::C> scalar_node(
+    const DiagArgs<typename Prec<PREC>::C>& a, int x, int y) {
     using S = typename Prec<PREC>::S;
     using C = typename Prec<PREC>::C;
-    __shared__ C sm[4][kDHY][kDHX];  // ux, uy, bx, by
-    __shared__ double red[8][kDiagSlots];
-    const int tid = threadIdx.y * kDTX + threadIdx.x;
-    double acc[8];  // slots 0..7
-    double div2 = 0.0;
-    long long cnt = 0;
-    unsigned long long mdiv = 0, mjz = 0, mvort = 0;
+    const S* src = static_cast<const S*>(a.src);
+    C f[9], g[10];
+    if (MODE == 0) {
+        gather_node(src, x, y, a.nx, a.ny, a.pitch, a.plane, a.wall_x, a.wall_y, f, g);
+    } else {
+        const long long o = (long long)y * a.pitch + x;
 #pragma unroll
-    for (int s = 0; s < 8; ++s) acc[s] = 0.0;
+        for (int p = 0; p < kPlanes; ++p) {
+            const C v = decode(src[(long long)p * a.plane + o]);
+            if (p < 9) f[p] = v; else g[p - 9] = v;
+        }
+    }
+    return node_moments(f, g, C(1), a.rho0);
+}
 
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int tx0 = (t % tiles_x) * kDTX, ty0 = (t / tiles_x) * kDTY;
-        for (int r = tid; r < kDHX * kDHY; r += kDTX * kDTY) {
-            const int hx = r % kDHX, hy = r / kDHX;
-            int gx = tx0 - 1 + hx, gy = ty0 - 1 + hy;
-            const bool interior = hx >= 1 && hx <= kDTX && hy >= 1 && hy <= kDTY && gx < a.nx && gy < a.ny;
-            bool have = true;
-            // (a tile may reach several periods past a lattice narrower than it)
-            if (a.wall_x) have = have && gx >= 0 && gx < a.nx;
-            else gx = ((gx % a.nx) + a.nx) % a.nx;
-            if (a.wall_y) have = have && gy >= 0 && gy < a.ny;
-            else gy = ((gy % a.ny) + a.ny) % a.ny;
-            C ux = 0, uy = 0, bx = 0, by = 0;
-            if (have) {
-                C f[9], g[10];
-                if (MODE == 0) {
-                    gather_node(static_cast<const S*>(a.prev), gx, gy, a.nx, a.ny, a.pitch, a.plane,
-                                a.wall_x, a.wall_y, f, g);
-                } else {
-                    const S* b = static_cast<const S*>(a.cur);
-                    const long long o = (long long)gy * a.pitch + gx;
+// Pre-collision populations of the V nodes x0 .. x0+V-1 of row y pulled
+// from the post-collision buffer src, where the lanes of the warp hold
+// consecutive vectors modulo nx (x0 wrapped into [0, nx), nx % V == 0):
+// the step's gather (step_row.cuh) with the warp's edge elements taken at
+// the wrapped neighbours.  FP16S values stay in storage units.
+template <int PREC, int V, bool WALLY>
+__device__ __forceinline__ void gather_row_wrapped(const typename Prec<PREC>::S* __restrict__ src, int nx,
+                                                   int ny, long long pitch, long long plane, int x0, int y,
+                                                   int lane, typename Prec<PREC>::C (&v)[kPlanes][V]) {
+    using S = typename Prec<PREC>::S;
+    using C = typename Prec<PREC>::C;
+    int ym = y - 1, yp = y + 1;
+    bool bm = false, bp = false;
+    if (WALLY) {
+        bm = ym < 0;
+        bp = yp >= ny;
+    } else {
+        if (ym < 0) ym += ny;
+        if (yp >= ny) yp -= ny;
+    }
+    const int xl = x0 == 0 ? nx - 1 : x0 - 1;
+    const int xr = x0 + V >= nx ? x0 + V - nx : x0 + V;
+    const long long o_m = (long long)ym * pitch, o_0 = (long long)y * pitch, o_p = (long long)yp * pitch;
+    S r[kPlanes][V];
+    S edge[kPlanes];
 #pragma unroll
-                    for (int p = 0; p < kPlanes; ++p) {
-                        const C val = decode(b[(long long)p * a.plane + o]);
-                        if (p < 9) f[p] = val; else g[p - 9] = val;
+    for (int p = 0; p < kPlanes; ++p) {
+        const int cx = pcx(p), cy = pcy(p);
+        const bool bounce = WALLY && (cy > 0 ? bm : (cy < 0 ? bp : false));  // warp-uniform
+        const S* row = src + (bounce ? (long long)popp(p) * plane + o_0
+                                     : (long long)p * plane + (cy > 0 ? o_m : (cy < 0 ? o_p : o_0)));
+        VecIO<S, V>::load(row + x0, r[p]);
+        edge[p] = S(0);
+        if (cx > 0 && !bounce && lane == 0) edge[p] = row[xl];
+        if (cx < 0 && !bounce && lane == 31) edge[p] = row[xr];
+    }
+    using Codec = StepCodec<S, V>;
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        const int cx = pcx(p), cy = pcy(p);
+        const bool bounce = WALLY && (cy > 0 ? bm : (cy < 0 ? bp : false));
+        C c[V];
+        Codec::to_compute(r[p], c);
+        if (cx == 0 || bounce) {
+#pragma unroll
+            for (int k = 0; k < V; ++k) v[p][k] = c[k];
+        } else if (cx > 0) {  // source x - 1
+            C left = __shfl_up_sync(kFull, c[V - 1], 1);
+            if (lane == 0) left = Codec::template one<C>(edge[p]);
+            v[p][0] = left;
+#pragma unroll
+            for (int k = 1; k < V; ++k) v[p][k] = c[k - 1];
+        } else {  // source x + 1
+            C right = __shfl_down_sync(kFull, c[0], 1);
+            if (lane == 31) right = Codec::template one<C>(edge[p]);
+#pragma unroll
+            for (int k = 0; k < V - 1; ++k) v[p][k] = c[k + 1];
+            v[p][V - 1] = right;
+        }
+    }
+}
+
+// ---- the tile kernel --------------------------------------------------------
+// V: nodes per lane (vector loads; V = 1 also for lattices whose nx is not
+// a multiple of the vector width).  GEN: x walls, one node per lane, every
+// node gathered one population at a time (nodes outside the lattice are
+// left at zero and never enter a valid stencil).  WALLY: y walls in the
+// vector gather of mode 0.
+// Launch bounds: FP32 and FP16S keep two blocks per SM (at most 128
+// registers, twice the rows in flight), FP16S with four nodes per lane
+// (8-byte loads; its register cap spills a little: 0.23 against 0.29 ms per
+// totals call at 4096^2 with one block per SM), FP32 with two (at four:
+// 0.29 against 0.26 ms).  FP64 is bound by its arithmetic.
+template <int PREC, int V, int MODE, bool WALLY, bool GEN>
+__global__ void __launch_bounds__(kDWarps * 32, PREC == 0 ? 1 : 2) diag_kernel(const DiagArgs<typename Prec<PREC>::C> a,
+                                                            double* __restrict__ partials) {
+    using S = typename Prec<PREC>::S;
+    using C = typename Prec<PREC>::C;
+    using MB = AbsBits<C>;
+    constexpr int WO = 30 * V;  // output columns per tile
+    __shared__ double red[kDWarps][kDiagSlots];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gw = blockIdx.x * kDWarps + warp, nw = gridDim.x * kDWarps;
+    // FP16S vector loads keep the step's storage units (2^12 x deviation)
+    const C unit = (PREC == 2 && !GEN) ? C(kHalfInvScale) : C(1);
+    const bool out_lane = lane >= 1 && lane <= 30;
+
+    LaneSum<C> ls[9];  // slots 0..8
+    long long cnt = 0;
+    typename MB::T mdiv = 0, mjz = 0, mvort = 0;
+
+    for (int t = gw; t < a.ntiles; t += nw) {
+        const int strip = t % a.strips, seg = t / a.strips;
+        const int xl = strip * WO - V + lane * V;  // the lane's first node (may lie outside)
+        int xw = xl;                               // ... wrapped (periodic x)
+        if (!GEN) {
+            xw %= a.nx;
+            if (xw < 0) xw += a.nx;
+        }
+        const int y0 = seg * a.rows, y1 = min(a.ny, y0 + a.rows);
+        // Odd segments walk upwards, so that the halo rows two neighbouring
+        // tiles share are read by both at about the same time (the second
+        // read then hits L2).
+        const bool up = seg & 1;
+        const C sgn = up ? C(-1) : C(1);  // orientation of the window in y
+        // u_x, u_y, b_x, b_y of the last three rows formed (slots 0, 1, 2;
+        // slot 2 the newest)
+        C wnd[3][4][V];
+        const int nrow = y1 - y0 + 2;
+        for (int i = 0; i < nrow; ++i) {
+            const int m = up ? y1 - i : y0 - 1 + i;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    wnd[0][q][k] = wnd[1][q][k];
+                    wnd[1][q][k] = wnd[2][q][k];
+                    wnd[2][q][k] = C(0);
+                }
+            int my = m;
+            bool have = true;
+            if (my < 0 || my >= a.ny) {
+                if (a.wall_y) have = false;
+                else my = my < 0 ? my + a.ny : my - a.ny;
+            }
+            if (have) {  // warp-uniform
+                NodeMom<C> nm[V];
+                bool inside = true;  // the lane's nodes lie inside the lattice
+                if (GEN) {
+                    inside = xl >= 0 && xl < a.nx;
+                    if (inside) nm[0] = scalar_node<PREC, MODE>(a, xl, my);
+                } else {
+                    C v[kPlanes][V];
+                    if (MODE == 0) {
+                        gather_row_wrapped<PREC, V, WALLY>(static_cast<const S*>(a.src), a.nx, a.ny, a.pitch,
+                                                           a.plane, xw, my, lane, v);
+                    } else {
+                        const S* src = static_cast<const S*>(a.src) + (long long)my * a.pitch + xw;
+                        S r[kPlanes][V];
+#pragma unroll
+                        for (int p = 0; p < kPlanes; ++p) VecIO<S, V>::load(src + (long long)p * a.plane, r[p]);
+#pragma unroll
+                        for (int p = 0; p < kPlanes; ++p) StepCodec<S, V>::to_compute(r[p], v[p]);
+                    }
+#pragma unroll
+                    for (int k = 0; k < V; ++k) {
+                        C f[9], g[10];
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) f[i] = v[i][k];
+#pragma unroll
+                        for (int q = 0; q < 10; ++q) g[q] = v[9 + q][k];
+                        nm[k] = node_moments(f, g, unit, a.rho0);
                     }
                 }
-                const Moments<C> m = moments(f, g, a.rho0);
-                ux = m.ux; uy = m.uy; bx = m.bx; by = m.by;
-                if (interior) {
-                    const double rho = (double)m.rho, dux = (double)ux, duy = (double)uy;
-                    const double dbx = (double)bx, dby = (double)by;
-                    acc[0] += rho;
-                    acc[1] += rho * dux;
-                    acc[2] += rho * duy;
-                    acc[3] += 0.5 * (dux * dux + duy * duy);
-                    acc[4] += 0.5 * (dbx * dbx + dby * dby);
-                    acc[5] += dux * dbx + duy * dby;
-                    acc[6] += dbx;
-                    acc[7] += dby;
-                    const C jz = current_density(g, ux, uy, bx, by, a.omega_m, a.neq_scale);
-                    mjz = max_bits(mjz, abs_bits((double)jz));
+                if (inside) {
+#pragma unroll
+                    for (int k = 0; k < V; ++k) {
+                        wnd[2][0][k] = nm[k].ux;
+                        wnd[2][1][k] = nm[k].uy;
+                        wnd[2][2][k] = nm[k].bx;
+                        wnd[2][3][k] = nm[k].by;
+                    }
+                    if (m >= y0 && m < y1 && out_lane) {
+                        C ps[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) ps[q] = C(0);
+#pragma unroll
+                        for (int k = 0; k < V; ++k) {
+                            if (xl + k < a.nx) {
+                                const NodeMom<C>& n = nm[k];
+                                ps[0] += n.drho;
+                                ps[1] += n.mx;
+                                ps[2] += n.my;
+                                ps[3] += C(0.5) * (n.ux * n.ux + n.uy * n.uy);
+                                ps[4] += C(0.5) * (n.bx * n.bx + n.by * n.by);
+                                ps[5] += n.ux * n.bx + n.uy * n.by;
+                                ps[6] += n.bx;
+                                ps[7] += n.by;
+                                mjz = max(mjz, MB::of(node_current(n, a.omega_m, a.neq_scale)));
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) ls[q].add(ps[q]);
+                    }
                 }
             }
-            sm[0][hy][hx] = ux; sm[1][hy][hx] = uy; sm[2][hy][hx] = bx; sm[3][hy][hx] = by;
-        }
-        __syncthreads();
-        {
-            const int lx = threadIdx.x, ly = threadIdx.y;
-            const int x = tx0 + lx, y = ty0 + ly;
-            bool ok = x < a.nx && y < a.ny;
-            if (a.wall_x) ok = ok && x >= 1 && x <= a.nx - 2;
-            if (a.wall_y) ok = ok && y >= 1 && y <= a.ny - 2;
-            if (ok) {
-                // d_a phi = 3 sum_i w_i phi(x + c_i) c_ia
-                auto dx = [&](int q) {
-                    const C e = sm[q][ly + 1][lx + 2] - sm[q][ly + 1][lx];
-                    const C d = (sm[q][ly + 2][lx + 2] - sm[q][ly + 2][lx]) + (sm[q][ly][lx + 2] - sm[q][ly][lx]);
-                    return (double)(C(1.0 / 3.0) * e + C(1.0 / 12.0) * d);
+            // gradient stencil on the row before m (window slot 1)
+            const int o = up ? m + 1 : m - 1;
+            if (i >= 2) {  // warp-uniform; y0 <= o < y1
+                // x - 1 and x + 1 neighbours of the lane's first and last node
+                C lft[3][4], rgt[3][4];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        lft[r][q] = __shfl_up_sync(kFull, wnd[r][q][V - 1], 1);
+                        rgt[r][q] = __shfl_down_sync(kFull, wnd[r][q][0], 1);
+                    }
+                auto at = [&](int r, int q, int j) -> C {  // field q of row slot r at node j (-1 .. V)
+                    return j < 0 ? lft[r][q] : (j >= V ? rgt[r][q] : wnd[r][q][j]);
                 };
-                auto dy = [&](int q) {
-                    const C e = sm[q][ly + 2][lx + 1] - sm[q][ly][lx + 1];
-                    const C d = (sm[q][ly + 2][lx + 2] - sm[q][ly][lx + 2]) + (sm[q][ly + 2][lx] - sm[q][ly][lx]);
-                    return (double)(C(1.0 / 3.0) * e + C(1.0 / 12.0) * d);
-                };
-                const double div = dx(2) + dy(3);
-                const double vort = dx(1) - dy(0);
-                div2 += div * div;
-                ++cnt;
-                mdiv = max_bits(mdiv, abs_bits(div));
-                mvort = max_bits(mvort, abs_bits(vort));
+                bool rowok = out_lane;
+                if (a.wall_y) rowok = rowok && o >= 1 && o <= a.ny - 2;
+                C d2 = C(0);
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    const int x = xl + k;
+                    bool ok = rowok && x < a.nx;
+                    if (a.wall_x) ok = ok && x >= 1 && x <= a.nx - 2;
+                    // isotropic gradient: d_a phi = 3 sum_i w_i phi(x + c_i) c_ia
+                    // (walking upwards slot 2 is the row below: d_y changes
+                    // sign, which is exact)
+                    const C dxbx = C(1.0 / 3.0) * (at(1, 2, k + 1) - at(1, 2, k - 1)) +
+                                   C(1.0 / 12.0) * ((at(2, 2, k + 1) - at(2, 2, k - 1)) +
+                                                    (at(0, 2, k + 1) - at(0, 2, k - 1)));
+                    const C dyby = sgn * (C(1.0 / 3.0) * (at(2, 3, k) - at(0, 3, k)) +
+                                          C(1.0 / 12.0) * ((at(2, 3, k + 1) - at(0, 3, k + 1)) +
+                                                           (at(2, 3, k - 1) - at(0, 3, k - 1))));
+                    const C dxuy = C(1.0 / 3.0) * (at(1, 1, k + 1) - at(1, 1, k - 1)) +
+                                   C(1.0 / 12.0) * ((at(2, 1, k + 1) - at(2, 1, k - 1)) +
+                                                    (at(0, 1, k + 1) - at(0, 1, k - 1)));
+                    const C dyux = sgn * (C(1.0 / 3.0) * (at(2, 0, k) - at(0, 0, k)) +
+                                          C(1.0 / 12.0) * ((at(2, 0, k + 1) - at(0, 0, k + 1)) +
+                                                           (at(2, 0, k - 1) - at(0, 0, k - 1))));
+                    if (ok) {
+                        const C div = dxbx + dyby;
+                        const C vort = dxuy - dyux;
+                        d2 += div * div;
+                        ++cnt;
+                        mdiv = max(mdiv, MB::of(div));
+                        mvort = max(mvort, MB::of(vort));
+                    }
+                }
+                ls[8].add(d2);
             }
         }
-        __syncthreads();  // the next tile overwrites sm
     }
-    const int warp = tid >> 5, lane = tid & 31;
+
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        const double v = warp_sum(acc[s]);
-        if (lane == 0) red[warp][s] = v;
+    for (int q = 0; q < 9; ++q) {
+        const double v = warp_sum(ls[q].take());
+        if (lane == 0) red[warp][q] = v;
     }
     {
-        const double v8 = warp_sum(div2), v9 = warp_sum((double)cnt);
-        const unsigned long long m10 = warp_max_bits(mdiv), m11 = warp_max_bits(mjz), m12 = warp_max_bits(mvort);
+        const double v9 = warp_sum((double)cnt);
+        const unsigned long long m10 = warp_max_bits(dbits(MB::value(mdiv)));
+        const unsigned long long m11 = warp_max_bits(dbits(MB::value(mjz)));
+        const unsigned long long m12 = warp_max_bits(dbits(MB::value(mvort)));
         if (lane == 0) {
-            red[warp][8] = v8;
             red[warp][9] = v9;
             red[warp][10] = __longlong_as_double((long long)m10);
             red[warp][11] = __longlong_as_double((long long)m11);
@@ -168,18 +437,19 @@ __global__ void __launch_bounds__(256) diag_kernel(const DiagArgs<typename Prec<
         }
     }
     __syncthreads();
-    if (tid < kDiagSlots) {
-        double v = red[0][tid];
-        for (int w = 1; w < 8; ++w)
-            v = tid < 10 ? v + red[w][tid]
-                         : __longlong_as_double((long long)max_bits(abs_bits(v), abs_bits(red[w][tid])));
-        partials[(long long)blockIdx.x * kDiagSlots + tid] = v;
+    if (threadIdx.x < kDiagSlots) {
+        const int q = threadIdx.x;
+        double v = red[0][q];
+        for (int w = 1; w < kDWarps; ++w)
+            v = q < 10 ? v + red[w][q] : __longlong_as_double((long long)max_bits(dbits(v), dbits(red[w][q])));
+        partials[(long long)blockIdx.x * kDiagSlots + q] = v;
     }
 }
 
-// Fixed-order final reduction of the per-block partials (one block).
+// Fixed-order final reduction of the per-block partials (one block); slot 0
+// becomes the mass rho0 * nodes + sum (rho - rho0).
 __global__ void __launch_bounds__(256) diag_final(const double* __restrict__ partials, int nblocks,
-                                                  double* __restrict__ totals) {
+                                                  double mass_base, double* __restrict__ totals) {
     __shared__ double red[8][kDiagSlots];
     double acc[10];
     unsigned long long mx[3] = {0, 0, 0};
@@ -189,7 +459,7 @@ __global__ void __launch_bounds__(256) diag_final(const double* __restrict__ par
 #pragma unroll
         for (int s = 0; s < 10; ++s) acc[s] += partials[(long long)b * kDiagSlots + s];
 #pragma unroll
-        for (int s = 0; s < 3; ++s) mx[s] = max_bits(mx[s], abs_bits(partials[(long long)b * kDiagSlots + 10 + s]));
+        for (int s = 0; s < 3; ++s) mx[s] = max_bits(mx[s], dbits(partials[(long long)b * kDiagSlots + 10 + s]));
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
@@ -207,21 +477,30 @@ __global__ void __launch_bounds__(256) diag_final(const double* __restrict__ par
         const int s = threadIdx.x;
         double v = red[0][s];
         for (int w = 1; w < 8; ++w)
-            v = s < 10 ? v + red[w][s] : __longlong_as_double((long long)max_bits(abs_bits(v), abs_bits(red[w][s])));
-        totals[s] = v;
+            v = s < 10 ? v + red[w][s] : __longlong_as_double((long long)max_bits(dbits(v), dbits(red[w][s])));
+        totals[s] = s == 0 ? mass_base + v : v;
     }
 }
 
 int diag_blocks(const Layout& L) {
-    return ((L.nx + kDTX - 1) / kDTX) * ((L.ny + kDTY - 1) / kDTY);
+    (void)L;
+    return kDiagMaxBlocks;
 }
 
 template <int PREC>
-static cudaError_t launch_diag_t(const DiagLaunch& d, double* partials, int* nblocks, cudaStream_t st) {
+static cudaError_t launch_diag_t(const DiagLaunch& d, double* partials, int capacity, int* nblocks,
+                                 cudaStream_t st) {
     using C = typename Prec<PREC>::C;
+    constexpr int VF = PREC == 2 ? 4 : 2;  // nodes per lane of the vector path
+    const bool gen = d.wall_x != 0;
+    // vector loads need every row of every plane to start on a vector boundary
+    const long long vb = (long long)VF * d.L.esize;
+    const void* src = d.mode == 0 ? d.prev : d.cur;
+    const bool aligned = (reinterpret_cast<uintptr_t>(src) % vb == 0) && (d.L.pitch * d.L.esize) % vb == 0 &&
+                         (d.L.plane * d.L.esize) % vb == 0;
+    const int V = (!gen && aligned && d.L.nx % VF == 0) ? VF : 1;
     DiagArgs<C> a;
-    a.prev = d.prev;
-    a.cur = d.cur;
+    a.src = src;
     a.nx = d.L.nx;
     a.ny = d.L.ny;
     a.pitch = d.L.pitch;
@@ -231,32 +510,50 @@ static cudaError_t launch_diag_t(const DiagLaunch& d, double* partials, int* nbl
     a.neq_scale = C(d.neq_scale);
     a.wall_x = d.wall_x;
     a.wall_y = d.wall_y;
-    const int tiles_x = (d.L.nx + kDTX - 1) / kDTX;
-    const int ntiles = diag_blocks(d.L);
+    const long long strips = (d.L.nx + 30LL * V - 1) / (30LL * V);
+    if (strips > INT_MAX) return cudaErrorInvalidValue;
+    a.strips = (int)strips;
     auto go = [&](auto kernel) -> cudaError_t {
         int per_sm = 0, sms = 0, dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kDTX * kDTY, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kDWarps * 32, 0);
         if (e != cudaSuccess) return e;
-        *nblocks = std::max(1, std::min(ntiles, std::max(1, per_sm) * sms));
-        kernel<<<*nblocks, dim3(kDTX, kDTY), 0, st>>>(a, tiles_x, ntiles, partials);
+        const int maxb = std::max(1, std::min({std::max(1, per_sm) * sms, capacity, kDiagMaxBlocks}));
+        // tile height: at most one tile per resident warp (tall tiles keep
+        // the halo rows few)
+        const long long warps = (long long)maxb * kDWarps;
+        const long long segs_want = std::max(1LL, warps / strips);
+        const long long rows = ((long long)d.L.ny + segs_want - 1) / segs_want;
+        const long long segs = ((long long)d.L.ny + rows - 1) / rows;
+        if (strips * segs > INT_MAX) return cudaErrorInvalidValue;
+        a.rows = (int)rows;
+        a.ntiles = (int)(strips * segs);
+        *nblocks = (int)std::max(1LL, std::min<long long>(maxb, (a.ntiles + kDWarps - 1) / kDWarps));
+        kernel<<<*nblocks, kDWarps * 32, 0, st>>>(a, partials);
         return cudaGetLastError();
     };
-    return d.mode == 0 ? go(diag_kernel<PREC, 0>) : go(diag_kernel<PREC, 1>);
+    if (gen) return d.mode == 0 ? go(diag_kernel<PREC, 1, 0, false, true>) : go(diag_kernel<PREC, 1, 1, false, true>);
+    if (V == 1) {
+        if (d.mode == 1) return go(diag_kernel<PREC, 1, 1, false, false>);
+        return d.wall_y ? go(diag_kernel<PREC, 1, 0, true, false>) : go(diag_kernel<PREC, 1, 0, false, false>);
+    }
+    if (d.mode == 1) return go(diag_kernel<PREC, VF, 1, false, false>);
+    return d.wall_y ? go(diag_kernel<PREC, VF, 0, true, false>) : go(diag_kernel<PREC, VF, 0, false, false>);
 }
 
-cudaError_t launch_diag(const DiagLaunch& d, double* partials, double* totals, cudaStream_t st) {
+cudaError_t launch_diag(const DiagLaunch& d, double* partials, int capacity, double* totals, cudaStream_t st) {
+    if (capacity < 1) return cudaErrorInvalidValue;
     cudaError_t e;
     int nblocks = 0;
     switch (d.prec) {
-    case 0: e = launch_diag_t<0>(d, partials, &nblocks, st); break;
-    case 1: e = launch_diag_t<1>(d, partials, &nblocks, st); break;
-    case 2: e = launch_diag_t<2>(d, partials, &nblocks, st); break;
+    case 0: e = launch_diag_t<0>(d, partials, capacity, &nblocks, st); break;
+    case 1: e = launch_diag_t<1>(d, partials, capacity, &nblocks, st); break;
+    case 2: e = launch_diag_t<2>(d, partials, capacity, &nblocks, st); break;
     default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
-    diag_final<<<1, 256, 0, st>>>(partials, nblocks, totals);
+    diag_final<<<1, 256, 0, st>>>(partials, nblocks, d.rho0 * (double)d.L.nx * (double)d.L.ny, totals);
     return cudaGetLastError();
 }
 

@@ -56,10 +56,10 @@ cudaError_t launch_plane_in(const Layout& L, int prec, void* buf, int p, double 
 // Diagnostics.  mode 0: gather the pre-collision state from `prev` (the
 // buffer the last step read); mode 1: use `cur` in place, with the
 // magnetic non-equilibrium scaled by neq_scale.  A persistent grid of at
-// most diag_blocks(L) blocks walks the 32 x 8 node tiles; each block writes
-// kDiagSlots doubles into `partials`, then they are reduced in a fixed order
-// into `totals` (kDiagSlots doubles).  diag_blocks(L) (the tile count) is
-// the room `partials` must have.
+// most `capacity` blocks walks strip tiles of the lattice; each block
+// writes kDiagSlots doubles into `partials` (room for `capacity` blocks),
+// then they are reduced in a fixed order into `totals` (kDiagSlots
+// doubles).  diag_blocks(L) is a capacity that never limits the grid.
 constexpr int kDiagSlots = 13;
 struct DiagLaunch {
     Layout L;
@@ -71,7 +71,7 @@ struct DiagLaunch {
     int wall_x, wall_y;
 };
 int diag_blocks(const Layout& L);
-cudaError_t launch_diag(const DiagLaunch& d, double* partials, double* totals, cudaStream_t st);
+cudaError_t launch_diag(const DiagLaunch& d, double* partials, int capacity, double* totals, cudaStream_t st);
 
 Layout make_layout(int nx, int ny, int prec);
 

@@ -24,6 +24,11 @@ template <typename C> struct StepArgs {
     int wall_x, wall_y;
 };
 
+// Pre-collision populations of the V nodes x0 .. x0+V-1 (x0 = (32 xblock +
+// lane) V) of row y, pulled from the post-collision buffer src: v[p][k] in
+// the compute type (FP16S values stay in storage units, 2^12 times the
+// deviation).  Returns whether the lane's nodes lie inside the lattice
+// (false: nothing was loaded and v is unset).
 // Requires nx % V == 0, all 32 lanes of the warp present, y < ny.  WALLY:
 // half-way bounce-back walls below row 0 and above row ny-1 (compile-time,
 // so that the periodic kernel has no branch between its 19 plane loads).
@@ -31,11 +36,9 @@ template <typename C> struct StepArgs {
 // hold fewer than 2^31 elements (fewer address instructions per plane),
 // long long otherwise.
 template <int PREC, int V, bool WALLY, typename Off = long long>
-__device__ __forceinline__ void step_row(const typename Prec<PREC>::S* __restrict__ src,
-                                         typename Prec<PREC>::S* __restrict__ dst, int nx, int ny,
-                                         long long pitch, long long plane,
-                                         const NodeParams<typename Prec<PREC>::C>& np, int xblock,
-                                         int y, int lane) {
+__device__ __forceinline__ bool gather_row(const typename Prec<PREC>::S* __restrict__ src, int nx, int ny,
+                                           long long pitch, long long plane, int xblock, int y, int lane,
+                                           typename Prec<PREC>::C (&v)[kPlanes][V]) {
     using S = typename Prec<PREC>::S;
     using C = typename Prec<PREC>::C;
     const int x0 = (xblock * 32 + lane) * V;
@@ -75,12 +78,8 @@ __device__ __forceinline__ void step_row(const typename Prec<PREC>::S* __restric
         if (cx < 0 && !bounce && !right_by_shfl && active) edge[p] = row[xr];
     }
     // Phase 2: decode and apply the +-1 x shift of the moving populations
-    // (FP16S values stay in storage units: the collision below runs in them).
-    constexpr bool kScaled = PREC == 2;
-    // FP16S: node pairs on FP32x2
-    constexpr int kMode = PREC == 2 ? kPairs : kNative;
+    // (FP16S values stay in storage units).
     using Codec = StepCodec<S, V>;
-    C v[kPlanes][V];
 #pragma unroll
     for (int p = 0; p < kPlanes; ++p) {
         const int cx = pcx(p), cy = pcy(p);
@@ -104,8 +103,28 @@ __device__ __forceinline__ void step_row(const typename Prec<PREC>::S* __restric
             v[p][V - 1] = right;
         }
     }
-    if (!active) return;
+    return active;
+}
+
+// One warp updates 32*V consecutive x nodes of row y: the pull gather above,
+// the collision, aligned V-wide vector stores.  Same requirements.
+template <int PREC, int V, bool WALLY, typename Off = long long>
+__device__ __forceinline__ void step_row(const typename Prec<PREC>::S* __restrict__ src,
+                                         typename Prec<PREC>::S* __restrict__ dst, int nx, int ny,
+                                         long long pitch, long long plane,
+                                         const NodeParams<typename Prec<PREC>::C>& np, int xblock,
+                                         int y, int lane) {
+    using S = typename Prec<PREC>::S;
+    using C = typename Prec<PREC>::C;
+    C v[kPlanes][V];
+    if (!gather_row<PREC, V, WALLY, Off>(src, nx, ny, pitch, plane, xblock, y, lane, v)) return;
+    // FP16S collides in storage units, node pairs on FP32x2
+    constexpr bool kScaled = PREC == 2;
+    constexpr int kMode = PREC == 2 ? kPairs : kNative;
     collide_nodes<C, V, kScaled, kMode>(v, np);
+    const int x0 = (xblock * 32 + lane) * V;
+    const Off o_0 = (Off)y * (Off)pitch, pl = (Off)plane;
+    using Codec = StepCodec<S, V>;
 #pragma unroll
     for (int p = 0; p < kPlanes; ++p) {
         S r[V];
