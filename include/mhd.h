@@ -207,15 +207,20 @@ mhd_status mhd_set_state(mhd_lattice* l, const void* host, size_t bytes);
  *   stream      cudaStream_t (may be NULL); the call waits for it;
  *   out         caller-owned host struct (out->step is set to 0).
  * The per-block partial sums go to one fixed scratch array of about 1.7 MB
- * that is compiled into the library: every GPU that loads the library holds
- * it until the process exits.  Its device address is looked up on the first
- * call made on each device (with that device current).  Every call uses the
- * same array and each call overwrites what it reads, so calls whose work
- * overlaps on a GPU (different streams or host threads at the same time)
- * race and must be serialised by the caller.  Lattices with
- * ceil(nx/32)*ceil(ny/8) > 16384 (about 4.2 M nodes, e.g. more than
- * 2048 x 2048) are rejected with MHD_EINVAL.  Non-finite totals ->
- * MHD_EUNSTABLE (with *out filled). */
+ * (room for 16384 blocks) that is compiled into the library: every GPU that
+ * loads the library holds it until the process exits.  The diagnostics grid
+ * is persistent and capped at the blocks the array holds, so the array
+ * limits no lattice size; a lattice whose state (19 * nx * ny elements)
+ * would not fit in the device's memory is rejected with MHD_EINVAL ("too
+ * large") before anything is launched.  The caller must pass the state's
+ * true extent: a smaller wrong size cannot be detected.  The array's device address is looked up on the first call made
+ * in each device's current context (with that device current) and again
+ * after the context changes (e.g. after cudaDeviceReset).  Every call uses
+ * the same array and each call overwrites what it reads, so calls whose
+ * work overlaps on a GPU (different streams or host threads at the same
+ * time) race and must be serialised by the caller.  Any alignment of the
+ * state pointers works (16-byte aligned states take the vector loads).
+ * Non-finite totals -> MHD_EUNSTABLE (with *out filled). */
 mhd_status mhd_totals_noalloc(const void* state, const void* prev_state, int nx, int ny,
                               const mhd_params* p, void* stream, mhd_totals* out);
 

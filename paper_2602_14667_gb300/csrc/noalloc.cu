@@ -12,10 +12,18 @@
 //
 // The scratch is one file-scope __device__ array (kNoallocScratchDoubles
 // doubles, about 1.7 MB), created when the library is loaded and held by
-// every GPU that loads the library until the process exits.  In host code
-// its name is only a host-side stand-in, so each device's address is looked
-// up once with cudaGetSymbolAddress, on the first call made on that device
-// (with that device current), and passed to the kernels.
+// every GPU that loads the library until the process exits.  It holds the
+// per-block partials of at most kNoallocMaxBlocks blocks; the diagnostics
+// grid is persistent (its blocks walk the lattice's tiles) and is capped at
+// that count, so the array bounds no lattice size.  In host code the
+// array's name is only a host-side stand-in, so each device's address is
+// looked up with cudaGetSymbolAddress, with that device current, on the
+// first call made in the device's current context, and passed to the
+// kernels.  The lookup is keyed on the context's unique id: after a
+// cudaDeviceReset the runtime creates a new context, in which the module
+// holding the array may sit at another address, and the first call there
+// looks it up again.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -27,8 +35,8 @@
 
 namespace {
 
-// Per-block partials of the diagnostics kernel: one 32 x 8 node tile per
-// block, kDiagSlots doubles each, then kDiagSlots doubles of final totals.
+// Per-block partials of the diagnostics kernel (kDiagSlots doubles for each
+// of at most kNoallocMaxBlocks blocks), then kDiagSlots doubles of totals.
 constexpr long long kNoallocMaxBlocks = 16384;
 constexpr long long kNoallocScratchDoubles = kNoallocMaxBlocks * mhd::kDiagSlots + 16;
 
@@ -36,7 +44,11 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoallocScratchDoubles
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-double* g_scratch_ptr[kMaxDevices] = {};
+struct ScratchCache {
+    unsigned long long ctx_id;  // id of the context the address belongs to
+    double* ptr;
+};
+ScratchCache g_scratch[kMaxDevices] = {};
 
 mhd_status nfail(mhd_status s, const std::string& m) {
     mhd::set_last_error(m);
@@ -47,21 +59,55 @@ mhd_status ncuda(cudaError_t e, const char* what) {
     return nfail(MHD_ECUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
 }
 
-// Device address of the scratch array on the current device (looked up once
-// per device).
+// Unique id of the calling thread's current context (0 if the driver
+// cannot tell).  The two driver calls are reached through the runtime's
+// entry-point query, so the library needs no link against the driver.
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void* fc = nullptr;
+        void* fi = nullptr;
+        cudaDriverEntryPointQueryResult qc, qi;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fc, 12000, cudaEnableDefault, &qc) == cudaSuccess &&
+            qc == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &fi, 12000, cudaEnableDefault, &qi) == cudaSuccess &&
+            qi == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<GetCurrent>(fc);
+            get_id = reinterpret_cast<GetId>(fi);
+        }
+        cudaGetLastError();
+        looked_up = true;
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of the scratch array in the current device's current
+// context: looked up on the first call made in that context (with the
+// device current) and kept; a context the driver cannot identify gets a
+// fresh lookup on every call.
 mhd_status scratch_on_current_device(double** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return ncuda(e, "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return nfail(MHD_ECUDA, "device ordinal out of range");
+    const unsigned long long id = current_context_id();
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    if (id == 0 || g_scratch[dev].ctx_id != id || !g_scratch[dev].ptr) {
         void* ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess) return ncuda(e, "cudaGetSymbolAddress(scratch)");
-        g_scratch_ptr[dev] = static_cast<double*>(ptr);
+        g_scratch[dev].ctx_id = id;
+        g_scratch[dev].ptr = static_cast<double*>(ptr);
     }
-    *out = g_scratch_ptr[dev];
+    *out = g_scratch[dev].ptr;
     return MHD_OK;
 }
 
@@ -83,11 +129,18 @@ extern "C" mhd_status mhd_totals_noalloc(const void* state, const void* prev_sta
     L.esize = p->precision == MHD_FP64 ? 8 : (p->precision == MHD_FP32 ? 4 : 2);
     L.pitch = nx;
     L.plane = (long long)nx * ny;
-    const long long blocks = mhd::diag_blocks(L);
-    if (blocks > kNoallocMaxBlocks)
-        return nfail(MHD_EINVAL, "lattice too large for mhd_totals_noalloc: ceil(nx/32)*ceil(ny/8) = " +
-                                     std::to_string(blocks) + " exceeds the limit of " +
-                                     std::to_string(kNoallocMaxBlocks) + " (about 4.2 M nodes)");
+    // A state larger than the device's memory cannot be valid: reject it
+    // before anything is launched (a smaller wrong size cannot be told from
+    // a right one; the caller must pass the state's true extent).
+    {
+        size_t free_b = 0, total = 0;
+        const cudaError_t e = cudaMemGetInfo(&free_b, &total);
+        if (e != cudaSuccess) return ncuda(e, "cudaMemGetInfo");
+        const double bytes = (double)mhd::kStatePlanes * (double)L.plane * (double)L.esize;
+        if (bytes > (double)total)
+            return nfail(MHD_EINVAL, "lattice too large for mhd_totals_noalloc: its state (" + std::to_string(bytes) +
+                                         " bytes) exceeds the device's memory");
+    }
     double* scratch = nullptr;
     mhd_status s = scratch_on_current_device(&scratch);
     if (s != MHD_OK) return s;
@@ -109,7 +162,10 @@ extern "C" mhd_status mhd_totals_noalloc(const void* state, const void* prev_sta
     // Every per-block slot that diag_final reads is written by the first
     // kernel of this call and the totals slots by diag_final, so nothing left
     // in the array by an earlier call is read and nothing needs clearing.
-    cudaError_t e = mhd::launch_diag(d, scratch, totals_d, st);
+    // The grid is capped at the blocks the array has room for.
+    cudaError_t e = mhd::launch_diag(d, scratch, (int)kNoallocMaxBlocks, totals_d, st);
+    if (e == cudaErrorInvalidValue)
+        return nfail(MHD_EINVAL, "lattice too large for mhd_totals_noalloc: its tile count exceeds the int range");
     if (e != cudaSuccess) return ncuda(e, "diagnostics kernel");
     double t[mhd::kDiagSlots];
     e = cudaMemcpyAsync(t, totals_d, sizeof t, cudaMemcpyDeviceToHost, st);

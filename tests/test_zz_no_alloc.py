@@ -70,13 +70,39 @@ def test_noalloc_totals_match_get_totals(prec, wall_y):
     assert torch.cuda.mem_get_info()[0] == free_before
 
 
-def test_noalloc_rejects_lattices_beyond_the_scratch():
+def test_noalloc_matches_get_totals_beyond_2048_squared():
+    """The scratch bounds the diagnostics grid (its blocks walk the tiles),
+    not the lattice: a 2304 x 2112 lattice, more nodes than 2048^2, reduces
+    through the same array."""
+    import torch
+
+    import mhd_inputs
+    from paper_2602_14667_gb300 import Lattice, _abi
+    nx, ny = 2304, 2112
+    fields = mhd_inputs.orszag_tang(nx, 0.04, 0.04, ny)
+    stream = torch.cuda.current_stream().cuda_stream
+    with Lattice(nx, ny, 0.53, 0.55, precision="fp32") as lat:
+        lat.set_fields(*fields)
+        lat.advance(5)
+        prev = lat.get_state()
+        lat.advance(1)
+        ref = lat.get_totals()
+        cur = lat.get_state()
+        params = lat.params
+    d_cur, d_prev = _device_copy(cur), _device_copy(prev)
+    for _ in range(2):
+        got = _abi.totals_noalloc(d_cur.data_ptr(), nx, ny, params, prev_ptr=d_prev.data_ptr(),
+                                  stream=stream)
+        _close(got, ref, nx * ny)
+
+
+def test_noalloc_rejects_invalid_sizes():
     import torch
 
     from paper_2602_14667_gb300 import MhdError, _abi
     dummy = torch.zeros(16, dtype=torch.float32, device="cuda")  # never read: rejected first
     params = _abi.mhd_params(1.0, 0.6, 0.6, 0, 0, _abi.MHD_FP32, 0, 0, 0, 0)
     with pytest.raises(MhdError, match="too large"):
-        _abi.totals_noalloc(dummy.data_ptr(), 4096, 4096, params)
+        _abi.totals_noalloc(dummy.data_ptr(), 1 << 30, 1 << 30, params)
     with pytest.raises(MhdError, match="EINVAL"):
         _abi.totals_noalloc(dummy.data_ptr(), 1, 4, params)
