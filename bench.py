@@ -69,6 +69,8 @@ def parse():
                     help="fixed launch shape 'V,BY' (skips the autotuner; for profiling)")
     ap.add_argument("--in-place", action="store_true",
                     help="ot4096 on one state buffer (in-place streaming) instead of two")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="ot4096 at N=1: leave out the extra rows (FP16S line and field error, ensemble)")
     return ap.parse_args()
 
 
@@ -271,7 +273,10 @@ def run_reference(args):
     out = {"metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "impl": "reference", "config": workload(args.n, args.precision),
+           "impl": "reference",
+           "config": dict(workload(args.n, args.precision),
+                          workload=f"orszag_tang_{ns}x{ns}_fp64_oracle_sample_of_{args.n}x{args.n}",
+                          nx=ns, ny=ns, sample_of=workload(args.n, args.precision)["workload"]),
            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -279,6 +284,77 @@ def run_reference(args):
 
 
 TUNE_CACHE = os.path.join(ROOT, "paper_2602_14667_gb300", "tune_cache.json")
+
+
+def extra_rows(fp32_mlups, peak):
+    """The other throughput targets of the path, measured in the same run
+    (each timed region well under a second):
+      fp16s     the 4096^2 workload with FP16 storage shifted by w_i rho0
+                (200 steps), its MLUPS, ratio to FP32 and HBM fraction, and
+                the FP16S field error where FP16S is usable: the 1024^2
+                Orszag-Tang vortex at tau = 0.51 after 1000 steps against
+                an FP64 run of the same lattice (relative L2 of u and b);
+      ensemble  the 512-lattice random-spectrum ensemble (39 M nodes) in one
+                persistent launch per step (100 steps)."""
+    import numpy as np
+    import torch
+
+    import mhd_inputs
+    from paper_2602_14667_gb300 import Batch, Lattice
+    out = {}
+    stream = torch.cuda.Stream()
+
+    def timed(obj, steps):
+        obj.advance(10)
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        obj.advance(steps)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    n = 4096
+    with Lattice(n, n, 0.50006, 0.50006, precision="fp16s", stream=stream.cuda_stream) as lat:
+        lat.set_fields(*mhd_inputs.orszag_tang(n, 0.04, 0.04))
+        shape = lat.autotune()
+        ms16 = timed(lat, 200)
+    v16 = n * n / (ms16 * 1e-3) / 1e6
+    gbs16 = BYTES_PER_NODE["fp16s"] * n * n / (ms16 * 1e-3) / 1e9
+    m, tau, steps = 1024, 0.51, 1000
+    fields = mhd_inputs.orszag_tang(m, 0.04, 0.04)
+    got = {}
+    for prec in ("fp64", "fp16s"):
+        with Lattice(m, m, tau, tau, precision=prec, stream=stream.cuda_stream) as lat:
+            lat.set_fields(*fields)
+            lat.advance(steps)
+            got[prec] = lat.get_fields()
+    err = {k: float(np.linalg.norm(got["fp16s"][k] - got["fp64"][k]) / np.linalg.norm(got["fp64"][k]))
+           for k in ("ux", "uy", "bx", "by")}
+    out["fp16s"] = {"value": v16, "unit": "MLUPS", "ms_per_step": ms16, "steps": 200,
+                    "ratio_to_fp32": v16 / fp32_mlups, "kernel_config": list(shape),
+                    "roofline": {"bound": "hbm", "achieved": gbs16, "peak": peak, "unit": "GB/s",
+                                 "frac": gbs16 / peak, "bytes_per_node": BYTES_PER_NODE["fp16s"]},
+                    "field_error": {"workload": f"orszag_tang_{m}x{m}_tau_{tau}", "steps": steps,
+                                    "reference": "fp64 run of the same lattice",
+                                    "rel_l2": err, "max_rel_l2": max(err.values())}}
+    draws = mhd_inputs.ensemble(512)
+    sizes = [(d["n"], d["n"]) for d in draws]
+    taus = [(0.5 + 3 * d["nu"], 0.5 + 3 * d["eta"]) for d in draws]
+    with Batch(sizes, taus, stream=stream.cuda_stream) as b:
+        for i, d in enumerate(draws):
+            b.set_fields(i, *mhd_inputs.random_spectrum(d["n"], d["n"], d["seed"], 0.02, 0.02))
+        bshape = b.autotune()
+        msb = timed(b, 100)
+        nodes = b.nodes
+    gbsb = 152 * nodes / (msb * 1e-3) / 1e9
+    out["ensemble"] = {"value": nodes / (msb * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": msb, "steps": 100,
+                       "workload": "ensemble_512_random_spectrum_fp32", "lattices": len(draws), "nodes": nodes,
+                       "kernel_config": list(bshape),
+                       "roofline": {"bound": "hbm", "achieved": gbsb, "peak": peak, "unit": "GB/s",
+                                    "frac": gbsb / peak, "bytes_per_node": 152}}
+    return out
 
 
 def run_gb300(args):
@@ -379,6 +455,9 @@ def run_gb300(args):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline()
+    extra = None
+    if not args.no_extra and world == 1 and prec == "fp32" and n == 4096 and not args.in_place:
+        extra = extra_rows(value, peak)
     cfg = workload(n, prec)
     nbuf = 1 if args.in_place else 2
     cfg.update({"kernel_config": list(shape), "graph_steps": 64,
@@ -411,6 +490,8 @@ def run_gb300(args):
            "clocks": clk.summary()}
     if tot is not None:
         out["totals"] = {k: tot[k] for k in ("mass", "e_kin", "e_mag", "jz_max", "divb_max")}
+    if extra is not None:
+        out.update(extra)
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -660,8 +741,10 @@ def run_diagnostics(args):
     CUDA events on the lattice's stream around `steps` calls of the totals
     (each: one persistent kernel over the lattice, the fixed-order final
     reduction, the copy of the 13 values to the host and the host's wait).
-    The kernel is bound by the FP64 units (FP64 per-node contributions), so
-    the roofline is the FP64 instruction rate."""
+    The kernel reads each of the 19 planes once (the pre-collision state is
+    gathered from the buffer the last step read), so its roofline is HBM
+    bandwidth at 19 x element-size bytes per node; the per-call time
+    includes the host's round trip, so the fraction is a lower bound."""
     import torch
 
     import mhd_inputs
@@ -684,16 +767,16 @@ def run_diagnostics(args):
             e1.record(stream)
             e1.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
-    ins = profiled(prec, None, "fp64_instructions_per_node", name=f"diag_kernel_{prec}_ncu.md",
-                   sources=DIAG_KERNEL_SOURCES)
-    roofline = None
-    if ins is not None:
-        rate = ins * nodes / (ms * 1e-3)
-        roofline = {"bound": "alu", "achieved": rate / 1e9, "peak": FP64_INSTR_PEAK / 1e9,
-                    "unit": "G FP64 instructions/s", "frac": rate / FP64_INSTR_PEAK,
-                    "peak_source": "derived: 2 FP64 instructions/clk/SM x 152 SMs x 2.07 GHz",
-                    "fp64_instructions_per_node": ins, "traffic": None,
-                    "note": "per call, including the final reduction, the D2H copy and the host wait"}
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+        peak = float(json.load(fh)["hbm_gbs"])
+    per_node = 19 * ESIZE[prec]
+    gbs = per_node * nodes / (ms * 1e-3) / 1e9
+    dram = profiled(prec, None, "dram_bytes_per_node", name=f"diag_kernel_{prec}_ncu.md",
+                    sources=DIAG_KERNEL_SOURCES)
+    roofline = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                "peak_source": "measured", "bytes_per_node": per_node,
+                "traffic": None if dram is None else dram * nodes,
+                "note": "per call, including the final reduction, the D2H copy and the host wait"}
     out = {"metric": "global diagnostics rate", "value": nodes / (ms * 1e-3) / 1e6, "unit": "Mnodes/s",
            "ms_per_call": ms, "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "dtype": DTYPE[prec] + " (f64 sums)", "data": "synthetic",
