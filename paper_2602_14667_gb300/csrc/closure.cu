@@ -1,9 +1,10 @@
 // closure.cu -- learned sub-grid closure for coarse lattices: data
-// generation (box filter, features, one-step targets), BF16 tensor-core MLP
-// training (forward, backward, Adam with FP32 master weights), and a closure
-// variant of the fused step that evaluates the MLP per node and adds its
+// generation (box filter, features, one-step targets) and the BF16
+// tensor-core MLP's layer-by-layer prediction.  The closure step itself
+// (closure_rows.cu, closure_tc.cu) evaluates the MLP per node and adds its
 // output to the projected a1^(2) before the recursion (task 3 of the
-// paper's "Algorithm of computation").  The closure is not part of the paper.
+// paper's "Algorithm of computation"); training is in mlp_train.cu.  The
+// closure is not part of the paper.
 //
 // MLP: 24 -> 64 -> 64 -> 3, ReLU, y = out_scale * (W3 h2 + b3) with
 // h1 = relu(W1 xn + b1), h2 = relu(W2 h1 + b2), xn = (x - mean) * scale.
@@ -322,222 +323,6 @@ __global__ void stats_finish(const double* __restrict__ P, int nblocks, long lon
     } else {
         prm[kOffOutScale + c - kIn] = (float)(sd > 0 ? sd : 1.0);
     }
-}
-
-// ---- closure step (inference fused beside the collision) ------------------------
-constexpr int kFeatStride = 40;  // bf16 per feature row (conflict-free fragment loads)
-constexpr int kW1Stride = 40;    // padded rows of the shared weights: row strides of 20 and
-constexpr int kW2Stride = 72;    // 36 words put the 32 lanes of a B-fragment load in 32 banks
-
-struct ClosureShared {
-    bf16 Wt1[kHid * kW1Stride];
-    bf16 Wt2[kHid * kW2Stride];
-    bf16 Wt3[kOutPad * kW2Stride];
-    float b1[kHid], b2[kHid], b3[kOutPad];
-    float mean[kIn], scale[kIn], out_scale[kOut];
-    float mom[4][kCHY][kCHX];
-    // pre-collision populations of the tile and of its halo ring, double
-    // buffered: cp.async fills one while the other tile is processed
-    float pop[2][kPlanes][kCTX * kCTY];
-    float hpop[2][kPlanes][kCHX * kCHY - kCTX * kCTY];
-    alignas(16) bf16 feat[kCTX * kCTY * kFeatStride];
-    float da[kCTX * kCTY][kOut];
-};
-// ldmatrix reads 16-byte rows: the fragment sources and their row strides
-// must keep every row address 16-byte aligned.
-static_assert(offsetof(ClosureShared, Wt1) % 16 == 0 && offsetof(ClosureShared, Wt2) % 16 == 0 &&
-                  offsetof(ClosureShared, Wt3) % 16 == 0 && offsetof(ClosureShared, feat) % 16 == 0,
-              "ldmatrix sources must be 16-byte aligned");
-static_assert((kW1Stride * sizeof(bf16)) % 16 == 0 && (kW2Stride * sizeof(bf16)) % 16 == 0 &&
-                  (kFeatStride * sizeof(bf16)) % 16 == 0,
-              "ldmatrix row strides must be multiples of 16 bytes");
-static_assert(offsetof(ClosureShared, b1) % 8 == 0 && offsetof(ClosureShared, b2) % 8 == 0 &&
-                  offsetof(ClosureShared, b3) % 8 == 0,
-              "bias pairs are read as float2");
-
-// One warp evaluates the MLP for 16 nodes (rows m0..m0+15 of the feature
-// tile) and writes out_scale * y into sh.da.  Fragments come from shared
-// memory by ldmatrix: the A fragment of a 16 x 16 k-chunk is matrices (rows
-// 0-7 | 8-15) x (k 0-7 | 8-15); one x4 load of a weight row block [n][k]
-// gives the B fragments of two consecutive k-chunks of an 8-wide n-tile.
-__device__ __forceinline__ void mlp_rows16(ClosureShared& sh, int m0, int lane) {
-    const int t = lane & 3, lr = lane & 7, lm = lane >> 3;
-    uint32_t a1[2][4];
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-        ldsm_x4(a1[c], sh.feat + (m0 + lr + 8 * (lm & 1)) * kFeatStride + 16 * c + 8 * (lm >> 1));
-    uint32_t h[4][4];  // layer input as A fragments (K = 64)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const float2 bb = *reinterpret_cast<const float2*>(sh.b1 + 8 * j + 2 * t);
-        float d[4] = {bb.x, bb.y, bb.x, bb.y};
-        uint32_t w[4];
-        ldsm_x4(w, sh.Wt1 + (8 * j + lr) * kW1Stride + 8 * lm);
-        const uint32_t b0[2] = {w[0], w[1]}, b1[2] = {w[2], w[3]};
-        mma16816(d, a1[0], b0);
-        mma16816(d, a1[1], b1);
-        // accumulator of n-tile j becomes half of k-chunk j/2 of the next A
-        h[j >> 1][(j & 1) * 2 + 0] = pack2(fmaxf(d[0], 0.f), fmaxf(d[1], 0.f));
-        h[j >> 1][(j & 1) * 2 + 1] = pack2(fmaxf(d[2], 0.f), fmaxf(d[3], 0.f));
-    }
-    uint32_t h2[4][4];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const float2 bb = *reinterpret_cast<const float2*>(sh.b2 + 8 * j + 2 * t);
-        float d[4] = {bb.x, bb.y, bb.x, bb.y};
-#pragma unroll
-        for (int c = 0; c < 4; c += 2) {
-            uint32_t w[4];
-            ldsm_x4(w, sh.Wt2 + (8 * j + lr) * kW2Stride + 16 * c + 8 * lm);
-            const uint32_t b0[2] = {w[0], w[1]}, b1[2] = {w[2], w[3]};
-            mma16816(d, h[c], b0);
-            mma16816(d, h[c + 1], b1);
-        }
-        h2[j >> 1][(j & 1) * 2 + 0] = pack2(fmaxf(d[0], 0.f), fmaxf(d[1], 0.f));
-        h2[j >> 1][(j & 1) * 2 + 1] = pack2(fmaxf(d[2], 0.f), fmaxf(d[3], 0.f));
-    }
-    const float2 bb = *reinterpret_cast<const float2*>(sh.b3 + 2 * t);
-    float d[4] = {bb.x, bb.y, bb.x, bb.y};
-#pragma unroll
-    for (int c = 0; c < 4; c += 2) {
-        uint32_t w[4];
-        ldsm_x4(w, sh.Wt3 + lr * kW2Stride + 16 * c + 8 * lm);
-        const uint32_t b0[2] = {w[0], w[1]}, b1[2] = {w[2], w[3]};
-        mma16816(d, h2[c], b0);
-        mma16816(d, h2[c + 1], b1);
-    }
-    // d0: (row g, col 2t), d1: (g, 2t+1), d2: (g+8, 2t), d3: (g+8, 2t+1)
-    const int g = lane >> 2;
-    if (2 * t < kOut) {
-        sh.da[m0 + g][2 * t] = d[0] * sh.out_scale[2 * t];
-        sh.da[m0 + g + 8][2 * t] = d[2] * sh.out_scale[2 * t];
-    }
-    if (2 * t + 1 < kOut) {
-        sh.da[m0 + g][2 * t + 1] = d[1] * sh.out_scale[2 * t + 1];
-        sh.da[m0 + g + 8][2 * t + 1] = d[3] * sh.out_scale[2 * t + 1];
-    }
-}
-
-// Persistent 32 x 8-node tiles.  The populations of the next tile are
-// gathered by cp.async into the other buffer while this tile's features,
-// MLP and collision run.
-__global__ void __launch_bounds__(256, 2) step_closure(const StepArgs<float> a, const ClosureParamsDev cp,
-                                                       int ntx, int ntiles) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    ClosureShared& sh = *reinterpret_cast<ClosureShared*>(smem_raw);
-    const int tid = threadIdx.y * kCTX + threadIdx.x, lane = threadIdx.x, ly = threadIdx.y;
-    const float* src = static_cast<const float*>(a.src);
-    float* dst = static_cast<float*>(a.dst);
-    // the network: weight rows in 16-byte pieces into the padded shared rows
-    // (issued together, ahead of the first tile's gather)
-    constexpr int kC1 = kInPad * 2 / 16, kC2 = kHid * 2 / 16;  // 16-byte pieces per weight row
-    for (int i = tid; i < kHid * kC1; i += 256)
-        cp_async16(sh.Wt1 + (i / kC1) * kW1Stride + (i % kC1) * 8, cp.Wt1 + (i / kC1) * kInPad + (i % kC1) * 8);
-    for (int i = tid; i < kHid * kC2; i += 256)
-        cp_async16(sh.Wt2 + (i / kC2) * kW2Stride + (i % kC2) * 8, cp.Wt2 + (i / kC2) * kHid + (i % kC2) * 8);
-    for (int i = tid; i < kOutPad * kC2; i += 256)
-        cp_async16(sh.Wt3 + (i / kC2) * kW2Stride + (i % kC2) * 8, cp.Wt3 + (i / kC2) * kHid + (i % kC2) * 8);
-    if (tid < kHid) { sh.b1[tid] = cp.b1[tid]; sh.b2[tid] = cp.b2[tid]; }
-    if (tid < kOutPad) sh.b3[tid] = cp.b3[tid];
-    if (tid < kIn) { sh.mean[tid] = cp.mean[tid]; sh.scale[tid] = cp.scale[tid]; }
-    if (tid < kOut) sh.out_scale[tid] = cp.out_scale[tid];
-    // one group with the first tile's gather: the first wait covers both
-    if ((int)blockIdx.x < ntiles) closure_prefetch(sh, src, a, ntx, blockIdx.x, 0, tid, lane, ly);
-    else cp_async_commit();
-    int b = 0;
-    for (int tl = blockIdx.x; tl < ntiles; tl += gridDim.x, b ^= 1) {
-        const int next = tl + gridDim.x;
-        __syncthreads();  // the other buffer's previous tile is done; shared parameters loaded
-        if (next < ntiles) closure_prefetch(sh, src, a, ntx, next, b ^ 1, tid, lane, ly);
-        else cp_async_commit();  // empty group: keeps the wait count uniform
-        cp_async_wait<1>();      // this tile's group has landed (for this thread)
-        __syncthreads();         // ... and for every thread
-        const int x0 = (tl % ntx) * kCTX, y0 = (tl / ntx) * kCTY;
-        const int x = x0 + lane, y = y0 + ly;
-        const bool inside = x < a.nx && y < a.ny;
-        float f[9], g[10];
-        if (tid < kHalo) {
-            int hx, hy;
-            ring_pos(tid, hx, hy);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) f[i] = sh.hpop[b][i][tid];
-#pragma unroll
-            for (int q = 0; q < 10; ++q) g[q] = sh.hpop[b][9 + q][tid];
-            const Moments<float> m = moments(f, g, a.np.rho0);
-            sh.mom[0][hy][hx] = m.ux; sh.mom[1][hy][hx] = m.uy;
-            sh.mom[2][hy][hx] = m.bx; sh.mom[3][hy][hx] = m.by;
-        }
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = sh.pop[b][i][tid];
-#pragma unroll
-        for (int q = 0; q < 10; ++q) g[q] = sh.pop[b][9 + q][tid];
-        float feat[kIn];
-        point_features(f, g, a.np.rho0, feat);
-        sh.mom[0][ly + 1][lane + 1] = feat[1]; sh.mom[1][ly + 1][lane + 1] = feat[2];
-        sh.mom[2][ly + 1][lane + 1] = feat[3]; sh.mom[3][ly + 1][lane + 1] = feat[4];
-        __syncthreads();
-        stencil_features<kCHX, kCHY>(sh.mom, lane, ly, feat + 8);
-        bf16* row = sh.feat + tid * kFeatStride;
-#pragma unroll
-        for (int c = 0; c < kInPad; c += 2) {
-            const float v0 = (inside && c < kIn) ? (feat[c] - sh.mean[c]) * sh.scale[c] : 0.f;
-            const float v1 = (inside && c + 1 < kIn) ? (feat[c + 1] - sh.mean[c + 1]) * sh.scale[c + 1] : 0.f;
-            *reinterpret_cast<uint32_t*>(row + c) = pack2(v0, v1);
-        }
-        __syncwarp();
-        // the warp's 32 nodes are rows 32*ly .. 32*ly + 31 of the feature tile
-        mlp_rows16(sh, 32 * ly, lane);
-        mlp_rows16(sh, 32 * ly + 16, lane);
-        __syncwarp();
-        if (inside) {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) f[i] = sh.pop[b][i][tid];
-#pragma unroll
-            for (int q = 0; q < 10; ++q) g[q] = sh.pop[b][9 + q][tid];
-            const float da[3] = {sh.da[tid][0], sh.da[tid][1], sh.da[tid][2]};
-            collide_impl<true, float>(f, g, a.np, da);
-            const long long o = (long long)y * a.pitch + x;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) dst[(long long)i * a.plane + o] = f[i];
-#pragma unroll
-            for (int q = 0; q < 10; ++q) dst[(long long)(9 + q) * a.plane + o] = g[q];
-        }
-    }
-    cp_async_wait<0>();  // nothing left in flight when the block exits
-}
-
-cudaError_t launch_step_closure(const StepLaunch& s, const ClosureParamsDev& cp, cudaStream_t st) {
-    if (s.prec != 1 || s.wall_x || s.wall_y) return cudaErrorInvalidValue;
-    // the weight blocks are staged in 16-byte pieces
-    for (const void* w : {(const void*)cp.Wt1, (const void*)cp.Wt2, (const void*)cp.Wt3})
-        if (reinterpret_cast<uintptr_t>(w) % 16) return cudaErrorInvalidValue;
-    StepArgs<float> a;
-    a.src = s.src;
-    a.dst = s.dst;
-    a.nx = s.L.nx;
-    a.ny = s.L.ny;
-    a.pitch = s.L.pitch;
-    a.plane = s.L.plane;
-    a.np.omega = (float)s.omega;
-    a.np.omega_m = (float)s.omega_m;
-    a.np.rho0 = (float)s.rho0;
-    a.np.variant = s.variant;
-    a.np.collision = s.collision;
-    a.np.mag_collision = s.mag_collision;
-    a.wall_x = 0;
-    a.wall_y = 0;
-    const int ntx = (s.L.nx + kCTX - 1) / kCTX, nty = (s.L.ny + kCTY - 1) / kCTY, ntiles = ntx * nty;
-    const size_t smem = sizeof(ClosureShared);
-    cudaError_t e = cudaFuncSetAttribute(step_closure, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0, sms = 0, dev = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_closure, 256, smem);
-    if (e != cudaSuccess) return e;
-    const int blocks = std::max(1, std::min(ntiles, std::max(1, per_sm) * sms));
-    step_closure<<<blocks, dim3(kCTX, kCTY), smem, st>>>(a, cp, ntx, ntiles);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_filter(const Layout& L, int prec, const void* prev, int r, float* out, cudaStream_t st) {

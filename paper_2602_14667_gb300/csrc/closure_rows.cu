@@ -1,0 +1,303 @@
+// closure_rows.cu -- the closure step (learned correction of a1^(2), the
+// closure is not part of the paper) with one warp per tile of rows and the
+// MLP on warp-level mma.sync.
+//
+// A warp walks one tile: a strip of 30 output columns (lanes 1..30; lanes
+// 0 and 31 hold the neighbouring columns, so x neighbours arrive by warp
+// shuffles) and a stack of rows, downwards in even row segments and upwards
+// in odd ones.  For every row it pulls the pre-collision populations of its
+// 32 nodes (the step's gather, one node per lane), keeps u and b of the
+// last three rows and the populations of the last two in registers, and
+// for the row before the newest one forms the 24 features (point values
+// and the 3 x 3 stencils), runs the 24 -> 64 -> 64 -> 3 MLP on the warp's 32
+// feature rows (BF16 operands, FP32 accumulation; bias in the accumulator,
+// ReLU and the BF16 packing of the next layer's operand in one conversion),
+// adds the output to the projected a1^(2) and collides (tasks 3-5 of the
+// paper's "Algorithm of computation").  The only block-wide barrier is the
+// one after the weights are staged in shared memory; the feature rows and
+// outputs pass through a per-warp shared tile.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstddef>
+#include <cstdint>
+
+#include "closure_device.cuh"
+#include "closure_internal.h"
+
+namespace mhd {
+
+namespace {
+
+constexpr int kRWarps = 8;      // warps per block, each on its own tiles
+constexpr int kRFeat = 40;      // bf16 per feature row (80 bytes: conflict-free ldmatrix rows)
+constexpr int kRW1 = 40;        // padded weight rows (bf16): strides of 20 and 36 words put
+constexpr int kRW2 = 72;        // the 32 lanes of a B-fragment load in 32 banks
+
+struct RowsShared {
+    bf16 Wt1[kHid * kRW1];
+    bf16 Wt2[kHid * kRW2];
+    bf16 Wt3[kOutPad * kRW2];
+    float b1[kHid], b2[kHid], b3[kOutPad];
+    float mean[kIn], scale[kIn], out_scale[kOut];
+    alignas(16) bf16 feat[kRWarps][32 * kRFeat];
+    float da[kRWarps][32][4];
+};
+static_assert(offsetof(RowsShared, Wt1) % 16 == 0 && offsetof(RowsShared, Wt2) % 16 == 0 &&
+                  offsetof(RowsShared, Wt3) % 16 == 0 && offsetof(RowsShared, feat) % 16 == 0,
+              "ldmatrix sources must be 16-byte aligned");
+static_assert((kRW1 * sizeof(bf16)) % 16 == 0 && (kRW2 * sizeof(bf16)) % 16 == 0 &&
+                  (kRFeat * sizeof(bf16)) % 16 == 0,
+              "ldmatrix row strides must be multiples of 16 bytes");
+static_assert(offsetof(RowsShared, b1) % 8 == 0 && offsetof(RowsShared, b2) % 8 == 0 &&
+                  offsetof(RowsShared, b3) % 8 == 0,
+              "bias pairs are read as float2");
+
+// relu(lo), relu(hi) rounded to BF16 (nearest even) and packed: lo in the
+// low half, as the next layer's A fragment wants it.
+__device__ __forceinline__ uint32_t relu_pack2(float lo, float hi) {
+    uint32_t u;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;\n" : "=r"(u) : "f"(hi), "f"(lo));
+    return u;
+}
+
+// MLP of rows m0 .. m0+15 of the warp's feature tile; out_scale * y into da.
+__device__ __forceinline__ void mlp16(const RowsShared& sh, const bf16* feat, float (*da)[4], int m0, int lane) {
+    const int t = lane & 3, lr = lane & 7, lm = lane >> 3;
+    uint32_t a1[2][4];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) ldsm_x4(a1[c], feat + (m0 + lr + 8 * (lm & 1)) * kRFeat + 16 * c + 8 * (lm >> 1));
+    uint32_t h[4][4];  // layer 2's A fragments (K = 64)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float2 bb = *reinterpret_cast<const float2*>(sh.b1 + 8 * j + 2 * t);
+        float d[4] = {bb.x, bb.y, bb.x, bb.y};
+        uint32_t w[4];
+        ldsm_x4(w, sh.Wt1 + (8 * j + lr) * kRW1 + 8 * lm);
+        const uint32_t b0[2] = {w[0], w[1]}, b1[2] = {w[2], w[3]};
+        mma16816(d, a1[0], b0);
+        mma16816(d, a1[1], b1);
+        // the accumulator of n-tile j is half of k-chunk j/2 of the next A
+        h[j >> 1][(j & 1) * 2 + 0] = relu_pack2(d[0], d[1]);
+        h[j >> 1][(j & 1) * 2 + 1] = relu_pack2(d[2], d[3]);
+    }
+    uint32_t h2[4][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float2 bb = *reinterpret_cast<const float2*>(sh.b2 + 8 * j + 2 * t);
+        float d[4] = {bb.x, bb.y, bb.x, bb.y};
+#pragma unroll
+        for (int c = 0; c < 4; c += 2) {
+            uint32_t w[4];
+            ldsm_x4(w, sh.Wt2 + (8 * j + lr) * kRW2 + 16 * c + 8 * lm);
+            const uint32_t b0[2] = {w[0], w[1]}, b1[2] = {w[2], w[3]};
+            mma16816(d, h[c], b0);
+            mma16816(d, h[c + 1], b1);
+        }
+        h2[j >> 1][(j & 1) * 2 + 0] = relu_pack2(d[0], d[1]);
+        h2[j >> 1][(j & 1) * 2 + 1] = relu_pack2(d[2], d[3]);
+    }
+    const float2 bb = *reinterpret_cast<const float2*>(sh.b3 + 2 * t);
+    float d[4] = {bb.x, bb.y, bb.x, bb.y};
+#pragma unroll
+    for (int c = 0; c < 4; c += 2) {
+        uint32_t w[4];
+        ldsm_x4(w, sh.Wt3 + lr * kRW2 + 16 * c + 8 * lm);
+        const uint32_t b0[2] = {w[0], w[1]}, b1[2] = {w[2], w[3]};
+        mma16816(d, h2[c], b0);
+        mma16816(d, h2[c + 1], b1);
+    }
+    // d0: (row g, col 2t), d1: (g, 2t+1), d2: (g+8, 2t), d3: (g+8, 2t+1)
+    const int g = lane >> 2;
+    if (2 * t < kOut) {
+        da[m0 + g][2 * t] = d[0] * sh.out_scale[2 * t];
+        da[m0 + g + 8][2 * t] = d[2] * sh.out_scale[2 * t];
+    }
+    if (2 * t + 1 < kOut) {
+        da[m0 + g][2 * t + 1] = d[1] * sh.out_scale[2 * t + 1];
+        da[m0 + g + 8][2 * t + 1] = d[3] * sh.out_scale[2 * t + 1];
+    }
+}
+
+// d_x, d_y (isotropic gradient), the 9-point Laplacian and d_xy of the four
+// fields (u_x, u_y, b_x, b_y) at the lane's node, from w[r][q] with slot 1
+// the node's row and slots 2 / 0 the rows on either side (sgn = +1 when
+// slot 2 is the row above, -1 when it is the row below); x neighbours come
+// from the neighbouring lanes.  Same stencils as stencil_features.
+__device__ __forceinline__ void stencil_rows(const float (&w)[3][4], float sgn, float* out16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float C = w[1][q], N = w[2][q], S = w[0][q];
+        const float E = __shfl_down_sync(kFull, C, 1), W = __shfl_up_sync(kFull, C, 1);
+        const float NE = __shfl_down_sync(kFull, N, 1), NW = __shfl_up_sync(kFull, N, 1);
+        const float SE = __shfl_down_sync(kFull, S, 1), SW = __shfl_up_sync(kFull, S, 1);
+        out16[4 * q + 0] = (1.0f / 3.0f) * (E - W) + (1.0f / 12.0f) * ((NE - NW) + (SE - SW));
+        out16[4 * q + 1] = sgn * ((1.0f / 3.0f) * (N - S) + (1.0f / 12.0f) * ((NE - SE) + (NW - SW)));
+        out16[4 * q + 2] = (4.0f * ((E + W) + (N + S)) + ((NE + NW) + (SE + SW)) - 20.0f * C) * (1.0f / 6.0f);
+        out16[4 * q + 3] = sgn * (0.25f * ((NE - NW) - (SE - SW)));
+    }
+}
+
+template <typename Off>
+__global__ void __launch_bounds__(kRWarps * 32, 2) step_closure_rows(const StepArgs<float> a,
+                                                                     const ClosureParamsDev cp, int strips,
+                                                                     int rows, int ntiles) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RowsShared& sh = *reinterpret_cast<RowsShared*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float* src = static_cast<const float*>(a.src);
+    float* dst = static_cast<float*>(a.dst);
+    // the network: weight rows in 16-byte pieces into the padded shared rows
+    constexpr int kC1 = kInPad * 2 / 16, kC2 = kHid * 2 / 16;  // 16-byte pieces per weight row
+    for (int i = tid; i < kHid * kC1; i += kRWarps * 32)
+        cp_async16(sh.Wt1 + (i / kC1) * kRW1 + (i % kC1) * 8, cp.Wt1 + (i / kC1) * kInPad + (i % kC1) * 8);
+    for (int i = tid; i < kHid * kC2; i += kRWarps * 32)
+        cp_async16(sh.Wt2 + (i / kC2) * kRW2 + (i % kC2) * 8, cp.Wt2 + (i / kC2) * kHid + (i % kC2) * 8);
+    for (int i = tid; i < kOutPad * kC2; i += kRWarps * 32)
+        cp_async16(sh.Wt3 + (i / kC2) * kRW2 + (i % kC2) * 8, cp.Wt3 + (i / kC2) * kHid + (i % kC2) * 8);
+    cp_async_commit();
+    if (tid < kHid) { sh.b1[tid] = cp.b1[tid]; sh.b2[tid] = cp.b2[tid]; }
+    if (tid < kOutPad) sh.b3[tid] = cp.b3[tid];
+    if (tid < kIn) { sh.mean[tid] = cp.mean[tid]; sh.scale[tid] = cp.scale[tid]; }
+    if (tid < kOut) sh.out_scale[tid] = cp.out_scale[tid];
+    cp_async_wait<0>();
+    __syncthreads();
+
+    bf16* feat = sh.feat[warp];
+    float(*da)[4] = sh.da[warp];
+    const bool out_lane = lane >= 1 && lane <= 30;
+    const float rho0 = a.np.rho0;
+    for (int t = blockIdx.x * kRWarps + warp; t < ntiles; t += gridDim.x * kRWarps) {
+        const int strip = t % strips, seg = t / strips;
+        const int xl = strip * 30 - 1 + lane;  // the lane's node (may lie outside: wrapped)
+        int xw = xl % a.nx;
+        if (xw < 0) xw += a.nx;
+        const int y0 = seg * rows, y1 = min(a.ny, y0 + rows);
+        const bool up = seg & 1;
+        const float sgn = up ? -1.f : 1.f;
+        float wnd[3][4] = {};         // u_x, u_y, b_x, b_y of the last three rows (slot 2 newest)
+        float cur[kPlanes] = {}, nxt[kPlanes] = {};  // populations of the rows in slots 1, 2
+        const int nrow = y1 - y0 + 2;
+        for (int i = 0; i < nrow; ++i) {
+            const int m = up ? y1 - i : y0 - 1 + i;
+            const int my = m < 0 ? m + a.ny : (m >= a.ny ? m - a.ny : m);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                wnd[0][q] = wnd[1][q];
+                wnd[1][q] = wnd[2][q];
+            }
+#pragma unroll
+            for (int p = 0; p < kPlanes; ++p) cur[p] = nxt[p];
+            {
+                float v[kPlanes][1];
+                gather_row_wrapped<1, 1, false, Off>(src, a.nx, a.ny, a.pitch, a.plane, xw, my, lane, v);
+#pragma unroll
+                for (int p = 0; p < kPlanes; ++p) nxt[p] = v[p][0];
+                float f[9], g[10];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) f[k] = nxt[k];
+#pragma unroll
+                for (int k = 0; k < 10; ++k) g[k] = nxt[9 + k];
+                const Moments<float> mm = moments(f, g, rho0);
+                wnd[2][0] = mm.ux;
+                wnd[2][1] = mm.uy;
+                wnd[2][2] = mm.bx;
+                wnd[2][3] = mm.by;
+            }
+            if (i < 2) continue;  // warp-uniform
+            const int o = up ? m + 1 : m - 1;  // the row in slot 1: y0 <= o < y1
+            float fe[kIn];
+            {
+                float f[9], g[10];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) f[k] = cur[k];
+#pragma unroll
+                for (int k = 0; k < 10; ++k) g[k] = cur[9 + k];
+                point_features(f, g, rho0, fe);
+            }
+            stencil_rows(wnd, sgn, fe + 8);
+            {
+                uint32_t pk[kInPad / 2];
+#pragma unroll
+                for (int c = 0; c < kInPad / 2; ++c) {
+                    const float v0 = 2 * c < kIn ? (fe[2 * c] - sh.mean[2 * c]) * sh.scale[2 * c] : 0.f;
+                    const float v1 = 2 * c + 1 < kIn ? (fe[2 * c + 1] - sh.mean[2 * c + 1]) * sh.scale[2 * c + 1] : 0.f;
+                    pk[c] = pack2(v0, v1);
+                }
+                uint4* row = reinterpret_cast<uint4*>(feat + lane * kRFeat);
+#pragma unroll
+                for (int c = 0; c < kInPad / 8; ++c)
+                    row[c] = make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
+            }
+            __syncwarp();
+            mlp16(sh, feat, da, 0, lane);
+            mlp16(sh, feat, da, 16, lane);
+            __syncwarp();
+            if (out_lane && xl < a.nx) {
+                float f[9], g[10];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) f[k] = cur[k];
+#pragma unroll
+                for (int k = 0; k < 10; ++k) g[k] = cur[9 + k];
+                const float d3[3] = {da[lane][0], da[lane][1], da[lane][2]};
+                collide_impl<true, float>(f, g, a.np, d3);
+                const Off off = (Off)o * (Off)a.pitch + xl, pl = (Off)a.plane;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) dst[(Off)k * pl + off] = f[k];
+#pragma unroll
+                for (int k = 0; k < 10; ++k) dst[(Off)(9 + k) * pl + off] = g[k];
+            }
+            __syncwarp();  // the next row rewrites the warp's feature and output tiles
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_step_closure(const StepLaunch& s, const ClosureParamsDev& cp, cudaStream_t st) {
+    if (s.prec != 1 || s.wall_x || s.wall_y) return cudaErrorInvalidValue;
+    // the weight blocks are staged in 16-byte pieces
+    for (const void* w : {(const void*)cp.Wt1, (const void*)cp.Wt2, (const void*)cp.Wt3})
+        if (reinterpret_cast<uintptr_t>(w) % 16) return cudaErrorInvalidValue;
+    StepArgs<float> a;
+    a.src = s.src;
+    a.dst = s.dst;
+    a.nx = s.L.nx;
+    a.ny = s.L.ny;
+    a.pitch = s.L.pitch;
+    a.plane = s.L.plane;
+    a.np.omega = (float)s.omega;
+    a.np.omega_m = (float)s.omega_m;
+    a.np.rho0 = (float)s.rho0;
+    a.np.variant = s.variant;
+    a.np.collision = s.collision;
+    a.np.mag_collision = s.mag_collision;
+    a.wall_x = 0;
+    a.wall_y = 0;
+    const size_t smem = sizeof(RowsShared);
+    // int element offsets while the 19 planes hold fewer than 2^31 elements
+    const bool small = (long long)kPlanes * s.L.plane < (1LL << 31);
+    auto kernel = small ? step_closure_rows<int> : step_closure_rows<long long>;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0, dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kRWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    // tiles: strips of 30 columns, row segments so that the tiles are about
+    // as many as the resident warps
+    const long long strips = (s.L.nx + 29) / 30;
+    const long long maxb = (long long)std::max(1, per_sm) * sms;
+    const long long segs_want = std::max(1LL, maxb * kRWarps / strips);
+    const long long rows = ((long long)s.L.ny + segs_want - 1) / segs_want;
+    const long long segs = ((long long)s.L.ny + rows - 1) / rows;
+    const long long ntiles = strips * segs;
+    if (ntiles > (1LL << 30)) return cudaErrorInvalidValue;
+    const int blocks = (int)std::max(1LL, std::min(maxb, (ntiles + kRWarps - 1) / kRWarps));
+    kernel<<<blocks, kRWarps * 32, smem, st>>>(a, cp, (int)strips, (int)rows, (int)ntiles);
+    return cudaGetLastError();
+}
+
+}  // namespace mhd

@@ -133,6 +133,68 @@ __device__ __forceinline__ void step_row(const typename Prec<PREC>::S* __restric
     }
 }
 
+// Pre-collision populations of the V nodes x0 .. x0+V-1 of row y pulled
+// from the post-collision buffer src, where the lanes of the warp hold
+// consecutive vectors modulo nx (x0 wrapped into [0, nx), nx % V == 0):
+// gather_row with the warp's edge elements taken at the wrapped neighbours.
+// FP16S values stay in storage units.  Off as in gather_row.
+template <int PREC, int V, bool WALLY, typename Off = long long>
+__device__ __forceinline__ void gather_row_wrapped(const typename Prec<PREC>::S* __restrict__ src, int nx,
+                                                   int ny, long long pitch, long long plane, int x0, int y,
+                                                   int lane, typename Prec<PREC>::C (&v)[kPlanes][V]) {
+    using S = typename Prec<PREC>::S;
+    using C = typename Prec<PREC>::C;
+    int ym = y - 1, yp = y + 1;
+    bool bm = false, bp = false;
+    if (WALLY) {
+        bm = ym < 0;
+        bp = yp >= ny;
+    } else {
+        if (ym < 0) ym += ny;
+        if (yp >= ny) yp -= ny;
+    }
+    const int xl = x0 == 0 ? nx - 1 : x0 - 1;
+    const int xr = x0 + V >= nx ? x0 + V - nx : x0 + V;
+    const Off pl = (Off)plane, pt = (Off)pitch;
+    const Off o_m = (Off)ym * pt, o_0 = (Off)y * pt, o_p = (Off)yp * pt;
+    S r[kPlanes][V];
+    S edge[kPlanes];
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        const int cx = pcx(p), cy = pcy(p);
+        const bool bounce = WALLY && (cy > 0 ? bm : (cy < 0 ? bp : false));  // warp-uniform
+        const S* row = src + (bounce ? (Off)popp(p) * pl + o_0 : (Off)p * pl + (cy > 0 ? o_m : (cy < 0 ? o_p : o_0)));
+        VecIO<S, V>::load(row + x0, r[p]);
+        edge[p] = S(0);
+        if (cx > 0 && !bounce && lane == 0) edge[p] = row[xl];
+        if (cx < 0 && !bounce && lane == 31) edge[p] = row[xr];
+    }
+    using Codec = StepCodec<S, V>;
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        const int cx = pcx(p), cy = pcy(p);
+        const bool bounce = WALLY && (cy > 0 ? bm : (cy < 0 ? bp : false));
+        C c[V];
+        Codec::to_compute(r[p], c);
+        if (cx == 0 || bounce) {
+#pragma unroll
+            for (int k = 0; k < V; ++k) v[p][k] = c[k];
+        } else if (cx > 0) {  // source x - 1
+            C left = __shfl_up_sync(kFull, c[V - 1], 1);
+            if (lane == 0) left = Codec::template one<C>(edge[p]);
+            v[p][0] = left;
+#pragma unroll
+            for (int k = 1; k < V; ++k) v[p][k] = c[k - 1];
+        } else {  // source x + 1
+            C right = __shfl_down_sync(kFull, c[0], 1);
+            if (lane == 31) right = Codec::template one<C>(edge[p]);
+#pragma unroll
+            for (int k = 0; k < V - 1; ++k) v[p][k] = c[k + 1];
+            v[p][V - 1] = right;
+        }
+    }
+}
+
 // Pre-collision populations of node (x, y) gathered from a post-collision
 // buffer (pull streaming with half-way bounce-back on wall axes).
 template <typename S, typename C>
