@@ -69,6 +69,8 @@ def parse():
                     help="fixed launch shape 'V,BY' (skips the autotuner; for profiling)")
     ap.add_argument("--in-place", action="store_true",
                     help="ot4096 on one state buffer (in-place streaming) instead of two")
+    ap.add_argument("--lattices", type=int, default=512,
+                    help="ensemble: the first K of the 512 drawn lattices (a smaller case for profiling)")
     ap.add_argument("--no-extra", action="store_true",
                     help="ot4096 at N=1: leave out the extra rows (FP16S line and field error, ensemble)")
     return ap.parse_args()
@@ -90,9 +92,10 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-# The translation unit of the step kernels (kernels.cu) and what it includes.
-STEP_KERNEL_SOURCES = ("f32x2.cuh", "internal.h", "kernels.cu", "lbm_device.cuh", "step_row.cuh")
-DIAG_KERNEL_SOURCES = ("diag.cu", "f32x2.cuh", "internal.h", "lbm_device.cuh", "step_row.cuh")
+# The device code of the step kernels: kernels.cu and the device headers it
+# includes (internal.h holds only host declarations).
+STEP_KERNEL_SOURCES = ("f32x2.cuh", "kernels.cu", "lbm_device.cuh", "step_row.cuh")
+DIAG_KERNEL_SOURCES = ("diag.cu", "f32x2.cuh", "lbm_device.cuh", "step_row.cuh")
 
 
 def kernel_source_hash(sources=STEP_KERNEL_SOURCES):
@@ -513,7 +516,7 @@ def run_ensemble(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    draws = mhd_inputs.ensemble(512)
+    draws = mhd_inputs.ensemble(512)[:max(1, min(512, args.lattices))]
     mine = partition(draws, rank, world)           # replicas: lattices split over ranks
     stream = torch.cuda.Stream()
     sizes = [(d["n"], d["n"]) for d in mine]
@@ -559,7 +562,7 @@ def run_ensemble(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic",
-           "config": {"workload": "ensemble_512_random_spectrum_fp32", "lattices": len(mine),
+           "config": {"workload": f"ensemble_{len(draws)}_random_spectrum_fp32", "lattices": len(mine),
                       "nodes": nodes, "kernel_config": list(shape), "finite_after_run": finite},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "peak_source": peak_kind, "traffic": None},
