@@ -594,7 +594,12 @@ def run_closure(args):
     plain runs judged on a held-out seed against the filtered fine run.  The
     fine relaxation time is 0.54 (coarse 0.51): the workload's nu = eta =
     5e-5 lies beyond the scheme's stability limit near tau = 1/2, and a
-    coarse 0.505 already lets some seeds go non-finite."""
+    coarse 0.505 already lets some seeds go non-finite.
+    Two more arms: the untrained network of the same seed put through the
+    same calibration (what it gains is not due to training), and the plain
+    scheme on the finest grid whose run is predicted to take no more GPU
+    time than the closure run (equal GPU time; its fields box-filtered onto
+    the 512^2 grid like the fine run's)."""
     import torch
 
     from paper_2602_14667_gb300 import closure_study as cs
@@ -603,13 +608,22 @@ def run_closure(args):
                          sample_stride=1500, samples_per_seed=4,
                          eval_coarse_steps=(500, 1000, 1500, 2000), epochs=20, batch=8192)
     t0 = time.perf_counter()
-    res = cs.run(cfg)
+    res = cs.run(cfg, control=True, equal_time=True)
     wall = time.perf_counter() - t0
-    last = cfg.eval_coarse_steps[-1]
+    steps = cfg.eval_coarse_steps
+    last = steps[-1]
+    has_closure = "closure" in res
     sp, jp = res["plain"][last]
-    sc, jc = res.get("closure", res["plain"])[last]
+    sc, jc = res["closure"][last] if has_closure else (None, None)
     cost_p = res["plain"]["s_per_step"]
-    cost_c = res.get("closure", res["plain"])["s_per_step"]
+    cost_c = res["closure"]["s_per_step"] if has_closure else None
+    unt = res["untrained"]
+    et = res["equal_time"]
+    fine = et["plain_fine"]
+
+    def arm(r):
+        return None if r is None else {str(k): r[k] for k in steps}
+
     out = {"metric": "coarse+closure vs plain error (energy spectrum, current density) against the "
                      "filtered 2048^2 run",
            "value": sc, "unit": "relative spectrum error (closure, last checkpoint)",
@@ -617,15 +631,22 @@ def run_closure(args):
            "config": {"workload": "closure_2048_to_512", "tau_fine": cfg.tau_fine,
                       "tau_coarse": cs.coarse_tau(cfg.tau_fine, cfg.factor), "rms": cfg.rms,
                       "samples": res["samples"], "train_loss": res["train_loss"],
-                      "amplitude": res["amplitude"], "checkpoints": list(cfg.eval_coarse_steps),
+                      "amplitude": res["amplitude"], "checkpoints": list(steps),
                       "calibration_scores": {str(k): v for k, v in res["calibration_scores"].items()}},
-           "plain": {str(k): res["plain"][k] for k in cfg.eval_coarse_steps},
-           "closure": {str(k): res["closure"][k] for k in cfg.eval_coarse_steps} if "closure" in res else None,
+           "closure_arm": "present" if has_closure else "absent (calibration chose amplitude 0)",
+           "plain": arm(res["plain"]), "closure": arm(res.get("closure")),
            "spectrum_error": {"plain": sp, "closure": sc}, "current_error": {"plain": jp, "closure": jc},
            "s_per_coarse_step": {"plain": cost_p, "closure": cost_c},
+           "untrained_control": {"amplitude": unt["amplitude"],
+                                 "calibration_scores": {str(k): v for k, v in unt["calibration_scores"].items()},
+                                 "errors": arm(unt["run"])},
+           "equal_gpu_time": {"gpu_s": et["gpu_s"],
+                              "plain_grid": None if fine is None else fine["n"],
+                              "plain_grid_tau": None if fine is None else fine["tau"],
+                              "plain_grid_gpu_s": None if fine is None else fine["gpu_s"],
+                              "errors": {"closure_512": arm(res.get("closure")), "plain_512": arm(res["plain"]),
+                                         "plain_grid": arm(fine), "untrained_512": arm(unt["run"])}},
            "training": training_rate(res),
-           "equal_gpu_time_note": "a plain run at the next finer grid the fine run can be filtered to "
-                                  "(1024^2) costs 8x the plain 512^2 run",
            "wall_s": wall}
     print(json.dumps(out), flush=True)
 

@@ -111,6 +111,18 @@ def train(cfg: StudyConfig, X, T):
     return mlp
 
 
+def untrained(cfg: StudyConfig, X, T):
+    """The control: the network of the same seed with the same input and
+    output normalisation and masked columns, not trained."""
+    mlp = _abi.MLP(seed=cfg.mlp_seed, max_batch=cfg.batch)
+    mlp.fit_normalisation(X, T)
+    prm = mlp.get_params()
+    for c in MASKED_FEATURES:
+        prm[24 + c] = 0.0
+    mlp.set_params(prm)
+    return mlp
+
+
 def _coarse_fields_from_state(state, n):
     """rho, ux, uy, bx, by of a packed FP32 coarse pre-collision state (host)."""
     w = np.array([4 / 9] + [1 / 36, 1 / 9] * 4)
@@ -165,6 +177,28 @@ def _block_mean(a, r):
     return a.reshape(n0 // r, r, n1 // r, r).mean(axis=(1, 3))
 
 
+def filtered_onto_coarse(fields, n_fine: int, factor: int, n_coarse: int):
+    """(rho, ux, uy, bx, by) of a periodic run on an n x n grid (any n),
+    box-filtered and sampled like the fine reference: coarse node X holds the
+    average over the fine nodes factor X .. factor X + factor - 1 (fine
+    spacing 2 pi / n_fine) of the run's trigonometric interpolant.  Linear
+    in rho, rho u and b, so u follows from the filtered momentum."""
+    rho, ux, uy, bx, by = fields
+    n = rho.shape[0]
+    k = np.fft.fftfreq(n, 1.0 / n)                       # signed integer wave numbers
+    h = 2.0 * np.pi / n_fine
+    D = np.mean([np.exp(1j * k * j * h) for j in range(factor)], axis=0)
+    K = np.rint(k).astype(int) % n_coarse
+    out = []
+    for q in (rho, rho * ux, rho * uy, bx, by):
+        c = np.fft.fft2(q) / (n * n) * D[:, None] * D[None, :]
+        acc = np.zeros((n_coarse, n_coarse), dtype=complex)
+        np.add.at(acc, (K[:, None], K[None, :]), c)
+        out.append(np.real(np.fft.ifft2(acc)) * n_coarse * n_coarse)
+    r, mx, my, b_x, b_y = out
+    return r, mx / r, my / r, b_x, b_y
+
+
 def reference(cfg: StudyConfig, seed: int):
     """Filtered fine fields at each of eval_coarse_steps, and the t = 0 fields
     block-averaged onto the coarse grid."""
@@ -211,6 +245,71 @@ def coarse_run(cfg: StudyConfig, fields0, refs, mlp=None, timing=False):
     return res
 
 
+def plain_run_at(cfg: StudyConfig, n: int, seed: int, refs, stream=None):
+    """Plain RR run of the same flow on an n x n lattice (acoustic scaling:
+    n / n_coarse steps per coarse step, tau = 1/2 + (tau_fine - 1/2) n / n_fine),
+    started from the t = 0 fields sampled at its nodes; its fields are
+    box-filtered onto the coarse grid and judged like the coarse runs.
+    Returns the errors per checkpoint and the GPU seconds of its steps."""
+    import torch
+
+    import mhd_inputs
+    nc = cfg.n_coarse
+    tau = 0.5 + (cfg.tau_fine - 0.5) * n / cfg.n_fine
+    res, gpu_s = {}, 0.0
+    with Lattice(n, n, tau, tau, precision="fp32", stream=None if stream is None else stream.cuda_stream) as lat:
+        lat.set_fields(*mhd_inputs.random_spectrum(n, n, seed, cfg.rms, cfg.rms))
+        done = 0
+        for k in cfg.eval_coarse_steps:
+            steps = k * n // nc - done
+            done += steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.advance(steps)
+            e1.record(stream)
+            e1.synchronize()
+            gpu_s += e0.elapsed_time(e1) * 1e-3
+            f = lat.get_fields()
+            model = filtered_onto_coarse((f["rho"], f["ux"], f["uy"], f["bx"], f["by"]), cfg.n_fine,
+                                         cfg.factor, nc)
+            res[k] = errors(model, refs[k], nc // 4)
+    res["gpu_s"] = gpu_s
+    res["n"] = n
+    res["tau"] = tau
+    return res
+
+
+def coarse_gpu_seconds(cfg: StudyConfig, fields0, mlp=None, stream=None):
+    """GPU seconds of the coarse run's steps up to the last checkpoint."""
+    import torch
+    nc = cfg.n_coarse
+    tau_c = coarse_tau(cfg.tau_fine, cfg.factor)
+    with Lattice(nc, nc, tau_c, tau_c, precision="fp32", stream=None if stream is None else stream.cuda_stream) as c:
+        c.set_fields(*fields0)
+        if mlp is not None:
+            _abi.set_closure(c, mlp)
+            c.autotune()          # the faster closure kernel; the state is kept
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c.advance(cfg.eval_coarse_steps[-1])
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) * 1e-3
+
+
+def equal_time_grid(cfg: StudyConfig, t_closure: float, t_plain: float) -> int:
+    """The finest n (a multiple of 128, so that every checkpoint is a whole
+    number of its steps) at which a plain run to the last checkpoint is
+    predicted to take at most the closure run's GPU time: acoustic scaling
+    makes the cost grow as n^3 (n^2 nodes, n steps per unit time)."""
+    n = cfg.n_coarse
+    while (n + 128) ** 3 / cfg.n_coarse ** 3 * t_plain <= t_closure:
+        n += 128
+    return n
+
+
 def _score(res, cfg):
     """Calibration objective: spectrum plus current-density errors, summed
     over the checkpoints (+inf for a run that went non-finite)."""
@@ -253,9 +352,15 @@ def evaluate(cfg: StudyConfig, mlp=None, seed=None):
     return out
 
 
-def run(cfg: StudyConfig | None = None) -> dict:
+def run(cfg: StudyConfig | None = None, control: bool = False, equal_time: bool = False) -> dict:
     """Data from the training seeds, GPU training, a posteriori calibration
-    on the first training seed, evaluation on the held-out seed."""
+    on the first training seed, evaluation on the held-out seed.
+
+    control: also calibrate and evaluate the untrained network of the same
+    seed and normalisation (res["untrained"]): whatever it gains is not due
+    to training.  equal_time: also time the coarse closure and plain runs on
+    the GPU and run the plain scheme on the finest grid that is predicted to
+    cost no more than the closure run (res["equal_time"])."""
     import torch
     cfg = cfg or StudyConfig()
     X, T = generate_data(cfg)
@@ -268,5 +373,21 @@ def run(cfg: StudyConfig | None = None) -> dict:
     res = evaluate(cfg, mlp if c != 0.0 else None)
     res.update(samples=int(X.shape[0]), train_loss=mlp.last_loss, amplitude=c,
                calibration_scores=scores, train_s=train_s, epochs=cfg.epochs)
+    if control:
+        ctl = untrained(cfg, X, T)
+        cu, su = calibrate(cfg, ctl)
+        refs, fields0 = reference(cfg, cfg.eval_seed)
+        res["untrained"] = {"amplitude": cu, "calibration_scores": su,
+                            "run": coarse_run(cfg, fields0, refs, ctl if cu != 0.0 else None)}
+        ctl.close()
+    if equal_time:
+        refs, fields0 = reference(cfg, cfg.eval_seed)
+        stream = torch.cuda.Stream()
+        t_plain = coarse_gpu_seconds(cfg, fields0, None, stream)
+        t_closure = coarse_gpu_seconds(cfg, fields0, mlp if c != 0.0 else None, stream)
+        n = equal_time_grid(cfg, t_closure, t_plain)
+        res["equal_time"] = {"gpu_s": {"plain_coarse": t_plain, "closure_coarse": t_closure},
+                             "plain_fine": plain_run_at(cfg, n, cfg.eval_seed, refs, stream) if n > cfg.n_coarse
+                             else None}
     mlp.close()
     return res
