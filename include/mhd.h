@@ -54,7 +54,13 @@ typedef enum {
     MHD_FP16S = 2  /* IEEE FP16 of 2^12 (f_i - w_i rho0) and 2^12 g, FP32 arithmetic */
 } mhd_precision;
 
-typedef enum { MHD_PERIODIC = 0, MHD_WALL = 1 } mhd_bc; /* per axis; walls: half-way bounce-back */
+/* Boundary of an axis.  MHD_WALL: half-way bounce-back.  MHD_HALO (bc_y
+ * only): the lattice is one slab of a periodic lattice split into row slabs
+ * (a domain decomposition of the y axis, e.g. one slab per GPU); it keeps
+ * one ghost row below row 0 and one above row ny-1, which
+ * mhd_slab_exchange fills from the neighbouring slabs after every step.
+ * Two-buffer streaming only, no closure. */
+typedef enum { MHD_PERIODIC = 0, MHD_WALL = 1, MHD_HALO = 2 } mhd_bc;
 
 typedef enum {
     MHD_RR = 0, /* recursive regularised (the paper's scheme) */
@@ -186,6 +192,28 @@ mhd_status mhd_set_populations(mhd_lattice* l, const double* f, const double* g)
 mhd_status mhd_state_bytes(const mhd_lattice* l, size_t* bytes);
 mhd_status mhd_get_state(mhd_lattice* l, void* host, size_t bytes);
 mhd_status mhd_set_state(mhd_lattice* l, const void* host, size_t bytes);
+
+/* Halo exchange between two neighbouring slabs of a row-decomposed
+ * periodic lattice (the decomposition of the y axis along which the step
+ * shards over GPUs; see MHD_HALO).  `lower` holds the rows just below
+ * `upper` in the global lattice (for the periodic wrap, the top slab is the
+ * lower neighbour of the bottom one; one slab alone is its own neighbour).
+ * Pull streaming carries across the boundary exactly the populations whose
+ * velocity crosses it: from the top row of `lower` into the ghost row below
+ * `upper` those with c_y = +1 (f_1, f_7, f_8 and g_4: 3 fluid populations and
+ * one magnetic vector), from the bottom row of `upper` into the ghost row
+ * above `lower` those with c_y = -1 (f_3, f_4, f_5 and g_2).  all_planes = 1
+ * copies all 19 populations of those rows instead, which mhd_get_totals of a
+ * slab needs (the gradient stencil at the slab's edge rows reads the moments
+ * of the ghost rows).  Both lattices: bc_y = MHD_HALO, the same nx,
+ * precision and bc_x, on devices that can copy to each other.  Usage: after
+ * mhd_set_fields / mhd_set_populations / mhd_set_state, and after every
+ * mhd_advance(l, 1), exchange every boundary once before the next step.
+ * The copies are queued on the receiving lattice's stream after that
+ * stream has been made to wait for the sending lattice's stream; nothing
+ * waits on the host.  A lattice that has not been exchanged keeps the
+ * ghost rows it had (zeros after mhd_create). */
+mhd_status mhd_slab_exchange(mhd_lattice* lower, mhd_lattice* upper, int all_planes);
 
 /* Allocation-free global diagnostics (the paper has no counterpart to this
  * call; it is a service for callers that cannot allocate device memory

@@ -5,7 +5,7 @@ method for magnetohydrodynamics").
 The solver is the CUDA library ``libmhdlbm.so`` behind the C ABI of
 ``include/mhd.h``; this package is its thin Python binding.
 """
-from ._abi import (MHD_BGK, MHD_FP16S, MHD_FP32, MHD_FP64, MHD_IN_PLACE, MHD_MAG_BGK,
+from ._abi import (MHD_BGK, MHD_FP16S, MHD_FP32, MHD_FP64, MHD_HALO, MHD_IN_PLACE, MHD_MAG_BGK,
                    MHD_MAG_REGULARISED, MHD_PERIODIC, MHD_RR, MHD_TWO_BUFFERS, MHD_WALL, Batch, Lattice,
                    MhdError, check, lib)
 
@@ -18,4 +18,4 @@ def tau_from_viscosity(nu: float) -> float:
 
 __all__ = ["Lattice", "Batch", "MhdError", "lib", "check", "tau_from_viscosity", "MHD_FP64", "MHD_FP32",
            "MHD_FP16S", "MHD_PERIODIC", "MHD_WALL", "MHD_RR", "MHD_BGK",
-           "MHD_MAG_BGK", "MHD_MAG_REGULARISED", "MHD_TWO_BUFFERS", "MHD_IN_PLACE"]
+           "MHD_MAG_BGK", "MHD_MAG_REGULARISED", "MHD_TWO_BUFFERS", "MHD_IN_PLACE", "MHD_HALO"]

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libmhdlbm.so")
 
 MHD_OK, MHD_EINVAL, MHD_ENOMEM, MHD_ECUDA, MHD_EUNSTABLE, MHD_ESTATE = range(6)
 MHD_FP64, MHD_FP32, MHD_FP16S = range(3)
-MHD_PERIODIC, MHD_WALL = range(2)
+MHD_PERIODIC, MHD_WALL, MHD_HALO = range(3)
 MHD_RR, MHD_BGK = range(2)
 MHD_MAG_BGK, MHD_MAG_REGULARISED = range(2)
 MHD_TWO_BUFFERS, MHD_IN_PLACE = range(2)
@@ -68,6 +68,7 @@ _SIGNATURES = {
     "mhd_autotune": [_P, ctypes.POINTER(mhd_kernel_config)],
     "mhd_destroy": [_P],
     "mhd_state_bytes": [_P, ctypes.POINTER(ctypes.c_size_t)],
+    "mhd_slab_exchange": [_P, _P, ctypes.c_int],
     "mhd_totals_noalloc": [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(mhd_params), _P,
                            ctypes.POINTER(mhd_totals)],
     "mhd_batch_create": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -146,10 +147,11 @@ class Lattice:
     def __init__(self, nx: int, ny: int, tau_f: float, tau_m: float, precision="fp32",
                  rho0: float = 1.0, wall_x: bool = False, wall_y: bool = False, eq_variant: int = 0,
                  collision: int = MHD_RR, stream=None, mag_collision: int = MHD_MAG_BGK,
-                 in_place: bool = False):
+                 in_place: bool = False, halo_y: bool = False):
         self.nx, self.ny = int(nx), int(ny)
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        self.params = mhd_params(rho0, tau_f, tau_m, int(wall_x), int(wall_y), prec, eq_variant,
+        bc_y = MHD_HALO if halo_y else int(wall_y)
+        self.params = mhd_params(rho0, tau_f, tau_m, int(wall_x), bc_y, prec, eq_variant,
                                  collision, mag_collision, MHD_IN_PLACE if in_place else MHD_TWO_BUFFERS)
         self._h = _P()
         s = None if stream is None else _P(int(stream))
@@ -247,6 +249,12 @@ class Lattice:
         c = mhd_kernel_config()
         check(lib().mhd_autotune(self._h, ctypes.byref(c)), "mhd_autotune")
         return c.nodes_per_thread, c.rows_per_block
+
+
+def slab_exchange(lower: "Lattice", upper: "Lattice", all_planes: bool = False) -> None:
+    """mhd_slab_exchange: fill the ghost rows across the boundary between two
+    neighbouring slabs (lower: the rows just below upper)."""
+    check(lib().mhd_slab_exchange(lower.handle, upper.handle, int(all_planes)), "mhd_slab_exchange")
 
 
 def totals_noalloc(state_ptr: int, nx: int, ny: int, params: "mhd_params", prev_ptr=None,

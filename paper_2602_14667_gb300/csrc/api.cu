@@ -16,6 +16,7 @@
 #include "closure_internal.h"
 #include "inplace.h"
 #include "internal.h"
+#include "lbm_device.cuh"
 
 namespace {
 
@@ -73,6 +74,13 @@ struct mhd_lattice {
     cudaStream_t cap = nullptr;
     mhd::Layout L{};
     void* buf[2] = {nullptr, nullptr};  // in place: buf[0] only
+    // slab (bc_y = MHD_HALO): each buffer holds ny + 2 rows, ghost rows
+    // first and last; buf[] point at row 0, alloc[] at the ghost row below,
+    // and Lx describes the ny + 2 rows the step runs over
+    bool halo = false;
+    mhd::Layout Lx{};
+    void* alloc[2] = {nullptr, nullptr};
+    cudaEvent_t xev = nullptr;  // marks the state a slab exchange copies from
     int cur = 0;
     bool in_place = false;
     bool aa_streamed = false;  // in place, after an odd number of steps: streamed layout
@@ -113,6 +121,15 @@ mhd::StepLaunch step_launch(const mhd_lattice* l, int from) {
     s.wall_y = l->p.bc_y == MHD_WALL;
     s.V = l->cfg.nodes_per_thread;
     s.BY = l->cfg.rows_per_block;
+    if (l->halo) {
+        // A slab steps as a periodic lattice of its ny + 2 rows: rows 0..ny-1
+        // pull from the ghost rows, which hold the neighbours' edge rows; the
+        // ghost rows' own update reads stale values and is overwritten by the
+        // next exchange.
+        s.L = l->Lx;
+        s.src = l->alloc[from];
+        s.dst = l->alloc[from ^ 1];
+    }
     return s;
 }
 
@@ -229,8 +246,11 @@ mhd_status check_params(const mhd_params* p) {
     if (!(std::isfinite(p->tau_f) && p->tau_f > 0.5)) return fail(MHD_EINVAL, "tau_f must be > 1/2");
     if (!(std::isfinite(p->tau_m) && p->tau_m > 0.5)) return fail(MHD_EINVAL, "tau_m must be > 1/2");
     if (!(std::isfinite(p->rho0) && p->rho0 > 0)) return fail(MHD_EINVAL, "rho0 must be > 0");
-    if ((p->bc_x != MHD_PERIODIC && p->bc_x != MHD_WALL) || (p->bc_y != MHD_PERIODIC && p->bc_y != MHD_WALL))
-        return fail(MHD_EINVAL, "bc_x / bc_y must be MHD_PERIODIC or MHD_WALL");
+    if ((p->bc_x != MHD_PERIODIC && p->bc_x != MHD_WALL) ||
+        (p->bc_y != MHD_PERIODIC && p->bc_y != MHD_WALL && p->bc_y != MHD_HALO))
+        return fail(MHD_EINVAL, "bc_x must be MHD_PERIODIC or MHD_WALL, bc_y one of those or MHD_HALO");
+    if (p->bc_y == MHD_HALO && p->streaming != MHD_TWO_BUFFERS)
+        return fail(MHD_EINVAL, "slabs (bc_y = MHD_HALO) use two-buffer streaming");
     if (p->precision < MHD_FP64 || p->precision > MHD_FP16S)
         return fail(MHD_EINVAL, "unknown precision");
     if (p->eq_variant != 0 && p->eq_variant != 1) return fail(MHD_EINVAL, "eq_variant must be 0 or 1");
@@ -263,11 +283,22 @@ mhd_status mhd_create(int nx, int ny, const mhd_params* p, void* stream, mhd_lat
     l->ny = ny;
     l->p = *p;
     l->stream = static_cast<cudaStream_t>(stream);
-    l->L = mhd::make_layout(nx, ny, p->precision);
     l->in_place = p->streaming == MHD_IN_PLACE;
+    l->halo = p->bc_y == MHD_HALO;
+    if (l->halo) {
+        l->Lx = mhd::make_layout(nx, ny + 2, p->precision);
+        l->L = l->Lx;  // the interior: rows 1..ny of each plane
+        l->L.ny = ny;
+    } else {
+        l->L = mhd::make_layout(nx, ny, p->precision);
+    }
     cudaError_t e = cudaGetDevice(&l->dev);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&l->cap, cudaStreamNonBlocking);
-    for (int b = 0; b < (l->in_place ? 1 : 2) && e == cudaSuccess; ++b) e = cudaMalloc(&l->buf[b], l->buf_bytes());
+    for (int b = 0; b < (l->in_place ? 1 : 2) && e == cudaSuccess; ++b) {
+        e = cudaMalloc(&l->alloc[b], l->buf_bytes());
+        if (e == cudaSuccess && l->halo) e = cudaMemset(l->alloc[b], 0, l->buf_bytes());
+        l->buf[b] = l->halo ? static_cast<char*>(l->alloc[b]) + l->L.pitch * l->L.esize : l->alloc[b];
+    }
     if (e == cudaSuccess)
         e = cudaMalloc(&l->partials, sizeof(double) * mhd::kDiagSlots * mhd::diag_blocks(l->L));
     if (e == cudaSuccess) e = cudaMalloc(&l->totals_d, sizeof(double) * mhd::kDiagSlots);
@@ -296,7 +327,7 @@ mhd_status mhd_destroy(mhd_lattice* l) {
     cudaSetDevice(l->dev);
     if (l->stream || l->buf[0]) cudaStreamSynchronize(l->stream);
     drop_graphs(l);
-    for (auto& b : l->buf)
+    for (auto& b : l->alloc)
         if (b) cudaFree(b);
     if (l->io) cudaFree(l->io);
     if (l->closure_buf) cudaFree(l->closure_buf);
@@ -305,6 +336,7 @@ mhd_status mhd_destroy(mhd_lattice* l) {
     if (l->totals_h) cudaFreeHost(l->totals_h);
     if (l->flags_d) cudaFree(l->flags_d);
     if (l->cap) cudaStreamDestroy(l->cap);
+    if (l->xev) cudaEventDestroy(l->xev);
     delete l;
     return MHD_OK;
 }
@@ -455,7 +487,9 @@ mhd_status mhd_get_totals(mhd_lattice* l, mhd_totals* out) {
     d.prec = l->p.precision;
     d.prev = l->buf[l->cur ^ 1];
     d.cur = l->buf[l->cur];
-    d.mode = l->prev_valid ? 0 : 1;
+    // (a slab reads the moments of its ghost rows for the stencil at its
+    // edge rows, so it reduces the stored state)
+    d.mode = (l->prev_valid && !l->halo) ? 0 : 1;
     d.omega_m = 1.0 / l->p.tau_m;
     d.rho0 = l->p.rho0;
     const double om1 = 1.0 - d.omega_m;
@@ -464,6 +498,7 @@ mhd_status mhd_get_totals(mhd_lattice* l, mhd_totals* out) {
     d.neq_scale = d.mode == 0 ? 1.0 : ((l->state_is_eq || std::fabs(om1) < 1e-12) ? 0.0 : 1.0 / om1);
     d.wall_x = l->p.bc_x == MHD_WALL;
     d.wall_y = l->p.bc_y == MHD_WALL;
+    d.halo_y = l->halo;
     CK(mhd::launch_diag(d, l->partials, mhd::diag_blocks(l->L), l->totals_d, l->stream), "diagnostics kernel");
     CK(cudaMemcpyAsync(l->totals_h, l->totals_d, sizeof(double) * mhd::kDiagSlots,
                        cudaMemcpyDeviceToHost, l->stream),
@@ -649,6 +684,42 @@ mhd_status mhd_state_bytes(const mhd_lattice* l, size_t* bytes) {
     if (!l || !bytes) return fail(MHD_EINVAL, "NULL argument");
     *bytes = (size_t)mhd::kStatePlanes * (size_t)l->n() * (size_t)l->L.esize;
     return MHD_OK;
+}
+
+mhd_status mhd_slab_exchange(mhd_lattice* lower, mhd_lattice* upper, int all_planes) {
+    if (!lower || !upper) return fail(MHD_EINVAL, "lattice is NULL");
+    if (!lower->halo || !upper->halo) return fail(MHD_EINVAL, "slab exchange needs bc_y = MHD_HALO lattices");
+    if (lower->nx != upper->nx || lower->p.precision != upper->p.precision || lower->p.bc_x != upper->p.bc_x)
+        return fail(MHD_EINVAL, "the slabs of one lattice share nx, precision and bc_x");
+    for (mhd_lattice* l : {lower, upper})
+        if (!l->xev) {
+            CK(cudaSetDevice(l->dev), "cudaSetDevice");
+            CK(cudaEventCreateWithFlags(&l->xev, cudaEventDisableTiming), "exchange event");
+        }
+    // the edge rows are final once each lattice's queued steps are done
+    CK(cudaSetDevice(lower->dev), "cudaSetDevice");
+    CK(cudaEventRecord(lower->xev, lower->stream), "exchange event");
+    CK(cudaSetDevice(upper->dev), "cudaSetDevice");
+    CK(cudaEventRecord(upper->xev, upper->stream), "exchange event");
+    const size_t es = lower->L.esize, row = (size_t)lower->nx * es;
+    // from `from`'s interior row `src_row` into `to`'s row `dst_row` (-1 or
+    // ny: a ghost row), the planes whose c_y equals `cy` (all with all_planes)
+    auto copy = [&](mhd_lattice* from, int src_row, mhd_lattice* to, int dst_row, int cy) -> mhd_status {
+        CK(cudaSetDevice(to->dev), "cudaSetDevice");
+        CK(cudaStreamWaitEvent(to->stream, from->xev, 0), "exchange wait");
+        const char* sb = static_cast<const char*>(from->buf[from->cur]);
+        char* db = static_cast<char*>(to->buf[to->cur]);
+        for (int p = 0; p < mhd::kStatePlanes; ++p) {
+            if (!all_planes && mhd::pcy(p) != cy) continue;
+            const char* src = sb + ((long long)p * from->L.plane + (long long)src_row * from->L.pitch) * (long long)es;
+            char* dst = db + ((long long)p * to->L.plane + (long long)dst_row * to->L.pitch) * (long long)es;
+            CK(cudaMemcpyAsync(dst, src, row, cudaMemcpyDefault, to->stream), "halo copy");
+        }
+        return MHD_OK;
+    };
+    mhd_status s = copy(lower, lower->ny - 1, upper, -1, +1);
+    if (s == MHD_OK) s = copy(upper, 0, lower, lower->ny, -1);
+    return s;
 }
 
 mhd_status mhd_get_state(mhd_lattice* l, void* host, size_t bytes) {

@@ -63,6 +63,7 @@ template <typename C> struct DiagArgs {
     long long pitch, plane;
     C omega_m, rho0, neq_scale;
     int wall_x, wall_y;
+    int halo_y;        // rows -1 and ny are read from the ghost rows (a slab)
     int strips;        // tiles along x (30 V output columns each)
     int rows;          // output rows per tile (H)
     int ntiles;
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(kDWarps * 32, PREC == 0 ? 1 : 2) diag_kernel(c
                 }
             int my = m;
             bool have = true;
-            if (my < 0 || my >= a.ny) {
+            if ((my < 0 || my >= a.ny) && !a.halo_y) {
                 if (a.wall_y) have = false;
                 else my = my < 0 ? my + a.ny : my - a.ny;
             }
@@ -448,6 +449,8 @@ static cudaError_t launch_diag_t(const DiagLaunch& d, double* partials, int capa
     a.neq_scale = C(d.neq_scale);
     a.wall_x = d.wall_x;
     a.wall_y = d.wall_y;
+    a.halo_y = d.halo_y;
+    if (d.halo_y && d.mode != 1) return cudaErrorInvalidValue;
     const long long strips = (d.L.nx + 30LL * V - 1) / (30LL * V);
     if (strips > INT_MAX) return cudaErrorInvalidValue;
     a.strips = (int)strips;

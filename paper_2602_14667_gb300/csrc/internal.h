@@ -69,6 +69,7 @@ struct DiagLaunch {
     int mode;
     double omega_m, rho0, neq_scale;
     int wall_x, wall_y;
+    int halo_y = 0;  // slab: rows -1 and ny are ghost rows of `cur` (mode 1 only)
 };
 int diag_blocks(const Layout& L);
 cudaError_t launch_diag(const DiagLaunch& d, double* partials, int capacity, double* totals, cudaStream_t st);
