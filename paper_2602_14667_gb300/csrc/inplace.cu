@@ -15,19 +15,27 @@
 namespace mhd {
 
 // FP16S phase A (node pairs on FP32x2 beside the x-shift logic of both the
-// gather and the write-back) needs about 150 registers to run without
-// spilling: blocks of at most 256 threads.
+// gather and the write-back) runs in blocks of at most 256 threads, two of
+// them per SM, i.e. at most 128 registers; at four nodes per lane it holds
+// the populations as packed halves (aa_row_a_h4), which spills least under
+// that cap (4096^2 in place: 71.6k MLUPS, against 70.7k with all four nodes
+// in FP32 and about 150 registers, 68.0k with those capped at 128).
 constexpr int aa_a_max_threads(int prec) { return prec == 2 ? 256 : 512; }
 
 template <int PREC, int V, bool WALLY, typename Off>
-__global__ void __launch_bounds__(aa_a_max_threads(PREC)) aa_step_a(const StepArgs<typename Prec<PREC>::C> a, int nxb,
+__global__ void __launch_bounds__(aa_a_max_threads(PREC), PREC == 2 ? 2 : 1) aa_step_a(const StepArgs<typename Prec<PREC>::C> a, int nxb,
                                                  int ntiles) {
     using S = typename Prec<PREC>::S;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int y = (t / nxb) * blockDim.y + threadIdx.y;
-        if (y < a.ny)  // whole warp
-            aa_row_a<PREC, V, WALLY, Off>(static_cast<S*>(a.dst), a.nx, a.ny, a.pitch, a.plane, a.np,
-                                          t % nxb, y, threadIdx.x);
+        if (y < a.ny) {  // whole warp
+            if constexpr (PREC == 2 && V == 4)
+                aa_row_a_h4<WALLY, Off>(static_cast<S*>(a.dst), a.nx, a.ny, a.pitch, a.plane, a.np, t % nxb, y,
+                                        threadIdx.x);
+            else
+                aa_row_a<PREC, V, WALLY, Off>(static_cast<S*>(a.dst), a.nx, a.ny, a.pitch, a.plane, a.np,
+                                              t % nxb, y, threadIdx.x);
+        }
     }
 }
 

@@ -182,6 +182,155 @@ __device__ __forceinline__ void aa_row_a(typename Prec<PREC>::S* buf, int nx, in
     }
 }
 
+// Phase A for FP16S storage at four nodes per lane, with the populations
+// held as packed halves (two nodes per 32-bit register) except while a
+// node pair collides: the x shifts of the gather and of the write-back move
+// packed halves with byte permutes, and each pair of nodes is decoded,
+// collided on FP32x2 in storage units and re-encoded before the next pair
+// is decoded.  The conversions, the pairs and the arithmetic are those of
+// the two-buffer step, so the bits are the same; about half the registers
+// of holding all four nodes' populations as FP32.  Same requirements as
+// aa_row_a.
+template <bool WALLY, typename Off = long long>
+__device__ __forceinline__ void aa_row_a_h4(__half* buf, int nx, int ny, long long pitch, long long plane,
+                                            const NodeParams<float>& np, int xblock, int y, int lane) {
+    constexpr int V = 4;
+    const int x0 = (xblock * 32 + lane) * V;
+    const bool active = x0 < nx;
+    int ym = y - 1, yp = y + 1;
+    bool bm = false, bp = false;
+    if (WALLY) {
+        bm = ym < 0;
+        bp = yp >= ny;
+    } else {
+        if (ym < 0) ym += ny;
+        if (yp >= ny) yp -= ny;
+    }
+    const int xl = (x0 == 0) ? nx - 1 : x0 - 1;
+    const int xr = (x0 + V >= nx) ? x0 + V - nx : x0 + V;
+    const bool right_by_shfl = (lane < 31) && (x0 + V < nx);
+    const Off pl = (Off)plane, pt = (Off)pitch;
+    const Off o_m = (Off)ym * pt, o_0 = (Off)y * pt, o_p = (Off)yp * pt;
+    auto slot_bounce = [&](int p) -> bool {
+        const int cy = pcy(p);
+        return WALLY && (cy > 0 ? bm : (cy < 0 ? bp : false));
+    };
+    auto slot_off = [&](int p) -> Off {
+        return slot_bounce(p) ? (Off)popp(p) * pl + o_0
+                              : (Off)p * pl + (pcy(p) > 0 ? o_m : (pcy(p) < 0 ? o_p : o_0));
+    };
+
+    // gather: halves (x0, x0+1) in lo, (x0+2, x0+3) in hi; every load first
+    uint32_t lo[kPlanes], hi[kPlanes];
+    unsigned short edge[kPlanes];
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        const int cx = pcx(p);
+        const bool bounce = slot_bounce(p);
+        const __half* row = buf + slot_off(p);
+        lo[p] = hi[p] = 0u;
+        edge[p] = 0;
+        if (active) {
+            const uint2 u = *reinterpret_cast<const uint2*>(row + x0);
+            lo[p] = u.x;
+            hi[p] = u.y;
+        }
+        if (cx > 0 && !bounce && lane == 0 && active) edge[p] = __half_as_ushort(row[xl]);
+        if (cx < 0 && !bounce && !right_by_shfl && active) edge[p] = __half_as_ushort(row[xr]);
+    }
+    // x shifts: source x - 1 -> (left, h0, h1, h2); source x + 1 -> (h1, h2, h3, right)
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        const int cx = pcx(p);
+        if (cx == 0 || slot_bounce(p)) continue;
+        if (cx > 0) {
+            uint32_t L = __shfl_up_sync(kFull, hi[p], 1);  // the left lane's h3 in the high half
+            if (lane == 0) L = (uint32_t)edge[p] << 16;
+            const uint32_t l2 = __byte_perm(L, lo[p], 0x5432), h2 = __byte_perm(lo[p], hi[p], 0x5432);
+            lo[p] = l2;
+            hi[p] = h2;
+        } else {
+            uint32_t R = __shfl_down_sync(kFull, lo[p], 1);  // the right lane's h0 in the low half
+            if (!right_by_shfl) R = (uint32_t)edge[p];
+            const uint32_t l2 = __byte_perm(lo[p], hi[p], 0x5432), h2 = __byte_perm(hi[p], R, 0x5432);
+            lo[p] = l2;
+            hi[p] = h2;
+        }
+    }
+    // collide pair (0, 1), then pair (2, 3); the results replace the inputs
+    NodeParams<F2> p2;
+    p2.omega = F2(np.omega);
+    p2.omega_m = F2(np.omega_m);
+    p2.rho0 = F2(np.rho0);
+    p2.variant = np.variant;
+    p2.collision = np.collision;
+    p2.mag_collision = np.mag_collision;
+    auto collide_pair = [&](uint32_t (&w)[kPlanes]) {
+        F2 f[9], g[10];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            __half2 h;
+            memcpy(&h, &w[i], 4);
+            f[i] = F2(__half22float2(h));
+        }
+#pragma unroll
+        for (int q = 0; q < 10; ++q) {
+            __half2 h;
+            memcpy(&h, &w[9 + q], 4);
+            g[q] = F2(__half22float2(h));
+        }
+        collide_impl<false, F2, true>(f, g, p2, nullptr);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const __half2 h = __floats2half2_rn(f[i].v.x, f[i].v.y);
+            memcpy(&w[i], &h, 4);
+        }
+#pragma unroll
+        for (int q = 0; q < 10; ++q) {
+            const __half2 h = __floats2half2_rn(g[q].v.x, g[q].v.y);
+            memcpy(&w[9 + q], &h, 4);
+        }
+    };
+    collide_pair(lo);
+    collide_pair(hi);
+    // write back: slot p's cells receive f*_opp(p) of the nodes that read them
+    __half* wbuf;
+    asm volatile("mov.b64 %0, %1;" : "=l"(wbuf) : "l"(buf));
+    auto store4 = [&](__half* dst, uint32_t a, uint32_t b, bool skip_first, bool skip_last) {
+        if (!skip_first && !skip_last) {
+            *reinterpret_cast<uint2*>(dst) = make_uint2(a, b);
+            return;
+        }
+        unsigned short* d = reinterpret_cast<unsigned short*>(dst);
+        if (!skip_first) d[0] = (unsigned short)(a & 0xffffu);
+        d[1] = (unsigned short)(a >> 16);
+        d[2] = (unsigned short)(b & 0xffffu);
+        if (!skip_last) d[3] = (unsigned short)(b >> 16);
+    };
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        const int cx = pcx(p);
+        const bool bounce = slot_bounce(p);
+        __half* row = wbuf + slot_off(p);
+        const int q = popp(p);
+        if (cx == 0 || bounce) {
+            if (active) store4(row + x0, lo[q], hi[q], false, false);
+        } else if (cx > 0) {
+            // slot read x - 1: node x0+k owns cell x0+k-1 -> (w1, w2, w3, right lane's w0)
+            const uint32_t N = __shfl_down_sync(kFull, lo[q], 1);
+            const uint32_t a = __byte_perm(lo[q], hi[q], 0x5432), b = __byte_perm(hi[q], N, 0x5432);
+            if (active) store4(row + x0, a, b, false, !right_by_shfl);
+            if (active && lane == 0) row[xl] = __ushort_as_half((unsigned short)(lo[q] & 0xffffu));
+        } else {
+            // slot read x + 1: node x0+k owns cell x0+k+1 -> (left lane's w3, w0, w1, w2)
+            const uint32_t P = __shfl_up_sync(kFull, hi[q], 1);
+            const uint32_t a = __byte_perm(P, lo[q], 0x5432), b = __byte_perm(lo[q], hi[q], 0x5432);
+            if (active) store4(row + x0, a, b, lane == 0, false);
+            if (active && !right_by_shfl) row[xr] = __ushort_as_half((unsigned short)(hi[q] >> 16));
+        }
+    }
+}
+
 // Phase B for one thread: V consecutive nodes of row y, all accesses local.
 template <int PREC, int V, typename Off = long long>
 __device__ __forceinline__ void aa_row_b(typename Prec<PREC>::S* buf, int nx, long long pitch,
