@@ -357,7 +357,7 @@ mhd_status mhd_set_fields(mhd_lattice* l, const double* ux, const double* uy, co
     {
         int flags = 0;
         CK(cudaMemsetAsync(l->flags_d, 0, sizeof(int), l->stream), "clear input flags");
-        const long long blocks = std::max(1LL, std::min((n + 255) / 256, 152LL * 8));
+        const long long blocks = std::max(1LL, std::min((n + 255) / 256, 8LL * mhd::device_sms()));
         check_fields_kernel<<<(unsigned)blocks, 256, 0, l->stream>>>(d[0], d[1], d[2], d[3], rho ? d[4] : nullptr, n,
                                                                       l->flags_d);
         CK(cudaGetLastError(), "input check kernel");

@@ -327,7 +327,7 @@ __global__ void stats_finish(const double* __restrict__ P, int nblocks, long lon
 
 cudaError_t launch_filter(const Layout& L, int prec, const void* prev, int r, float* out, cudaStream_t st) {
     const long long nc = (long long)(L.nx / r) * (L.ny / r);
-    const int blocks = (int)std::min<long long>((nc + 255) / 256, 152 * 16);
+    const int blocks = (int)std::min<long long>((nc + 255) / 256, 16LL * device_sms());
     switch (prec) {
     case 0: filter_kernel<0><<<blocks, 256, 0, st>>>(prev, L, r, out); break;
     case 1: filter_kernel<1><<<blocks, 256, 0, st>>>(prev, L, r, out); break;
@@ -340,7 +340,7 @@ cudaError_t launch_filter(const Layout& L, int prec, const void* prev, int r, fl
 cudaError_t launch_sgs(const Layout& L, int prec, const void* prev, int r, double tau_coarse, float* out,
                        cudaStream_t st) {
     const long long nc = (long long)(L.nx / r) * (L.ny / r);
-    const int blocks = (int)std::min<long long>((nc + 255) / 256, 152 * 16);
+    const int blocks = (int)std::min<long long>((nc + 255) / 256, 16LL * device_sms());
     const double inv = 1.0 / (1.0 - 1.0 / tau_coarse);
     switch (prec) {
     case 0: sgs_kernel<0><<<blocks, 256, 0, st>>>(prev, L, r, inv, out); break;
@@ -360,7 +360,7 @@ cudaError_t launch_features(const float* st_, int nx, int ny, float rho0, float*
 cudaError_t launch_targets(const float* sT, const float* sT1, int nx, int ny, double rho0, double omega,
                            float* out, cudaStream_t st) {
     const long long n = (long long)nx * ny;
-    const int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 16);
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 16LL * device_sms());
     targets_kernel<<<blocks, 256, 0, st>>>(sT, sT1, nx, ny, rho0, omega, out);
     return cudaGetLastError();
 }
@@ -371,7 +371,7 @@ cudaError_t launch_targets(const float* sT, const float* sT1, int nx, int ny, do
 
 cudaError_t launch_gather_batch(const float* X, const float* T, const int* idx, int nreal, int rows,
                                 const float* prm, const MlpDev& d, cudaStream_t st) {
-    const int blocks = std::max(1, std::min((rows + 255) / 256, 152 * 8));
+    const int blocks = std::max(1, std::min((rows + 255) / 256, 8 * device_sms()));
     gather_batch<<<blocks, 256, 0, st>>>(X, T, idx, nreal, rows, prm, d.xb, d.tb);
     return cudaGetLastError();
 }
@@ -396,11 +396,11 @@ __global__ void scale_outputs(const float* __restrict__ Y, int nreal, const floa
 }
 
 cudaError_t launch_mlp_predict(const MlpDev& d, int rows, int nreal, const float* prm, float* Yraw, cudaStream_t st) {
-    const int fwd_blocks = std::max(1, std::min((rows / 16 + 7) / 8, 152 * 8));
+    const int fwd_blocks = std::max(1, std::min((rows / 16 + 7) / 8, 8 * device_sms()));
     mlp_fwd<kInPad, kHid, true><<<fwd_blocks, 256, 0, st>>>(d.xb, d.Wt1, d.b1, rows, d.Z1, d.H1);
     mlp_fwd<kHid, kHid, true><<<fwd_blocks, 256, 0, st>>>(d.H1, d.Wt2, d.b2, rows, d.Z2, d.H2);
     mlp_fwd<kHid, kOutPad, false><<<fwd_blocks, 256, 0, st>>>(d.H2, d.Wt3, d.b3, rows, d.Y, nullptr);
-    scale_outputs<<<std::max(1, std::min((nreal + 255) / 256, 1216)), 256, 0, st>>>(d.Y, nreal, prm, Yraw);
+    scale_outputs<<<std::max(1, std::min((nreal + 255) / 256, 8 * device_sms())), 256, 0, st>>>(d.Y, nreal, prm, Yraw);
     return cudaGetLastError();
 }
 

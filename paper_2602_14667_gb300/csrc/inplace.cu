@@ -155,7 +155,7 @@ cudaError_t launch_aa_step(const StepLaunch& s, int phase, cudaStream_t st) {
 
 cudaError_t launch_aa_unstream(const Layout& L, int prec, void* buf, int wall_y, cudaStream_t st) {
     long long blocks = ((long long)L.nx * L.ny + 255) / 256;
-    blocks = std::max(1LL, std::min(blocks, 152LL * 16));
+    blocks = std::max(1LL, std::min(blocks, 16LL * device_sms()));
     switch (prec) {
     case 0: aa_unstream_kernel<0><<<(unsigned)blocks, 256, 0, st>>>(L, buf, wall_y); break;
     case 1: aa_unstream_kernel<1><<<(unsigned)blocks, 256, 0, st>>>(L, buf, wall_y); break;

@@ -76,6 +76,10 @@ cudaError_t launch_diag(const DiagLaunch& d, double* partials, int capacity, dou
 
 Layout make_layout(int nx, int ny, int prec);
 
+// SM count of the current device (queried once per device; 152 on GB300 if
+// the query fails).  Grid-stride launchers size their grids with it.
+int device_sms();
+
 // message returned by mhd_last_error() in the calling thread
 void set_last_error(const std::string& msg);
 

@@ -148,21 +148,26 @@ __device__ __forceinline__ void encode_d(double v, double& s) { s = v; }
 __device__ __forceinline__ void encode_d(double v, float& s) { s = __double2float_rn(v); }
 __device__ __forceinline__ void encode_d(double v, __half& s) { s = __double2half(v * 4096.0); }
 
+// The initial equilibrium and the moments read back are evaluated in the
+// compute type of the storage (FP64 for FP64, FP32 for FP32 and FP16S), as
+// the step evaluates its collision: on GB300 FP64 arithmetic would make
+// these memory-bound conversions bound by the FP64 units instead.
 template <int PREC>
 __global__ void init_kernel(Layout L, void* buf, const double* rho, const double* ux,
                             const double* uy, const double* bx, const double* by, double rho0,
                             int variant) {
     using S = typename Prec<PREC>::S;
+    using C = typename Prec<PREC>::C;
     const long long n = (long long)L.nx * L.ny;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(k / L.nx), x = (int)(k % L.nx);
-        double f[9], g[10];
-        equilibrium<double>(rho ? rho[k] : rho0, ux[k], uy[k], bx[k], by[k], rho0, variant, f, g);
+        C f[9], g[10];
+        equilibrium<C>(C(rho ? rho[k] : rho0), C(ux[k]), C(uy[k]), C(bx[k]), C(by[k]), C(rho0), variant, f, g);
         S* b = static_cast<S*>(buf);
         const long long o = (long long)y * L.pitch + x;
-        for (int i = 0; i < 9; ++i) encode_d(f[i], b[(long long)i * L.plane + o]);
-        for (int q = 0; q < 10; ++q) encode_d(g[q], b[(long long)(9 + q) * L.plane + o]);
+        for (int i = 0; i < 9; ++i) encode(f[i], b[(long long)i * L.plane + o]);
+        for (int q = 0; q < 10; ++q) encode(g[q], b[(long long)(9 + q) * L.plane + o]);
     }
 }
 
@@ -170,17 +175,18 @@ template <int PREC>
 __global__ void fields_kernel(Layout L, const void* buf, double rho0, double* rho, double* ux,
                               double* uy, double* bx, double* by) {
     using S = typename Prec<PREC>::S;
+    using C = typename Prec<PREC>::C;
     const long long n = (long long)L.nx * L.ny;
     const S* b = static_cast<const S*>(buf);
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(k / L.nx), x = (int)(k % L.nx);
         const long long o = (long long)y * L.pitch + x;
-        double f[9], g[10];
-        for (int i = 0; i < 9; ++i) f[i] = (double)decode(b[(long long)i * L.plane + o]);
-        for (int q = 0; q < 10; ++q) g[q] = (double)decode(b[(long long)(9 + q) * L.plane + o]);
-        const Moments<double> m = moments<double>(f, g, rho0);
-        if (rho) rho[k] = m.rho;
+        C f[9], g[10];
+        for (int i = 0; i < 9; ++i) f[i] = decode(b[(long long)i * L.plane + o]);
+        for (int q = 0; q < 10; ++q) g[q] = decode(b[(long long)(9 + q) * L.plane + o]);
+        const Moments<C> m = moments<C>(f, g, C(rho0));
+        if (rho) rho[k] = rho0 + (double)m.drho;  // the deviation keeps its relative precision
         if (ux) ux[k] = m.ux;
         if (uy) uy[k] = m.uy;
         if (bx) bx[k] = m.bx;
@@ -231,9 +237,23 @@ __global__ void unstream_kernel(Layout L, void* buf, const float* F) {
     }
 }
 
+int device_sms() {
+    static int cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!cached[dev]) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
+        cached[dev] = sms;
+    }
+    return cached[dev];
+}
+
+// grid-stride launches: at most 16 blocks of 256 threads per SM
 static dim3 flat_grid(long long n) {
     long long b = (n + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
+    const long long cap = 16LL * device_sms();
+    if (b > cap) b = cap;
     if (b < 1) b = 1;
     return dim3((unsigned)b);
 }

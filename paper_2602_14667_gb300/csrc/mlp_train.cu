@@ -468,7 +468,7 @@ cudaError_t launch_epoch_permutation(int* idx, long long n, unsigned long long s
                                      cudaStream_t st) {
     int h = 1;
     while ((1LL << (2 * h)) < n) ++h;
-    const long long blocks = std::max(1LL, std::min((n + 255) / 256, 152LL * 16));
+    const long long blocks = std::max(1LL, std::min((n + 255) / 256, 16LL * device_sms()));
     epoch_permutation<<<(unsigned)blocks, 256, 0, st>>>(idx, n, h, seed, step);
     return cudaGetLastError();
 }
