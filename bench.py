@@ -599,7 +599,10 @@ def run_closure(args):
     same calibration (what it gains is not due to training), and the plain
     scheme on the finest grid whose run is predicted to take no more GPU
     time than the closure run (equal GPU time; its fields box-filtered onto
-    the 512^2 grid like the fine run's)."""
+    the 512^2 grid like the fine run's).  And the closure with its MLP
+    evaluated on every 4th and every 8th step only (the stored correction
+    reused between), each calibrated, judged, timed and compared with its
+    own equal-time plain grid."""
     import torch
 
     from paper_2602_14667_gb300 import closure_study as cs
@@ -608,7 +611,7 @@ def run_closure(args):
                          sample_stride=1500, samples_per_seed=4,
                          eval_coarse_steps=(500, 1000, 1500, 2000), epochs=20, batch=8192)
     t0 = time.perf_counter()
-    res = cs.run(cfg, control=True, equal_time=True)
+    res = cs.run(cfg, control=True, equal_time=True, intervals=(4, 8))
     wall = time.perf_counter() - t0
     steps = cfg.eval_coarse_steps
     last = steps[-1]
@@ -646,6 +649,13 @@ def run_closure(args):
                               "plain_grid_gpu_s": None if fine is None else fine["gpu_s"],
                               "errors": {"closure_512": arm(res.get("closure")), "plain_512": arm(res["plain"]),
                                          "plain_grid": arm(fine), "untrained_512": arm(unt["run"])}},
+           "closure_interval": {str(k): {"amplitude": v["amplitude"], "gpu_s": v["gpu_s"],
+                                         "cost_vs_plain_512": v["gpu_s"] / et["gpu_s"]["plain_coarse"],
+                                         "errors": arm(v["run"]),
+                                         "equal_time_plain_grid": None if v["plain_fine"] is None
+                                         else v["plain_fine"]["n"],
+                                         "equal_time_plain_errors": arm(v["plain_fine"])}
+                                 for k, v in res["intervals"].items()},
            "training": training_rate(res),
            "wall_s": wall}
     print(json.dumps(out), flush=True)

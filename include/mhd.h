@@ -396,6 +396,18 @@ mhd_status mhd_set_closure(mhd_lattice* l, const mhd_mlp* mlp);
 typedef enum { MHD_CLOSURE_WARP_MMA = 0, MHD_CLOSURE_TCGEN05 = 1 } mhd_closure_kernel;
 mhd_status mhd_set_closure_kernel(mhd_lattice* l, int kind);
 mhd_status mhd_get_closure_kernel(const mhd_lattice* l, int* kind);
+/* Refresh interval of the closure (an option of this implementation; the
+ * closure itself is not in the paper): the features and the MLP are
+ * evaluated on every k-th step only -- the steps whose count since the last
+ * change of the state, of the closure or of k is a multiple of k -- and the
+ * correction they give each node is stored (3 x nx*ny FP32, allocated by
+ * this call) and added again on the k - 1 steps between, which then cost a
+ * plain step plus 12 bytes per node.  k = 1 (the default) evaluates the MLP
+ * on every step.  k must divide 64 (the steps of a captured CUDA graph);
+ * k > 1 needs an FP32 periodic two-buffer lattice with nx % 4 == 0
+ * (MHD_EINVAL otherwise).  Takes effect on the lattice's next step. */
+mhd_status mhd_set_closure_interval(mhd_lattice* l, int k);
+mhd_status mhd_get_closure_interval(const mhd_lattice* l, int* k);
 
 #ifdef __cplusplus
 }

@@ -19,7 +19,8 @@ plain reference for the GPU kernels (no shared code with them):
                   forward and backward in FP64, optional BF16 rounding of the
                   weights and of each layer's input (as the tensor-core
                   kernels do), Adam;
-* closure_run  -- coarse steps with the correction applied.
+* closure_run  -- coarse steps with the correction applied (evaluated on
+                  every step, or on every k-th step and reused between).
 Arrays: f (9, ny, nx), g (5, 2, ny, nx) as in oracle/__init__.py.
 """
 from __future__ import annotations
@@ -262,7 +263,17 @@ def closure_step(p: Params, f, g, mlp: MLP | None, bf16_like_gpu: bool = False):
     return stream(p, fs, gs)
 
 
-def closure_run(p: Params, f, g, steps: int, mlp: MLP | None, bf16_like_gpu: bool = False):
-    for _ in range(steps):
-        f, g = closure_step(p, f, g, mlp, bf16_like_gpu)
+def closure_run(p: Params, f, g, steps: int, mlp: MLP | None, bf16_like_gpu: bool = False,
+                interval: int = 1):
+    """steps coarse steps with the correction.  interval k > 1: the
+    correction is evaluated from the state on steps 0, k, 2k, ... and the
+    same per-node values are applied on the k - 1 steps after each."""
+    da = None
+    for s in range(steps):
+        if mlp is not None and s % interval == 0:
+            X, _ = features(p, f, g)
+            da, _ = mlp.forward(X, bf16_like_gpu)
+            da = da.reshape(p.ny, p.nx, 3)
+        fs, gs = collide_da(p, f, g, da)
+        f, g = stream(p, fs, gs)
     return f, g

@@ -98,6 +98,8 @@ _SIGNATURES = {
     "mhd_set_precollision_state": [_P, _P],
     "mhd_set_closure_kernel": [_P, ctypes.c_int],
     "mhd_get_closure_kernel": [_P, ctypes.POINTER(ctypes.c_int)],
+    "mhd_set_closure_interval": [_P, ctypes.c_int],
+    "mhd_get_closure_interval": [_P, ctypes.POINTER(ctypes.c_int)],
     "mhd_closure_sgs_targets": [_P, ctypes.c_int, ctypes.c_double, _P],
     "mhd_set_closure": [_P, _P],
     "mhd_get_state": [_P, _P, ctypes.c_size_t],
@@ -467,6 +469,18 @@ def set_closure_kernel(lattice: "Lattice", kind: int):
 def get_closure_kernel(lattice: "Lattice") -> int:
     k = ctypes.c_int()
     check(lib().mhd_get_closure_kernel(lattice.handle, ctypes.byref(k)), "mhd_get_closure_kernel")
+    return k.value
+
+
+def set_closure_interval(lattice: "Lattice", k: int):
+    """Evaluate the closure MLP on every k-th step and reuse its stored
+    correction on the steps between (mhd_set_closure_interval)."""
+    check(lib().mhd_set_closure_interval(lattice.handle, int(k)), "mhd_set_closure_interval")
+
+
+def get_closure_interval(lattice: "Lattice") -> int:
+    k = ctypes.c_int()
+    check(lib().mhd_get_closure_interval(lattice.handle, ctypes.byref(k)), "mhd_get_closure_interval")
     return k.value
 
 

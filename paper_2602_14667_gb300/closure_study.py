@@ -218,10 +218,11 @@ def reference(cfg: StudyConfig, seed: int):
     return refs, fields0
 
 
-def coarse_run(cfg: StudyConfig, fields0, refs, mlp=None, timing=False):
-    """Coarse run (closure if mlp) started, like the fine run, from the t = 0
-    fields with equilibrium populations; (spectrum, current) errors at each
-    checkpoint, and the GPU time per coarse step if timing."""
+def coarse_run(cfg: StudyConfig, fields0, refs, mlp=None, timing=False, interval=1):
+    """Coarse run (closure if mlp, its MLP evaluated on every interval-th
+    step) started, like the fine run, from the t = 0 fields with equilibrium
+    populations; (spectrum, current) errors at each checkpoint, and the GPU
+    time per coarse step if timing."""
     import torch
     nc = cfg.n_coarse
     tau_c = coarse_tau(cfg.tau_fine, cfg.factor)
@@ -229,6 +230,7 @@ def coarse_run(cfg: StudyConfig, fields0, refs, mlp=None, timing=False):
     with Lattice(nc, nc, tau_c, tau_c, precision="fp32") as c:
         if mlp is not None:
             _abi.set_closure(c, mlp)
+            _abi.set_closure_interval(c, interval)
         c.set_fields(*fields0)
         done = 0
         for k in cfg.eval_coarse_steps:
@@ -249,8 +251,10 @@ def plain_run_at(cfg: StudyConfig, n: int, seed: int, refs, stream=None):
     """Plain RR run of the same flow on an n x n lattice (acoustic scaling:
     n / n_coarse steps per coarse step, tau = 1/2 + (tau_fine - 1/2) n / n_fine),
     started from the t = 0 fields sampled at its nodes; its fields are
-    box-filtered onto the coarse grid and judged like the coarse runs.
-    Returns the errors per checkpoint and the GPU seconds of its steps."""
+    box-filtered onto the coarse grid and judged like the coarse runs.  A
+    checkpoint falls on the nearest whole step (at most half a step of the
+    n-grid off).  Returns the errors per checkpoint and the GPU seconds of
+    its steps."""
     import torch
 
     import mhd_inputs
@@ -261,7 +265,7 @@ def plain_run_at(cfg: StudyConfig, n: int, seed: int, refs, stream=None):
         lat.set_fields(*mhd_inputs.random_spectrum(n, n, seed, cfg.rms, cfg.rms))
         done = 0
         for k in cfg.eval_coarse_steps:
-            steps = k * n // nc - done
+            steps = (2 * k * n + nc) // (2 * nc) - done   # round(k n / nc)
             done += steps
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -280,7 +284,7 @@ def plain_run_at(cfg: StudyConfig, n: int, seed: int, refs, stream=None):
     return res
 
 
-def coarse_gpu_seconds(cfg: StudyConfig, fields0, mlp=None, stream=None):
+def coarse_gpu_seconds(cfg: StudyConfig, fields0, mlp=None, stream=None, interval=1):
     """GPU seconds of the coarse run's steps up to the last checkpoint."""
     import torch
     nc = cfg.n_coarse
@@ -290,6 +294,7 @@ def coarse_gpu_seconds(cfg: StudyConfig, fields0, mlp=None, stream=None):
         if mlp is not None:
             _abi.set_closure(c, mlp)
             c.autotune()          # the faster closure kernel; the state is kept
+            _abi.set_closure_interval(c, interval)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -299,14 +304,14 @@ def coarse_gpu_seconds(cfg: StudyConfig, fields0, mlp=None, stream=None):
         return e0.elapsed_time(e1) * 1e-3
 
 
-def equal_time_grid(cfg: StudyConfig, t_closure: float, t_plain: float) -> int:
-    """The finest n (a multiple of 128, so that every checkpoint is a whole
-    number of its steps) at which a plain run to the last checkpoint is
-    predicted to take at most the closure run's GPU time: acoustic scaling
-    makes the cost grow as n^3 (n^2 nodes, n steps per unit time)."""
+def equal_time_grid(cfg: StudyConfig, t_closure: float, t_plain: float, step: int = 32) -> int:
+    """The finest n (a multiple of `step`) at which a plain run to the last
+    checkpoint is predicted to take at most the closure run's GPU time:
+    acoustic scaling makes the cost grow as n^3 (n^2 nodes, n steps per unit
+    time)."""
     n = cfg.n_coarse
-    while (n + 128) ** 3 / cfg.n_coarse ** 3 * t_plain <= t_closure:
-        n += 128
+    while (n + step) ** 3 / cfg.n_coarse ** 3 * t_plain <= t_closure:
+        n += step
     return n
 
 
@@ -320,7 +325,7 @@ def _score(res, cfg):
 CALIBRATION_GRID = (-4.0, -3.0, -2.0, -1.5, -1.0, -0.5, 0.0, 0.5, 1.0)
 
 
-def calibrate(cfg: StudyConfig, mlp, seed=None):
+def calibrate(cfg: StudyConfig, mlp, seed=None, interval=1):
     """A posteriori amplitude of the learned stress: scale out_scale by each c
     of CALIBRATION_GRID, run the coarse closure on a TRAINING seed and keep
     the c with the smallest summed spectrum + current errors (c = 0 is the
@@ -333,7 +338,7 @@ def calibrate(cfg: StudyConfig, mlp, seed=None):
         p = base.copy()
         p[48:51] *= c
         mlp.set_params(p)
-        scores[c] = _score(coarse_run(cfg, fields0, refs, None if c == 0.0 else mlp), cfg)
+        scores[c] = _score(coarse_run(cfg, fields0, refs, None if c == 0.0 else mlp, interval=interval), cfg)
     best = min(scores, key=scores.get)
     p = base.copy()
     p[48:51] *= best
@@ -352,7 +357,8 @@ def evaluate(cfg: StudyConfig, mlp=None, seed=None):
     return out
 
 
-def run(cfg: StudyConfig | None = None, control: bool = False, equal_time: bool = False) -> dict:
+def run(cfg: StudyConfig | None = None, control: bool = False, equal_time: bool = False,
+        intervals=()) -> dict:
     """Data from the training seeds, GPU training, a posteriori calibration
     on the first training seed, evaluation on the held-out seed.
 
@@ -360,7 +366,10 @@ def run(cfg: StudyConfig | None = None, control: bool = False, equal_time: bool 
     seed and normalisation (res["untrained"]): whatever it gains is not due
     to training.  equal_time: also time the coarse closure and plain runs on
     the GPU and run the plain scheme on the finest grid that is predicted to
-    cost no more than the closure run (res["equal_time"])."""
+    cost no more than the closure run (res["equal_time"]).  intervals: for
+    each k, the closure with its MLP evaluated on every k-th step, its
+    amplitude calibrated anew, judged and timed the same way, with its own
+    equal-time plain grid (res["intervals"][k])."""
     import torch
     cfg = cfg or StudyConfig()
     X, T = generate_data(cfg)
@@ -369,6 +378,7 @@ def run(cfg: StudyConfig | None = None, control: bool = False, equal_time: bool 
     mlp = train(cfg, X, T)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
+    raw = mlp.get_params()        # before calibration scales the output
     c, scores = calibrate(cfg, mlp)
     res = evaluate(cfg, mlp if c != 0.0 else None)
     res.update(samples=int(X.shape[0]), train_loss=mlp.last_loss, amplitude=c,
@@ -380,14 +390,30 @@ def run(cfg: StudyConfig | None = None, control: bool = False, equal_time: bool 
         res["untrained"] = {"amplitude": cu, "calibration_scores": su,
                             "run": coarse_run(cfg, fields0, refs, ctl if cu != 0.0 else None)}
         ctl.close()
-    if equal_time:
+    if equal_time or intervals:
         refs, fields0 = reference(cfg, cfg.eval_seed)
         stream = torch.cuda.Stream()
         t_plain = coarse_gpu_seconds(cfg, fields0, None, stream)
-        t_closure = coarse_gpu_seconds(cfg, fields0, mlp if c != 0.0 else None, stream)
-        n = equal_time_grid(cfg, t_closure, t_plain)
-        res["equal_time"] = {"gpu_s": {"plain_coarse": t_plain, "closure_coarse": t_closure},
-                             "plain_fine": plain_run_at(cfg, n, cfg.eval_seed, refs, stream) if n > cfg.n_coarse
-                             else None}
+        plain_at = {}
+
+        def equal_time_arm(t_closure):
+            n = equal_time_grid(cfg, t_closure, t_plain)
+            if n > cfg.n_coarse and n not in plain_at:
+                plain_at[n] = plain_run_at(cfg, n, cfg.eval_seed, refs, stream)
+            return plain_at.get(n)
+
+        if equal_time:
+            t_closure = coarse_gpu_seconds(cfg, fields0, mlp if c != 0.0 else None, stream)
+            res["equal_time"] = {"gpu_s": {"plain_coarse": t_plain, "closure_coarse": t_closure},
+                                 "plain_fine": equal_time_arm(t_closure)}
+        res["intervals"] = {}
+        for k in intervals:
+            mlp.set_params(raw)
+            ck, sk = calibrate(cfg, mlp, interval=k)
+            net = mlp if ck != 0.0 else None
+            t_k = coarse_gpu_seconds(cfg, fields0, net, stream, interval=k)
+            res["intervals"][k] = {"amplitude": ck, "calibration_scores": sk,
+                                   "run": coarse_run(cfg, fields0, refs, net, interval=k),
+                                   "gpu_s": t_k, "plain_fine": equal_time_arm(t_k)}
     mlp.close()
     return res

@@ -98,6 +98,12 @@ struct mhd_lattice {
     void* closure_buf = nullptr;  // lattice-owned copy of the closure's inference parameters
     int closure_kind = MHD_CLOSURE_WARP_MMA;
     mhd::ClosureParamsDev closure{};
+    // the MLP runs on every closure_interval-th step (counted by
+    // closure_count since the last change of state or closure) and its
+    // output, kept in da (3 planes of nx*ny floats), serves the steps between
+    int closure_interval = 1;
+    long long closure_count = 0;
+    float* da = nullptr;
 
     long long n() const { return (long long)nx * ny; }
     size_t buf_bytes() const { return (size_t)mhd::kStatePlanes * L.plane * L.esize; }
@@ -133,11 +139,18 @@ mhd::StepLaunch step_launch(const mhd_lattice* l, int from) {
     return s;
 }
 
-cudaError_t launch_lattice_step(const mhd_lattice* l, int from, cudaStream_t st) {
+// One step from buffer `from`.  A closure lattice evaluates its MLP when
+// `count` (its closure step count) is a multiple of the interval, and
+// otherwise reuses the stored correction.
+cudaError_t launch_lattice_step(const mhd_lattice* l, int from, cudaStream_t st, long long count = 0) {
     const mhd::StepLaunch s = step_launch(l, from);
-    if (l->closure_buf)
-        return l->closure_kind == MHD_CLOSURE_TCGEN05 ? mhd::launch_step_closure_tc(s, l->closure, st)
-                                                      : mhd::launch_step_closure(s, l->closure, st);
+    if (l->closure_buf) {
+        if (l->closure_interval > 1 && count % l->closure_interval != 0) return mhd::launch_step_da_cached(s, l->da, st);
+        mhd::ClosureParamsDev cp = l->closure;
+        cp.da_out = l->closure_interval > 1 ? l->da : nullptr;
+        return l->closure_kind == MHD_CLOSURE_TCGEN05 ? mhd::launch_step_closure_tc(s, cp, st)
+                                                      : mhd::launch_step_closure(s, cp, st);
+    }
     return mhd::launch_step(s, st);
 }
 
@@ -331,6 +344,7 @@ mhd_status mhd_destroy(mhd_lattice* l) {
         if (b) cudaFree(b);
     if (l->io) cudaFree(l->io);
     if (l->closure_buf) cudaFree(l->closure_buf);
+    if (l->da) cudaFree(l->da);
     if (l->partials) cudaFree(l->partials);
     if (l->totals_d) cudaFree(l->totals_d);
     if (l->totals_h) cudaFreeHost(l->totals_h);
@@ -373,6 +387,7 @@ mhd_status mhd_set_fields(mhd_lattice* l, const double* ux, const double* uy, co
     l->step = 0;
     l->fields_set = true;
     l->prev_valid = false;
+    l->closure_count = 0;  // the next closure step evaluates the MLP
     l->state_is_eq = true;
     l->aa_streamed = false;
     return MHD_OK;
@@ -385,8 +400,10 @@ static mhd_status capture_graph(mhd_lattice* l, int from) {
     CK(cudaStreamBeginCapture(l->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
     int c = from;
     cudaError_t le = cudaSuccess;
+    // (a closure lattice with an interval > 1 captures only from a step
+    // count that is a multiple of the interval, which divides kGraphSteps)
     for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k) {
-        le = l->in_place ? launch_inplace_step(l, l->buf[0], c, l->cap) : launch_lattice_step(l, c, l->cap);
+        le = l->in_place ? launch_inplace_step(l, l->buf[0], c, l->cap) : launch_lattice_step(l, c, l->cap, k);
         c ^= 1;
     }
     cudaError_t ee = cudaStreamEndCapture(l->cap, &g);
@@ -427,7 +444,20 @@ mhd_status mhd_advance(mhd_lattice* l, long long nsteps) {
         l->state_is_eq = false;
         return MHD_OK;
     }
+    auto single = [&]() -> mhd_status {
+        CK(launch_lattice_step(l, l->cur, l->stream, l->closure_count), "step launch");
+        l->cur ^= 1;
+        --nsteps;
+        ++l->step;
+        ++l->closure_count;
+        return MHD_OK;
+    };
     while (nsteps >= kGraphSteps) {
+        if (l->closure_buf && l->closure_count % l->closure_interval != 0) {
+            mhd_status s = single();  // step up to the next evaluation of the MLP first
+            if (s != MHD_OK) return s;
+            continue;
+        }
         if (!l->graph[l->cur]) {
             mhd_status s = capture_graph(l, l->cur);
             if (s != MHD_OK) return s;
@@ -435,12 +465,11 @@ mhd_status mhd_advance(mhd_lattice* l, long long nsteps) {
         CK(cudaGraphLaunch(l->graph[l->cur], l->stream), "graph launch");
         nsteps -= kGraphSteps;
         l->step += kGraphSteps;
+        l->closure_count += kGraphSteps;
     }
     while (nsteps > 0) {
-        CK(launch_lattice_step(l, l->cur, l->stream), "step launch");
-        l->cur ^= 1;
-        --nsteps;
-        ++l->step;
+        mhd_status s = single();
+        if (s != MHD_OK) return s;
     }
     l->prev_valid = true;
     l->state_is_eq = false;
@@ -565,6 +594,7 @@ mhd_status mhd_set_populations(mhd_lattice* l, const double* f, const double* g)
     }
     l->fields_set = true;
     l->prev_valid = false;
+    l->closure_count = 0;  // the next closure step evaluates the MLP
     l->state_is_eq = false;
     l->aa_streamed = false;
     return MHD_OK;
@@ -618,6 +648,29 @@ mhd_status mhd_set_closure(mhd_lattice* l, const mhd_mlp* mlp) {
         CK(cudaMemcpyAsync(const_cast<void*>(q.d), q.s, q.b, cudaMemcpyDeviceToDevice, l->stream), "copy closure");
     CK(cudaStreamSynchronize(l->stream), "mhd_set_closure");
     drop_graphs(l);
+    l->closure_count = 0;
+    return MHD_OK;
+}
+
+mhd_status mhd_set_closure_interval(mhd_lattice* l, int k) {
+    if (!l) return fail(MHD_EINVAL, "lattice is NULL");
+    if (k < 1 || k > kGraphSteps || kGraphSteps % k != 0)
+        return fail(MHD_EINVAL, "the closure interval must divide 64");
+    if (k > 1 && (l->nx % 4 || l->p.precision != MHD_FP32 || l->p.bc_x != MHD_PERIODIC ||
+                  l->p.bc_y != MHD_PERIODIC || l->in_place))
+        return fail(MHD_EINVAL, "a closure interval > 1 needs an FP32 periodic two-buffer lattice with nx % 4 == 0");
+    CK(cudaSetDevice(l->dev), "cudaSetDevice");
+    CK(cudaStreamSynchronize(l->stream), "mhd_set_closure_interval");
+    if (k > 1 && !l->da) CK(cudaMalloc(&l->da, sizeof(float) * 3 * (size_t)l->n()), "cudaMalloc(closure correction)");
+    if (k != l->closure_interval) drop_graphs(l);
+    l->closure_interval = k;
+    l->closure_count = 0;
+    return MHD_OK;
+}
+
+mhd_status mhd_get_closure_interval(const mhd_lattice* l, int* k) {
+    if (!l || !k) return fail(MHD_EINVAL, "NULL argument");
+    *k = l->closure_interval;
     return MHD_OK;
 }
 
@@ -629,6 +682,7 @@ mhd_status mhd_set_closure_kernel(mhd_lattice* l, int kind) {
         CK(cudaStreamSynchronize(l->stream), "mhd_set_closure_kernel");
         drop_graphs(l);
         l->closure_kind = kind;
+        l->closure_count = 0;
     }
     return MHD_OK;
 }
@@ -675,6 +729,7 @@ mhd_status mhd_set_precollision_state(mhd_lattice* l, const float* state) {
     CK(cudaStreamSynchronize(l->stream), "mhd_set_precollision_state");
     l->fields_set = true;
     l->prev_valid = false;
+    l->closure_count = 0;  // the next closure step evaluates the MLP
     l->state_is_eq = false;
     l->aa_streamed = false;
     return MHD_OK;
@@ -761,6 +816,7 @@ mhd_status mhd_set_state(mhd_lattice* l, const void* host, size_t bytes) {
     CK(cudaStreamSynchronize(l->stream), "mhd_set_state");
     l->fields_set = true;
     l->prev_valid = false;
+    l->closure_count = 0;  // the next closure step evaluates the MLP
     l->state_is_eq = false;
     l->aa_streamed = false;
     return MHD_OK;

@@ -35,12 +35,19 @@ struct ClosureParamsDev {
     const __nv_bfloat16 *Wt1, *Wt2, *Wt3;
     const float *b1, *b2, *b3, *mean, *scale, *out_scale;
     int* err;  // set to 1 by the closure step if a tensor-core wait gave up
+    // if set, the closure step also stores each node's correction here (3
+    // planes of nx*ny floats: xx, xy, yy; node y*nx + x) for the steps that
+    // reuse it (launch_step_da_cached)
+    float* da_out = nullptr;
 };
 
 // The closure step: MLP on warp-level mma.sync fragments (kind 0) or on the
 // tcgen05 tensor cores with tensor-memory accumulators (kind 1).
 cudaError_t launch_step_closure(const StepLaunch& s, const ClosureParamsDev& cp, cudaStream_t st);
 cudaError_t launch_step_closure_tc(const StepLaunch& s, const ClosureParamsDev& cp, cudaStream_t st);
+// The fused step with a stored correction da (the layout of da_out) added to
+// a1^(2) before the recursion: the steps between two evaluations of the MLP.
+cudaError_t launch_step_da_cached(const StepLaunch& s, const float* da, cudaStream_t st);
 cudaError_t launch_filter(const Layout& L, int prec, const void* prev, int r, float* out, cudaStream_t st);
 cudaError_t launch_sgs(const Layout& L, int prec, const void* prev, int r, double tau_coarse, float* out,
                        cudaStream_t st);

@@ -241,6 +241,11 @@ __global__ void __launch_bounds__(kRWarps * 32, 2) step_closure_rows(const StepA
 #pragma unroll
                 for (int k = 0; k < 10; ++k) g[k] = cur[9 + k];
                 const float d3[3] = {da[lane][0], da[lane][1], da[lane][2]};
+                if (cp.da_out) {
+                    const Off nn = (Off)a.nx * (Off)a.ny, node = (Off)o * (Off)a.nx + xl;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) cp.da_out[(Off)k * nn + node] = d3[k];
+                }
                 collide_impl<true, float>(f, g, a.np, d3);
                 const Off off = (Off)o * (Off)a.pitch + xl, pl = (Off)a.plane;
 #pragma unroll
@@ -253,7 +258,83 @@ __global__ void __launch_bounds__(kRWarps * 32, 2) step_closure_rows(const StepA
     }
 }
 
+// The steps between two evaluations of the MLP: the fused step (the pull
+// gather of step_row, four nodes per lane) with each node's stored
+// correction added to a1^(2); 12 bytes per node more than the plain step.
+template <typename Off>
+__global__ void __launch_bounds__(512) step_da_cached(const StepArgs<float> a, const float* __restrict__ da,
+                                                      int nxb, int ntiles) {
+    constexpr int V = 4;
+    const Off nn = (Off)a.nx * (Off)a.ny;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int y = (t / nxb) * blockDim.y + threadIdx.y;
+        if (y >= a.ny) continue;  // whole warp
+        const int lane = threadIdx.x, xb = t % nxb;
+        float v[kPlanes][V];
+        const bool active = gather_row<1, V, false, Off>(static_cast<const float*>(a.src), a.nx, a.ny, a.pitch,
+                                                          a.plane, xb, y, lane, v);
+        if (!active) continue;
+        const int x0 = (xb * 32 + lane) * V;
+        float d[3][V];
+        const Off node = (Off)y * (Off)a.nx + x0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) VecIO<float, V>::load(da + (Off)k * nn + node, d[k]);
+        float* dst = static_cast<float*>(a.dst);
+        const Off o_0 = (Off)y * (Off)a.pitch + x0, pl = (Off)a.plane;
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            float f[9], g[10];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = v[i][k];
+#pragma unroll
+            for (int q = 0; q < 10; ++q) g[q] = v[9 + q][k];
+            const float d3[3] = {d[0][k], d[1][k], d[2][k]};
+            collide_impl<true, float>(f, g, a.np, d3);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) v[i][k] = f[i];
+#pragma unroll
+            for (int q = 0; q < 10; ++q) v[9 + q][k] = g[q];
+        }
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) VecIO<float, V>::store(dst + ((Off)p * pl + o_0), v[p]);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_step_da_cached(const StepLaunch& s, const float* da, cudaStream_t st) {
+    constexpr int V = 4;
+    if (s.prec != 1 || s.wall_x || s.wall_y || s.L.nx % V) return cudaErrorInvalidValue;
+    if (reinterpret_cast<uintptr_t>(da) % 16 || ((long long)s.L.nx * s.L.ny) % V) return cudaErrorInvalidValue;
+    StepArgs<float> a;
+    a.src = s.src;
+    a.dst = s.dst;
+    a.nx = s.L.nx;
+    a.ny = s.L.ny;
+    a.pitch = s.L.pitch;
+    a.plane = s.L.plane;
+    a.np.omega = (float)s.omega;
+    a.np.omega_m = (float)s.omega_m;
+    a.np.rho0 = (float)s.rho0;
+    a.np.variant = s.variant;
+    a.np.collision = s.collision;
+    a.np.mag_collision = s.mag_collision;
+    a.wall_x = 0;
+    a.wall_y = 0;
+    const int nxb = (s.L.nx + 32 * V - 1) / (32 * V), ntiles = nxb * s.L.ny;  // one-warp blocks, one row each
+    const bool small = (long long)kPlanes * s.L.plane < (1LL << 31);
+    auto kernel = small ? step_da_cached<int> : step_da_cached<long long>;
+    int per_sm = 0, sms = 0, dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32, 0);
+    if (e != cudaSuccess) return e;
+    // the residency of the plain FP32 step: about 4 KB of every plane in flight per SM
+    per_sm = std::min(std::max(1, per_sm), 4096 / (32 * V * (int)sizeof(float)));
+    const int blocks = std::max(1, std::min(ntiles, per_sm * sms));
+    kernel<<<blocks, dim3(32, 1), 0, st>>>(a, da, nxb, ntiles);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_step_closure(const StepLaunch& s, const ClosureParamsDev& cp, cudaStream_t st) {
     if (s.prec != 1 || s.wall_x || s.wall_y) return cudaErrorInvalidValue;

@@ -217,6 +217,11 @@ __global__ void __launch_bounds__(256, 2) step_closure_tc(const StepArgs<float> 
         if (inside) {
             const float da[3] = {(out[0] + sh.b3[0]) * sh.out_scale[0], (out[1] + sh.b3[1]) * sh.out_scale[1],
                                  (out[2] + sh.b3[2]) * sh.out_scale[2]};
+            if (cp.da_out) {
+                const long long nn = (long long)a.nx * a.ny, node = (long long)y * a.nx + x;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) cp.da_out[k * nn + node] = da[k];
+            }
             collide_impl<true, float>(f, g, a.np, da);
             const long long o = (long long)y * a.pitch + x;
 #pragma unroll

@@ -375,3 +375,52 @@ def test_closure_kernels_agree_and_autotune_picks_one():
     for k in ("ux", "uy", "bx", "by"):
         err = np.linalg.norm(out[0][k] - out[1][k]) / np.linalg.norm(out[0][k])
         assert err < 1e-5, (k, err)
+
+
+@KINDS
+def test_closure_interval_matches_oracle(orc, kind):
+    """Closure interval 4: the MLP runs on steps 0, 4 and 8 and its stored
+    correction is reused on the steps between (the cached-correction step
+    kernel).  After 9 steps the stored post-collision state must match the
+    oracle's run with the same interval (FP32 against FP64 over 9 steps),
+    which differs visibly from evaluating the MLP on every step."""
+    from oracle import closure as clo
+    from paper_2602_14667_gb300 import Lattice, _abi
+    nx, ny = 72, 40
+    p, f, g = _state(orc, nx, ny, 8, steps=4)
+    st = _packed(f, g)
+    f64, g64 = _unpacked(st, nx, ny)
+    Xo, _ = clo.features(p, f64, g64)
+    net = _random_net(clo, Xo, np.full((4, 3), 1.0), seed=5)
+    net.p["out_scale"][:] = 2e-5
+    with _abi.MLP(seed=0, max_batch=64) as m, Lattice(nx, ny, p.tau_f, p.tau_m, precision="fp32") as lat:
+        m.set_params(net.flat())
+        ref_net = clo.MLP.from_flat(m.get_params())
+        _abi.set_closure(lat, m)
+        _abi.set_closure_kernel(lat, kind)
+        _abi.set_closure_interval(lat, 4)
+        assert _abi.get_closure_interval(lat) == 4
+        _abi.set_precollision_state(lat, st)
+        lat.advance(9)
+        fg, gg = lat.get_populations()
+    def ninth(interval):
+        f8, g8 = clo.closure_run(p, f64, g64, 8, ref_net, bf16_like_gpu=True, interval=interval)
+        X8, _ = clo.features(p, f8, g8)
+        da, _ = ref_net.forward(X8, bf16_like_gpu=True)   # step 8 evaluates the MLP in both
+        return orc.collide_da(p, f8, g8, da.reshape(ny, nx, 3))
+    fs, gs = ninth(4)
+    f1, _ = ninth(1)
+    tol = 5e-6
+    assert np.abs(f1 - fs).max() > 10 * tol
+    assert np.abs(fg - fs).max() < tol and np.abs(gg - gs).max() < tol, (np.abs(fg - fs).max(), np.abs(gg - gs).max())
+
+
+def test_closure_interval_rejects_what_it_cannot_run():
+    from paper_2602_14667_gb300 import Lattice, MhdError, _abi
+    with Lattice(64, 32, 0.6, 0.6, precision="fp32") as lat:
+        for k in (0, 3, 128):
+            with pytest.raises(MhdError, match="EINVAL"):
+                _abi.set_closure_interval(lat, k)
+    with Lattice(64, 32, 0.6, 0.6, precision="fp16s") as lat:
+        with pytest.raises(MhdError, match="EINVAL"):
+            _abi.set_closure_interval(lat, 4)

@@ -217,3 +217,28 @@ def test_gradient_scales_bound_the_gradients_and_the_bf16_backward_rounding(clo)
         assert (np.abs(gb[k] - g0[k]) <= 3 * 2.0 ** -9 * s0[k]).all(), k
         moved |= bool(np.any(gb[k] != g0[k]))
     assert moved
+
+
+def test_closure_interval_with_a_constant_correction_changes_nothing(orc, clo):
+    """A network whose output does not depend on its input (zero weights, a
+    bias on the last layer) gives the same correction on every step, so
+    evaluating it every k-th step and reusing it in between must give the
+    same run for every k; with a state-dependent network the runs differ."""
+    import mhd_inputs
+    n = 16
+    p = orc.Params(n, n, 0.56, 0.6)
+    f, g = orc.init(p, *mhd_inputs.random_spectrum(n, n, 3, 0.03, 0.03, kmax=3))
+    const = clo.MLP(seed=2)
+    for k in ("W1", "W2", "W3"):
+        const.p[k][:] = 0.0
+    const.p["b3"] = np.array([0.3, -0.2, 0.1])
+    const.p["out_scale"][:] = 1e-4
+    ref = clo.closure_run(p, f, g, 9, const, interval=1)
+    for k in (2, 4, 9):
+        got = clo.closure_run(p, f, g, 9, const, interval=k)
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), k
+    net = clo.MLP(seed=2)
+    net.p["out_scale"][:] = 1e-4
+    a = clo.closure_run(p, f, g, 9, net, interval=1)
+    b = clo.closure_run(p, f, g, 9, net, interval=4)
+    assert np.abs(a[0] - b[0]).max() > 1e-10
