@@ -662,8 +662,8 @@ def run_closure(args):
 
 
 def run_closure_step(args):
-    """Cost of the closure step alone: a 512^2 FP32 lattice (random-spectrum
-    fields, tau 0.505) advanced with the plain step and with the closure step
+    """Cost of the closure step alone: an n^2 FP32 lattice (512^2 unless --n
+    names another size; random-spectrum fields, tau 0.505) advanced with the plain step and with the closure step
     (an untrained network: the MLP cost does not depend on the weights),
     CUDA events around `steps` graph-launched steps each."""
     import torch
@@ -698,15 +698,15 @@ def run_closure_step(args):
     mlp.close()
     # Dominant kernel: step_closure.  Its algorithmic work is the MLP,
     # 24x64 + 64x64 + 64x3 multiply-adds = 11,648 flop per node (BF16 tensor
-    # cores, FP32 accumulation); its state (2 x 19 planes FP32, 40 MB at
-    # 512^2) stays in L2 across steps.  Peak: the measured dense BF16 burst.
+    # cores, FP32 accumulation); its state (2 x 19 planes FP32: 40 MB at
+    # 512^2, 160 MB at 1024^2) stays mostly in L2 across steps.  Peak: the measured dense BF16 burst.
     flops = 2 * (24 * 64 + 64 * 64 + 64 * 3) * n * n
     # the closure kernel autotune would keep: the faster of the two
     best_kind = "closure" if out["closure"] <= out["closure_tcgen05"] else "closure_tcgen05"
     achieved = flops / (out[best_kind] * 1e-3) / 1e12
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
         peak = float(json.load(fh)["bf16_tflops"])
-    res = {"metric": "closure step cost (512^2 coarse lattice)", "value": out[best_kind] / out["plain"],
+    res = {"metric": f"closure step cost ({n}^2 coarse lattice)", "value": out[best_kind] / out["plain"],
            "unit": "closure / plain time per step", "higher_is_better": False, "n_gpus": 1,
            "ms_per_step": out, "mlups": {k: n * n / (v * 1e-3) / 1e6 for k, v in out.items()},
            "config": {"workload": f"closure_step_{n}x{n}_fp32", "tau": 0.505,

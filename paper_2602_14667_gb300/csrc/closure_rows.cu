@@ -5,17 +5,20 @@
 // A warp walks one tile: a strip of 30 output columns (lanes 1..30; lanes
 // 0 and 31 hold the neighbouring columns, so x neighbours arrive by warp
 // shuffles) and a stack of rows, downwards in even row segments and upwards
-// in odd ones.  For every row it pulls the pre-collision populations of its
-// 32 nodes (the step's gather, one node per lane), keeps u and b of the
-// last three rows and the populations of the last two in registers, and
-// for the row before the newest one forms the 24 features (point values
-// and the 3 x 3 stencils), runs the 24 -> 64 -> 64 -> 3 MLP on the warp's 32
-// feature rows (BF16 operands, FP32 accumulation; bias in the accumulator,
-// ReLU and the BF16 packing of the next layer's operand in one conversion),
-// adds the output to the projected a1^(2) and collides (tasks 3-5 of the
-// paper's "Algorithm of computation").  The only block-wide barrier is the
-// one after the weights are staged in shared memory; the feature rows and
-// outputs pass through a per-warp shared tile.
+// in odd ones.  The pull of every row of the walk (the pre-collision
+// populations of its 32 nodes, one node per lane) is copied with cp.async
+// into a per-warp stage of three row slots one row ahead of its use (the
+// next row of the tile, or the first row of the warp's next tile), so the
+// loads of one row overlap the work on the previous one.  The warp keeps u
+// and b of the last three rows in registers; for the row before the newest
+// one it forms the 24 features (point values and the 3 x 3 stencils), runs
+// the 24 -> 64 -> 64 -> 3 MLP on its 32 feature rows as two M tiles sharing
+// every weight fragment (BF16 operands, FP32 accumulation; bias in the
+// accumulator, ReLU and the BF16 packing of the next layer's operand in one
+// conversion), adds the output to the projected a1^(2) and collides (tasks
+// 3-5 of the paper's "Algorithm of computation").  The only block-wide
+// barrier is the one after the weights are staged in shared memory; the
+// stage, the feature rows and the outputs are per warp.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -40,9 +43,12 @@ struct RowsShared {
     bf16 Wt2[kHid * kRW2];
     bf16 Wt3[kOutPad * kRW2];
     float b1[kHid], b2[kHid], b3[kOutPad];
-    float mean[kIn], scale[kIn], out_scale[kOut];
+    alignas(16) float mean[kIn];
+    alignas(16) float scale[kIn];
+    float out_scale[kOut];
     alignas(16) bf16 feat[kRWarps][32 * kRFeat];
     float da[kRWarps][32][4];
+    float stage[kRWarps][3][kPlanes][32];  // per warp: three pulled rows, plane-major, a column per lane
 };
 static_assert(offsetof(RowsShared, Wt1) % 16 == 0 && offsetof(RowsShared, Wt2) % 16 == 0 &&
                   offsetof(RowsShared, Wt3) % 16 == 0 && offsetof(RowsShared, feat) % 16 == 0,
@@ -62,61 +68,82 @@ __device__ __forceinline__ uint32_t relu_pack2(float lo, float hi) {
     return u;
 }
 
-// MLP of rows m0 .. m0+15 of the warp's feature tile; out_scale * y into da.
-__device__ __forceinline__ void mlp16(const RowsShared& sh, const bf16* feat, float (*da)[4], int m0, int lane) {
+// MLP of the warp's 32 feature rows (two M tiles sharing every B fragment);
+// out_scale * y into da.
+__device__ __forceinline__ void mlp32(const RowsShared& sh, const bf16* feat, float (*da)[4], int lane) {
     const int t = lane & 3, lr = lane & 7, lm = lane >> 3;
-    uint32_t a1[2][4];
+    uint32_t h[2][4][4];  // layer 2's A fragments (K = 64) of both M tiles
+    {
+        uint32_t a1[2][2][4];
 #pragma unroll
-    for (int c = 0; c < 2; ++c) ldsm_x4(a1[c], feat + (m0 + lr + 8 * (lm & 1)) * kRFeat + 16 * c + 8 * (lm >> 1));
-    uint32_t h[4][4];  // layer 2's A fragments (K = 64)
+        for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const float2 bb = *reinterpret_cast<const float2*>(sh.b1 + 8 * j + 2 * t);
-        float d[4] = {bb.x, bb.y, bb.x, bb.y};
-        uint32_t w[4];
-        ldsm_x4(w, sh.Wt1 + (8 * j + lr) * kRW1 + 8 * lm);
-        const uint32_t b0[2] = {w[0], w[1]}, b1[2] = {w[2], w[3]};
-        mma16816(d, a1[0], b0);
-        mma16816(d, a1[1], b1);
-        // the accumulator of n-tile j is half of k-chunk j/2 of the next A
-        h[j >> 1][(j & 1) * 2 + 0] = relu_pack2(d[0], d[1]);
-        h[j >> 1][(j & 1) * 2 + 1] = relu_pack2(d[2], d[3]);
+            for (int c = 0; c < 2; ++c)
+                ldsm_x4(a1[mt][c], feat + (16 * mt + lr + 8 * (lm & 1)) * kRFeat + 16 * c + 8 * (lm >> 1));
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float2 bb = *reinterpret_cast<const float2*>(sh.b1 + 8 * j + 2 * t);
+            uint32_t w[4];
+            ldsm_x4(w, sh.Wt1 + (8 * j + lr) * kRW1 + 8 * lm);
+            const uint32_t b0[2] = {w[0], w[1]}, b1[2] = {w[2], w[3]};
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                float d[4] = {bb.x, bb.y, bb.x, bb.y};
+                mma16816(d, a1[mt][0], b0);
+                mma16816(d, a1[mt][1], b1);
+                // the accumulator of n-tile j is half of k-chunk j/2 of the next A
+                h[mt][j >> 1][(j & 1) * 2 + 0] = relu_pack2(d[0], d[1]);
+                h[mt][j >> 1][(j & 1) * 2 + 1] = relu_pack2(d[2], d[3]);
+            }
+        }
     }
-    uint32_t h2[4][4];
+    uint32_t h2[2][4][4];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const float2 bb = *reinterpret_cast<const float2*>(sh.b2 + 8 * j + 2 * t);
-        float d[4] = {bb.x, bb.y, bb.x, bb.y};
+        float d[2][4] = {{bb.x, bb.y, bb.x, bb.y}, {bb.x, bb.y, bb.x, bb.y}};
 #pragma unroll
         for (int c = 0; c < 4; c += 2) {
             uint32_t w[4];
             ldsm_x4(w, sh.Wt2 + (8 * j + lr) * kRW2 + 16 * c + 8 * lm);
             const uint32_t b0[2] = {w[0], w[1]}, b1[2] = {w[2], w[3]};
-            mma16816(d, h[c], b0);
-            mma16816(d, h[c + 1], b1);
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                mma16816(d[mt], h[mt][c], b0);
+                mma16816(d[mt], h[mt][c + 1], b1);
+            }
         }
-        h2[j >> 1][(j & 1) * 2 + 0] = relu_pack2(d[0], d[1]);
-        h2[j >> 1][(j & 1) * 2 + 1] = relu_pack2(d[2], d[3]);
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            h2[mt][j >> 1][(j & 1) * 2 + 0] = relu_pack2(d[mt][0], d[mt][1]);
+            h2[mt][j >> 1][(j & 1) * 2 + 1] = relu_pack2(d[mt][2], d[mt][3]);
+        }
     }
     const float2 bb = *reinterpret_cast<const float2*>(sh.b3 + 2 * t);
-    float d[4] = {bb.x, bb.y, bb.x, bb.y};
+    float d[2][4] = {{bb.x, bb.y, bb.x, bb.y}, {bb.x, bb.y, bb.x, bb.y}};
 #pragma unroll
     for (int c = 0; c < 4; c += 2) {
         uint32_t w[4];
         ldsm_x4(w, sh.Wt3 + lr * kRW2 + 16 * c + 8 * lm);
         const uint32_t b0[2] = {w[0], w[1]}, b1[2] = {w[2], w[3]};
-        mma16816(d, h2[c], b0);
-        mma16816(d, h2[c + 1], b1);
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            mma16816(d[mt], h2[mt][c], b0);
+            mma16816(d[mt], h2[mt][c + 1], b1);
+        }
     }
     // d0: (row g, col 2t), d1: (g, 2t+1), d2: (g+8, 2t), d3: (g+8, 2t+1)
     const int g = lane >> 2;
-    if (2 * t < kOut) {
-        da[m0 + g][2 * t] = d[0] * sh.out_scale[2 * t];
-        da[m0 + g + 8][2 * t] = d[2] * sh.out_scale[2 * t];
-    }
-    if (2 * t + 1 < kOut) {
-        da[m0 + g][2 * t + 1] = d[1] * sh.out_scale[2 * t + 1];
-        da[m0 + g + 8][2 * t + 1] = d[3] * sh.out_scale[2 * t + 1];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        if (2 * t < kOut) {
+            da[16 * mt + g][2 * t] = d[mt][0] * sh.out_scale[2 * t];
+            da[16 * mt + g + 8][2 * t] = d[mt][2] * sh.out_scale[2 * t];
+        }
+        if (2 * t + 1 < kOut) {
+            da[16 * mt + g][2 * t + 1] = d[mt][1] * sh.out_scale[2 * t + 1];
+            da[16 * mt + g + 8][2 * t + 1] = d[mt][3] * sh.out_scale[2 * t + 1];
+        }
     }
 }
 
@@ -161,44 +188,83 @@ __global__ void __launch_bounds__(kRWarps * 32, 2) step_closure_rows(const StepA
     if (tid < kOutPad) sh.b3[tid] = cp.b3[tid];
     if (tid < kIn) { sh.mean[tid] = cp.mean[tid]; sh.scale[tid] = cp.scale[tid]; }
     if (tid < kOut) sh.out_scale[tid] = cp.out_scale[tid];
-    cp_async_wait<0>();
+
+    // tile t: strip t % strips of 30 output columns (lane l holds column
+    // 30 * strip - 1 + l, wrapped), rows [y0, y1) of segment t / strips; row
+    // i of its walk is y0 - 1 + i (even segments) or y1 - i (odd ones)
+    struct Tile {
+        int xl, xw, y0, y1;
+        bool up;
+    };
+    auto tile_of = [&](int t) {
+        Tile T;
+        const int strip = t % strips, seg = t / strips;
+        T.xl = strip * 30 - 1 + lane;
+        T.xw = T.xl % a.nx;
+        if (T.xw < 0) T.xw += a.nx;
+        T.y0 = seg * rows;
+        T.y1 = min(a.ny, T.y0 + rows);
+        T.up = seg & 1;
+        return T;
+    };
+    // the pull of row i of tile T into stage slot sl: each lane copies its
+    // own node's 19 cells into its own column of the slot
+    auto issue_row = [&](const Tile& T, int i, int sl) {
+        const int m = T.up ? T.y1 - i : T.y0 - 1 + i;
+        const int my = m < 0 ? m + a.ny : (m >= a.ny ? m - a.ny : m);
+        const int ym = my == 0 ? a.ny - 1 : my - 1, yp = my + 1 == a.ny ? 0 : my + 1;
+        const int xm = T.xw == 0 ? a.nx - 1 : T.xw - 1, xp = T.xw + 1 == a.nx ? 0 : T.xw + 1;
+        const Off pt = (Off)a.pitch, pl = (Off)a.plane;
+        const Off r_m = (Off)ym * pt, r_0 = (Off)my * pt, r_p = (Off)yp * pt;
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) {
+            const int cx = pcx(p), cy = pcy(p);
+            const Off o = (Off)p * pl + (cy > 0 ? r_m : (cy < 0 ? r_p : r_0)) + (cx > 0 ? xm : (cx < 0 ? xp : T.xw));
+            cp_async4(&sh.stage[warp][sl][p][lane], src + o);
+        }
+    };
+    const int stride = gridDim.x * kRWarps;
+    int t = blockIdx.x * kRWarps + warp;
+    // the first row of the warp's first tile is in flight while the weights land
+    if (t < ntiles) issue_row(tile_of(t), 0, 0);
+    cp_async_commit();
+    cp_async_wait<1>();  // this thread's weight pieces (the older group)
     __syncthreads();
 
     bf16* feat = sh.feat[warp];
     float(*da)[4] = sh.da[warp];
     const bool out_lane = lane >= 1 && lane <= 30;
     const float rho0 = a.np.rho0;
-    for (int t = blockIdx.x * kRWarps + warp; t < ntiles; t += gridDim.x * kRWarps) {
-        const int strip = t % strips, seg = t / strips;
-        const int xl = strip * 30 - 1 + lane;  // the lane's node (may lie outside: wrapped)
-        int xw = xl % a.nx;
-        if (xw < 0) xw += a.nx;
-        const int y0 = seg * rows, y1 = min(a.ny, y0 + rows);
-        const bool up = seg & 1;
-        const float sgn = up ? -1.f : 1.f;
-        float wnd[3][4] = {};         // u_x, u_y, b_x, b_y of the last three rows (slot 2 newest)
-        float cur[kPlanes] = {}, nxt[kPlanes] = {};  // populations of the rows in slots 1, 2
-        const int nrow = y1 - y0 + 2;
+    int sl = 0;  // stage slot of the row about to be used
+    for (; t < ntiles; t += stride) {
+        const Tile T = tile_of(t);
+        const float sgn = T.up ? -1.f : 1.f;
+        float wnd[3][4] = {};  // u_x, u_y, b_x, b_y of the last three rows (slot 2 newest)
+        const int nrow = T.y1 - T.y0 + 2;
         for (int i = 0; i < nrow; ++i) {
-            const int m = up ? y1 - i : y0 - 1 + i;
-            const int my = m < 0 ? m + a.ny : (m >= a.ny ? m - a.ny : m);
+            // three slots: the row in flight (next of this tile, or the first
+            // of the warp's next tile), the newest row, and the row before it
+            const int sl_next = sl == 2 ? 0 : sl + 1, sl_prev = sl == 0 ? 2 : sl - 1;
+            if (i + 1 < nrow)
+                issue_row(T, i + 1, sl_next);
+            else if (t + stride < ntiles)
+                issue_row(tile_of(t + stride), 0, sl_next);
+            cp_async_commit();
+            cp_async_wait<1>();
+            const float(*nxt)[32] = sh.stage[warp][sl];
+            const float(*cur)[32] = sh.stage[warp][sl_prev];
+            sl = sl_next;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 wnd[0][q] = wnd[1][q];
                 wnd[1][q] = wnd[2][q];
             }
-#pragma unroll
-            for (int p = 0; p < kPlanes; ++p) cur[p] = nxt[p];
             {
-                float v[kPlanes][1];
-                gather_row_wrapped<1, 1, false, Off>(src, a.nx, a.ny, a.pitch, a.plane, xw, my, lane, v);
-#pragma unroll
-                for (int p = 0; p < kPlanes; ++p) nxt[p] = v[p][0];
                 float f[9], g[10];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) f[k] = nxt[k];
+                for (int k = 0; k < 9; ++k) f[k] = nxt[k][lane];
 #pragma unroll
-                for (int k = 0; k < 10; ++k) g[k] = nxt[9 + k];
+                for (int k = 0; k < 10; ++k) g[k] = nxt[9 + k][lane];
                 const Moments<float> mm = moments(f, g, rho0);
                 wnd[2][0] = mm.ux;
                 wnd[2][1] = mm.uy;
@@ -206,48 +272,50 @@ __global__ void __launch_bounds__(kRWarps * 32, 2) step_closure_rows(const StepA
                 wnd[2][3] = mm.by;
             }
             if (i < 2) continue;  // warp-uniform
-            const int o = up ? m + 1 : m - 1;  // the row in slot 1: y0 <= o < y1
+            const int o = T.up ? T.y1 - i + 1 : T.y0 - 2 + i;  // the row of cur: y0 <= o < y1
             float fe[kIn];
             {
                 float f[9], g[10];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) f[k] = cur[k];
+                for (int k = 0; k < 9; ++k) f[k] = cur[k][lane];
 #pragma unroll
-                for (int k = 0; k < 10; ++k) g[k] = cur[9 + k];
+                for (int k = 0; k < 10; ++k) g[k] = cur[9 + k][lane];
                 point_features(f, g, rho0, fe);
             }
             stencil_rows(wnd, sgn, fe + 8);
             {
                 uint32_t pk[kInPad / 2];
 #pragma unroll
-                for (int c = 0; c < kInPad / 2; ++c) {
-                    const float v0 = 2 * c < kIn ? (fe[2 * c] - sh.mean[2 * c]) * sh.scale[2 * c] : 0.f;
-                    const float v1 = 2 * c + 1 < kIn ? (fe[2 * c + 1] - sh.mean[2 * c + 1]) * sh.scale[2 * c + 1] : 0.f;
-                    pk[c] = pack2(v0, v1);
+                for (int c4 = 0; c4 < kIn / 4; ++c4) {
+                    const float4 mu = *reinterpret_cast<const float4*>(sh.mean + 4 * c4);
+                    const float4 sc = *reinterpret_cast<const float4*>(sh.scale + 4 * c4);
+                    pk[2 * c4] = pack2((fe[4 * c4] - mu.x) * sc.x, (fe[4 * c4 + 1] - mu.y) * sc.y);
+                    pk[2 * c4 + 1] = pack2((fe[4 * c4 + 2] - mu.z) * sc.z, (fe[4 * c4 + 3] - mu.w) * sc.w);
                 }
+#pragma unroll
+                for (int c = kIn / 2; c < kInPad / 2; ++c) pk[c] = 0u;
                 uint4* row = reinterpret_cast<uint4*>(feat + lane * kRFeat);
 #pragma unroll
                 for (int c = 0; c < kInPad / 8; ++c)
                     row[c] = make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
             }
             __syncwarp();
-            mlp16(sh, feat, da, 0, lane);
-            mlp16(sh, feat, da, 16, lane);
+            mlp32(sh, feat, da, lane);
             __syncwarp();
-            if (out_lane && xl < a.nx) {
+            if (out_lane && T.xl < a.nx) {
                 float f[9], g[10];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) f[k] = cur[k];
+                for (int k = 0; k < 9; ++k) f[k] = cur[k][lane];
 #pragma unroll
-                for (int k = 0; k < 10; ++k) g[k] = cur[9 + k];
+                for (int k = 0; k < 10; ++k) g[k] = cur[9 + k][lane];
                 const float d3[3] = {da[lane][0], da[lane][1], da[lane][2]};
                 if (cp.da_out) {
-                    const Off nn = (Off)a.nx * (Off)a.ny, node = (Off)o * (Off)a.nx + xl;
+                    const Off nn = (Off)a.nx * (Off)a.ny, node = (Off)o * (Off)a.nx + T.xl;
 #pragma unroll
                     for (int k = 0; k < 3; ++k) cp.da_out[(Off)k * nn + node] = d3[k];
                 }
                 collide_impl<true, float>(f, g, a.np, d3);
-                const Off off = (Off)o * (Off)a.pitch + xl, pl = (Off)a.plane;
+                const Off off = (Off)o * (Off)a.pitch + T.xl, pl = (Off)a.plane;
 #pragma unroll
                 for (int k = 0; k < 9; ++k) dst[(Off)k * pl + off] = f[k];
 #pragma unroll
@@ -256,6 +324,7 @@ __global__ void __launch_bounds__(kRWarps * 32, 2) step_closure_rows(const StepA
             __syncwarp();  // the next row rewrites the warp's feature and output tiles
         }
     }
+    cp_async_wait<0>();
 }
 
 // The steps between two evaluations of the MLP: the fused step (the pull

@@ -424,3 +424,29 @@ def test_closure_interval_rejects_what_it_cannot_run():
     with Lattice(64, 32, 0.6, 0.6, precision="fp16s") as lat:
         with pytest.raises(MhdError, match="EINVAL"):
             _abi.set_closure_interval(lat, 4)
+
+
+def test_closure_interval_count_survives_graphs_and_split_advances():
+    """The interval counts steps across calls and CUDA graphs: 3 + 69 + 5
+    steps in three calls (the second steps singly up to the next evaluation
+    of the MLP, then launches a captured 64-step graph) give the same bits as
+    77 steps in one call (a graph, then single steps)."""
+    import mhd_inputs
+    from oracle import closure as clo
+    from paper_2602_14667_gb300 import Lattice, _abi
+    n = 128
+    net = clo.MLP(seed=8)
+    net.p["out_scale"][:] = 2e-5
+    fields = mhd_inputs.random_spectrum(n, n, 12, 0.03, 0.03)
+    out = []
+    with _abi.MLP(seed=0, max_batch=64) as m:
+        m.set_params(net.flat())
+        for split in ((3, 69, 5), (77,)):
+            with Lattice(n, n, 0.53, 0.56, precision="fp32") as lat:
+                lat.set_fields(*fields)
+                _abi.set_closure(lat, m)
+                _abi.set_closure_interval(lat, 8)
+                for s in split:
+                    lat.advance(s)
+                out.append(lat.get_state())
+    assert np.array_equal(out[0], out[1])
