@@ -159,6 +159,17 @@ mhd_status mhd_advance(mhd_lattice* l, long long nsteps);
 mhd_status mhd_get_fields(mhd_lattice* l, double* rho, double* ux, double* uy, double* bx,
                           double* by);
 
+/* FP32 forms of mhd_set_fields and mhd_get_fields, for host data in single
+ * precision (half the bytes over the host link).  Same arguments, layout
+ * (row-major nx*ny, x fastest), NULL rules, ownership and errors.  Inputs
+ * are widened exactly, so mhd_set_fields_f32 sets the state mhd_set_fields
+ * sets for the same values held as double; each output is the value
+ * mhd_get_fields returns, rounded to float (to nearest even). */
+mhd_status mhd_set_fields_f32(mhd_lattice* l, const float* ux, const float* uy, const float* bx,
+                              const float* by, const float* rho);
+mhd_status mhd_get_fields_f32(mhd_lattice* l, float* rho, float* ux, float* uy, float* bx,
+                              float* by);
+
 /* Global diagnostics of the current state (see mhd_totals), reduced on the
  * GPU in FP64 with a fixed order (bitwise reproducible).  Waits for the
  * stream.  MHD_EUNSTABLE (with *out filled) if any total is not finite.

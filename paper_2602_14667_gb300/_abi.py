@@ -54,12 +54,15 @@ class MhdError(RuntimeError):
 _lib = None
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
+_F = ctypes.POINTER(ctypes.c_float)
 
 _SIGNATURES = {
     "mhd_create": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(mhd_params), _P, ctypes.POINTER(_P)],
     "mhd_set_fields": [_P, _D, _D, _D, _D, _D],
     "mhd_advance": [_P, ctypes.c_longlong],
     "mhd_get_fields": [_P, _D, _D, _D, _D, _D],
+    "mhd_set_fields_f32": [_P, _F, _F, _F, _F, _F],
+    "mhd_get_fields_f32": [_P, _F, _F, _F, _F, _F],
     "mhd_get_totals": [_P, ctypes.POINTER(mhd_totals)],
     "mhd_get_populations": [_P, _D, _D],
     "mhd_set_populations": [_P, _D, _D],
@@ -136,6 +139,12 @@ def _dptr(a):
     return a.ctypes.data_as(_D)
 
 
+def _fptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_F)
+
+
 def _in(a, n):
     arr = np.ascontiguousarray(a, dtype=np.float64)
     if arr.size != n:
@@ -186,6 +195,17 @@ class Lattice:
         self.close()
 
     def set_fields(self, ux, uy, bx, by, rho=None):
+        """Initial equilibrium from u, b (and rho); float32 arrays (all of
+        them C-contiguous float32) go through mhd_set_fields_f32, anything
+        else is converted to float64 for mhd_set_fields."""
+        given = [a for a in (ux, uy, bx, by, rho) if a is not None]
+        if all(isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags["C_CONTIGUOUS"] for a in given):
+            for a in given:
+                if a.size != self.n:
+                    raise ValueError(f"expected {self.n} values, got {a.size}")
+            check(lib().mhd_set_fields_f32(self._h, *[_fptr(a) for a in (ux, uy, bx, by, rho)]),
+                  "mhd_set_fields_f32")
+            return
         arrs = [_in(a, self.n) for a in (ux, uy, bx, by)]
         r = None if rho is None else _in(rho, self.n)
         check(lib().mhd_set_fields(self._h, *[_dptr(a) for a in arrs], _dptr(r)), "mhd_set_fields")
@@ -193,15 +213,23 @@ class Lattice:
     def advance(self, nsteps: int):
         check(lib().mhd_advance(self._h, int(nsteps)), "mhd_advance")
 
-    def get_fields(self, out=None):
-        """rho, ux, uy, bx, by as a dict; `out` may give five C-contiguous
-        float64 arrays of nx*ny to fill instead (e.g. pinned host memory)."""
+    def get_fields(self, out=None, dtype=np.float64):
+        """rho, ux, uy, bx, by as a dict of float64 (or float32: dtype, or
+        float32 `out` arrays, read through mhd_get_fields_f32); `out` may give
+        five C-contiguous arrays of nx*ny, all of one of the two types, to
+        fill instead (e.g. pinned host memory)."""
         if out is None:
-            out = [np.empty((self.ny, self.nx)) for _ in range(5)]
+            out = [np.empty((self.ny, self.nx), dtype=dtype) for _ in range(5)]
+        dt = out[0].dtype
+        if dt not in (np.float64, np.float32):
+            raise ValueError("out arrays must be float64 or float32")
         for a in out:
-            if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or a.size != self.n:
-                raise ValueError("out arrays must be C-contiguous float64 of nx*ny")
-        check(lib().mhd_get_fields(self._h, *[_dptr(a) for a in out]), "mhd_get_fields")
+            if a.dtype != dt or not a.flags["C_CONTIGUOUS"] or a.size != self.n:
+                raise ValueError("out arrays must be C-contiguous, of one type, with nx*ny values")
+        if dt == np.float32:
+            check(lib().mhd_get_fields_f32(self._h, *[_fptr(a) for a in out]), "mhd_get_fields_f32")
+        else:
+            check(lib().mhd_get_fields(self._h, *[_dptr(a) for a in out]), "mhd_get_fields")
         return dict(zip(("rho", "ux", "uy", "bx", "by"), out))
 
     def get_totals(self, check_stable: bool = True) -> dict:

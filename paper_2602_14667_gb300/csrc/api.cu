@@ -48,8 +48,9 @@ bool finite_array(const double* a, long long n) {
 
 // Input check of mhd_set_fields on the device copies: bit 0 of *flags for a
 // non-finite field value, bit 1 for rho <= 0 (or non-finite rho).
-__global__ void check_fields_kernel(const double* ux, const double* uy, const double* bx, const double* by,
-                                    const double* rho, long long n, int* flags) {
+template <typename T>
+__global__ void check_fields_kernel(const T* ux, const T* uy, const T* bx, const T* by, const T* rho, long long n,
+                                    int* flags) {
     int f = 0;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
@@ -355,16 +356,20 @@ mhd_status mhd_destroy(mhd_lattice* l) {
     return MHD_OK;
 }
 
-mhd_status mhd_set_fields(mhd_lattice* l, const double* ux, const double* uy, const double* bx,
-                          const double* by, const double* rho) {
+// mhd_set_fields / mhd_set_fields_f32: T is the host (and device copy) type
+// of the fields, staged in the lattice's io buffer (5 x nx*ny doubles).
+extern "C++" {
+template <typename T>
+static mhd_status set_fields_t(mhd_lattice* l, const T* ux, const T* uy, const T* bx, const T* by, const T* rho) {
     if (!l || !ux || !uy || !bx || !by) return fail(MHD_EINVAL, "NULL argument");
     const long long n = l->n();
     CK(cudaSetDevice(l->dev), "cudaSetDevice");
     mhd_status s = ensure_io(l);
     if (s != MHD_OK) return s;
-    const size_t bytes = sizeof(double) * n;
-    double* d[5] = {l->io, l->io + n, l->io + 2 * n, l->io + 3 * n, l->io + 4 * n};
-    const double* h[5] = {ux, uy, bx, by, rho};
+    const size_t bytes = sizeof(T) * n;
+    T* io = reinterpret_cast<T*>(l->io);
+    T* d[5] = {io, io + n, io + 2 * n, io + 3 * n, io + 4 * n};
+    const T* h[5] = {ux, uy, bx, by, rho};
     for (int q = 0; q < 5; ++q)
         if (h[q]) CK(cudaMemcpyAsync(d[q], h[q], bytes, cudaMemcpyHostToDevice, l->stream), "H2D fields");
     // the inputs are checked on the device copies, before the state is touched
@@ -372,8 +377,8 @@ mhd_status mhd_set_fields(mhd_lattice* l, const double* ux, const double* uy, co
         int flags = 0;
         CK(cudaMemsetAsync(l->flags_d, 0, sizeof(int), l->stream), "clear input flags");
         const long long blocks = std::max(1LL, std::min((n + 255) / 256, 8LL * mhd::device_sms()));
-        check_fields_kernel<<<(unsigned)blocks, 256, 0, l->stream>>>(d[0], d[1], d[2], d[3], rho ? d[4] : nullptr, n,
-                                                                      l->flags_d);
+        check_fields_kernel<T><<<(unsigned)blocks, 256, 0, l->stream>>>(d[0], d[1], d[2], d[3],
+                                                                         rho ? d[4] : nullptr, n, l->flags_d);
         CK(cudaGetLastError(), "input check kernel");
         CK(cudaMemcpyAsync(&flags, l->flags_d, sizeof(int), cudaMemcpyDeviceToHost, l->stream), "input flags");
         CK(cudaStreamSynchronize(l->stream), "mhd_set_fields");
@@ -391,6 +396,17 @@ mhd_status mhd_set_fields(mhd_lattice* l, const double* ux, const double* uy, co
     l->state_is_eq = true;
     l->aa_streamed = false;
     return MHD_OK;
+}
+}  // extern "C++"
+
+mhd_status mhd_set_fields(mhd_lattice* l, const double* ux, const double* uy, const double* bx,
+                          const double* by, const double* rho) {
+    return set_fields_t(l, ux, uy, bx, by, rho);
+}
+
+mhd_status mhd_set_fields_f32(mhd_lattice* l, const float* ux, const float* uy, const float* bx, const float* by,
+                              const float* rho) {
+    return set_fields_t(l, ux, uy, bx, by, rho);
 }
 
 // Graph of kGraphSteps steps starting from buffer `from` (two buffers) or
@@ -476,7 +492,9 @@ mhd_status mhd_advance(mhd_lattice* l, long long nsteps) {
     return MHD_OK;
 }
 
-mhd_status mhd_get_fields(mhd_lattice* l, double* rho, double* ux, double* uy, double* bx, double* by) {
+extern "C++" {
+template <typename T>
+static mhd_status get_fields_t(mhd_lattice* l, T* rho, T* ux, T* uy, T* bx, T* by) {
     if (!l) return fail(MHD_EINVAL, "lattice is NULL");
     if (!l->fields_set) return fail(MHD_ESTATE, "set fields or populations first");
     CK(cudaSetDevice(l->dev), "cudaSetDevice");
@@ -488,18 +506,26 @@ mhd_status mhd_get_fields(mhd_lattice* l, double* rho, double* ux, double* uy, d
     mhd_status s = ensure_io(l);
     if (s != MHD_OK) return s;
     const long long n = l->n();
-    double* d[5] = {l->io, l->io + n, l->io + 2 * n, l->io + 3 * n, l->io + 4 * n};
-    double* h[5] = {rho, ux, uy, bx, by};
+    T* io = reinterpret_cast<T*>(l->io);
+    T* d[5] = {io, io + n, io + 2 * n, io + 3 * n, io + 4 * n};
+    T* h[5] = {rho, ux, uy, bx, by};
     CK(mhd::launch_fields(l->L, l->p.precision, l->buf[l->cur], l->p.rho0, h[0] ? d[0] : nullptr,
                           h[1] ? d[1] : nullptr, h[2] ? d[2] : nullptr, h[3] ? d[3] : nullptr,
                           h[4] ? d[4] : nullptr, l->stream),
        "fields kernel");
     for (int q = 0; q < 5; ++q)
-        if (h[q])
-            CK(cudaMemcpyAsync(h[q], d[q], sizeof(double) * n, cudaMemcpyDeviceToHost, l->stream),
-               "D2H fields");
+        if (h[q]) CK(cudaMemcpyAsync(h[q], d[q], sizeof(T) * n, cudaMemcpyDeviceToHost, l->stream), "D2H fields");
     CK(cudaStreamSynchronize(l->stream), "mhd_get_fields");
     return MHD_OK;
+}
+}  // extern "C++"
+
+mhd_status mhd_get_fields(mhd_lattice* l, double* rho, double* ux, double* uy, double* bx, double* by) {
+    return get_fields_t(l, rho, ux, uy, bx, by);
+}
+
+mhd_status mhd_get_fields_f32(mhd_lattice* l, float* rho, float* ux, float* uy, float* bx, float* by) {
+    return get_fields_t(l, rho, ux, uy, bx, by);
 }
 
 mhd_status mhd_get_totals(mhd_lattice* l, mhd_totals* out) {

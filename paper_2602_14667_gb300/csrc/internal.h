@@ -37,13 +37,20 @@ cudaError_t launch_step(const StepLaunch& s, cudaStream_t st);
 // is (V, BY) a legal launch shape for this lattice?
 bool step_shape_ok(const Layout& L, int prec, int wall_x, int V, int BY);
 
-// f = f_eq(rho, u, b), g = g_eq(u, b) from device FP64 fields (rho may be null)
+// f = f_eq(rho, u, b), g = g_eq(u, b) from device FP64 (or FP32) fields
+// (rho may be null)
 cudaError_t launch_init(const Layout& L, int prec, void* buf, const double* rho, const double* ux,
                         const double* uy, const double* bx, const double* by, double rho0,
                         int variant, cudaStream_t st);
-// rho, u, b (FP64, nx*ny each, any may be null) of the stored state
+cudaError_t launch_init(const Layout& L, int prec, void* buf, const float* rho, const float* ux,
+                        const float* uy, const float* bx, const float* by, double rho0, int variant,
+                        cudaStream_t st);
+// rho, u, b (FP64, or FP64 rounded to FP32; nx*ny each, any may be null)
+// of the stored state
 cudaError_t launch_fields(const Layout& L, int prec, const void* buf, double rho0, double* rho,
                           double* ux, double* uy, double* bx, double* by, cudaStream_t st);
+cudaError_t launch_fields(const Layout& L, int prec, const void* buf, double rho0, float* rho, float* ux,
+                          float* uy, float* bx, float* by, cudaStream_t st);
 // stored state whose pull-gather reproduces the packed FP32 pre-collision
 // state F (periodic axes)
 cudaError_t launch_unstream(const Layout& L, int prec, void* buf, const float* F, cudaStream_t st);

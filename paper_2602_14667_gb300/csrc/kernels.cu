@@ -152,10 +152,11 @@ __device__ __forceinline__ void encode_d(double v, __half& s) { s = __double2hal
 // compute type of the storage (FP64 for FP64, FP32 for FP32 and FP16S), as
 // the step evaluates its collision: on GB300 FP64 arithmetic would make
 // these memory-bound conversions bound by the FP64 units instead.
-template <int PREC>
-__global__ void init_kernel(Layout L, void* buf, const double* rho, const double* ux,
-                            const double* uy, const double* bx, const double* by, double rho0,
-                            int variant) {
+// T: the type of the device field arrays (double, or float for the FP32
+// field calls: converted exactly to double or as the FP32 value).
+template <int PREC, typename T>
+__global__ void init_kernel(Layout L, void* buf, const T* rho, const T* ux, const T* uy, const T* bx,
+                            const T* by, double rho0, int variant) {
     using S = typename Prec<PREC>::S;
     using C = typename Prec<PREC>::C;
     const long long n = (long long)L.nx * L.ny;
@@ -171,9 +172,8 @@ __global__ void init_kernel(Layout L, void* buf, const double* rho, const double
     }
 }
 
-template <int PREC>
-__global__ void fields_kernel(Layout L, const void* buf, double rho0, double* rho, double* ux,
-                              double* uy, double* bx, double* by) {
+template <int PREC, typename T>
+__global__ void fields_kernel(Layout L, const void* buf, double rho0, T* rho, T* ux, T* uy, T* bx, T* by) {
     using S = typename Prec<PREC>::S;
     using C = typename Prec<PREC>::C;
     const long long n = (long long)L.nx * L.ny;
@@ -186,11 +186,13 @@ __global__ void fields_kernel(Layout L, const void* buf, double rho0, double* rh
         for (int i = 0; i < 9; ++i) f[i] = decode(b[(long long)i * L.plane + o]);
         for (int q = 0; q < 10; ++q) g[q] = decode(b[(long long)(9 + q) * L.plane + o]);
         const Moments<C> m = moments<C>(f, g, C(rho0));
-        if (rho) rho[k] = rho0 + (double)m.drho;  // the deviation keeps its relative precision
-        if (ux) ux[k] = m.ux;
-        if (uy) uy[k] = m.uy;
-        if (bx) bx[k] = m.bx;
-        if (by) by[k] = m.by;
+        // the deviation keeps its relative precision; a float output is the
+        // double value rounded to nearest
+        if (rho) rho[k] = T(rho0 + (double)m.drho);
+        if (ux) ux[k] = T(m.ux);
+        if (uy) uy[k] = T(m.uy);
+        if (bx) bx[k] = T(m.bx);
+        if (by) by[k] = T(m.by);
     }
 }
 
@@ -268,19 +270,52 @@ static dim3 flat_grid(long long n) {
         }                                                                 \
     } while (0)
 
+#define MHD_DISPATCH_T(prec, KERNEL, T, grid, block, st, ...)               \
+    do {                                                                     \
+        switch (prec) {                                                      \
+        case 0: KERNEL<0, T><<<grid, block, 0, st>>>(__VA_ARGS__); break;    \
+        case 1: KERNEL<1, T><<<grid, block, 0, st>>>(__VA_ARGS__); break;    \
+        case 2: KERNEL<2, T><<<grid, block, 0, st>>>(__VA_ARGS__); break;    \
+        default: return cudaErrorInvalidValue;                               \
+        }                                                                    \
+    } while (0)
+
+template <typename T>
+static cudaError_t launch_init_t(const Layout& L, int prec, void* buf, const T* rho, const T* ux, const T* uy,
+                                 const T* bx, const T* by, double rho0, int variant, cudaStream_t st) {
+    MHD_DISPATCH_T(prec, init_kernel, T, flat_grid((long long)L.nx * L.ny), 256, st, L, buf, rho, ux, uy, bx,
+                   by, rho0, variant);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_fields_t(const Layout& L, int prec, const void* buf, double rho0, T* rho, T* ux,
+                                   T* uy, T* bx, T* by, cudaStream_t st) {
+    MHD_DISPATCH_T(prec, fields_kernel, T, flat_grid((long long)L.nx * L.ny), 256, st, L, buf, rho0, rho, ux,
+                   uy, bx, by);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init(const Layout& L, int prec, void* buf, const double* rho, const double* ux,
                         const double* uy, const double* bx, const double* by, double rho0,
                         int variant, cudaStream_t st) {
-    MHD_DISPATCH(prec, init_kernel, flat_grid((long long)L.nx * L.ny), 256, st, L, buf, rho, ux, uy,
-                 bx, by, rho0, variant);
-    return cudaGetLastError();
+    return launch_init_t(L, prec, buf, rho, ux, uy, bx, by, rho0, variant, st);
+}
+
+cudaError_t launch_init(const Layout& L, int prec, void* buf, const float* rho, const float* ux,
+                        const float* uy, const float* bx, const float* by, double rho0, int variant,
+                        cudaStream_t st) {
+    return launch_init_t(L, prec, buf, rho, ux, uy, bx, by, rho0, variant, st);
 }
 
 cudaError_t launch_fields(const Layout& L, int prec, const void* buf, double rho0, double* rho,
                           double* ux, double* uy, double* bx, double* by, cudaStream_t st) {
-    MHD_DISPATCH(prec, fields_kernel, flat_grid((long long)L.nx * L.ny), 256, st, L, buf, rho0, rho,
-                 ux, uy, bx, by);
-    return cudaGetLastError();
+    return launch_fields_t(L, prec, buf, rho0, rho, ux, uy, bx, by, st);
+}
+
+cudaError_t launch_fields(const Layout& L, int prec, const void* buf, double rho0, float* rho, float* ux,
+                          float* uy, float* bx, float* by, cudaStream_t st) {
+    return launch_fields_t(L, prec, buf, rho0, rho, ux, uy, bx, by, st);
 }
 
 cudaError_t launch_unstream(const Layout& L, int prec, void* buf, const float* F, cudaStream_t st) {

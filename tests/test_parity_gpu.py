@@ -262,6 +262,38 @@ def test_graph_and_single_launches_agree():
     np.testing.assert_array_equal(ga, gb)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16s"])
+def test_fp32_field_calls_match_the_fp64_ones(prec):
+    """mhd_set_fields_f32 sets, bit for bit, the state mhd_set_fields sets for
+    the same values held as double; mhd_get_fields_f32 returns the FP64
+    fields of mhd_get_fields rounded to float, element by element; both
+    reject what the FP64 calls reject (non-finite fields, rho <= 0)."""
+    import mhd_inputs
+    from paper_2602_14667_gb300 import Lattice, MhdError
+    nx, ny = 96, 40
+    u = [a.astype(np.float32) for a in mhd_inputs.random_spectrum(nx, ny, 5, 0.04, 0.04, kmax=6)]
+    rho = (1.0 + 0.25 * u[0]).astype(np.float32)
+    with Lattice(nx, ny, 0.55, 0.6, precision=prec) as a, Lattice(nx, ny, 0.55, 0.6, precision=prec) as b:
+        a.set_fields(*u, rho=rho)
+        b.set_fields(*[v.astype(np.float64) for v in u], rho=rho.astype(np.float64))
+        assert np.array_equal(a.get_state(), b.get_state())
+        a.set_fields(*u)
+        b.set_fields(*[v.astype(np.float64) for v in u])
+        assert np.array_equal(a.get_state(), b.get_state())
+        a.advance(7)
+        f64 = a.get_fields()
+        f32 = a.get_fields(dtype=np.float32)
+        for k, v in f64.items():
+            assert f32[k].dtype == np.float32 and np.array_equal(f32[k], v.astype(np.float32)), k
+        bad = u[2].copy()
+        bad[3, 5] = np.inf
+        with pytest.raises(MhdError, match="EINVAL"):
+            a.set_fields(u[0], u[1], bad, u[3])
+        with pytest.raises(MhdError, match="EINVAL"):
+            a.set_fields(*u, rho=np.zeros_like(rho))
+        assert np.array_equal(a.get_fields(dtype=np.float32)["ux"], f32["ux"])  # state untouched
+
+
 def test_checkpoint_restart_is_bitwise():
     n = 64
     fields = _ot(n)
