@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="ot4096", choices=["ot4096", "ensemble", "closure", "closure_step", "diagnostics", "training"],
+    ap.add_argument("--workload", default="ot4096", choices=["ot4096", "ensemble", "closure", "closure_step", "diagnostics", "training", "slabs"],
                     help="ot4096: the headline single lattice; ensemble: 512 random-spectrum "
                          "lattices in one persistent launch per step; closure: the learned-closure "
                          "study; closure_step: the closure step's cost; diagnostics: the global "
@@ -837,6 +837,64 @@ def run_diagnostics(args):
     print(json.dumps(out), flush=True)
 
 
+def run_slabs(args):
+    """Cost of the row-slab decomposition of one lattice on one GPU: the
+    Orszag-Tang lattice (4096^2 FP32 by default) advanced whole and as S = 2
+    and 4 slabs of equal rows (bc_y = MHD_HALO), every slab on the same
+    stream: each step is the fused step of every slab, then the exchange of
+    the boundary-crossing rows of every boundary (mhd_slab_exchange: one
+    copy kernel per direction).  CUDA events around `steps` steps; the
+    exchanges alone are timed the same way.  The slabs' populations equal
+    the whole lattice's bit for bit (tests/test_slabs_gpu.py)."""
+    import torch
+
+    import mhd_inputs
+    from paper_2602_14667_gb300 import Lattice
+    from paper_2602_14667_gb300.slabs import SlabGroup
+    torch.cuda.set_device(0)
+    n, prec, tau = args.n, args.precision, 0.50006
+    stream = torch.cuda.Stream()
+    fields = mhd_inputs.orszag_tang(n, 0.04, 0.04)
+
+    def timed(fn, reps):
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {}
+    with Lattice(n, n, tau, tau, precision=prec, stream=stream.cuda_stream) as lat:
+        lat.set_fields(*fields)
+        shape = lat.kernel_config
+        lat.advance(args.warmup)
+        # single launches, as the slabs step (no 64-step graphs)
+        out["whole"] = {"ms_per_step": timed(lambda: lat.advance(1), args.steps)}
+    with ClockSampler(0) as clk:
+        for S in (2, 4):
+            with SlabGroup(n, n, S, tau, tau, precision=prec, stream=stream.cuda_stream) as sg:
+                sg.kernel_config = shape
+                sg.set_fields(*fields)
+                sg.advance(args.warmup)
+                ms = timed(lambda: sg.advance(1), args.steps)
+                ex = timed(sg.exchange, args.steps)
+            out[f"slabs_{S}"] = {"ms_per_step": ms, "exchange_us_per_step": ex * 1e3,
+                                 "overhead_vs_whole": ms / out["whole"]["ms_per_step"] - 1}
+    for v in out.values():
+        v["mlups"] = n * n / (v["ms_per_step"] * 1e-3) / 1e6
+    res = {"metric": f"row-slab decomposition on one GPU ({n}^2 {prec})", "value": out["slabs_2"]["mlups"],
+           "unit": "MLUPS (2 slabs)", "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "dtype": DTYPE[prec], "data": "synthetic",
+           "config": {"workload": f"slabs_orszag_tang_{n}x{n}_{prec}", "kernel_config": list(shape),
+                      "stream": "all slabs on one stream; single step launches"},
+           "runs": out, "clocks": clk.summary()}
+    print(json.dumps(res), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -851,6 +909,8 @@ def main():
         run_diagnostics(args)
     elif args.workload == "training":
         run_training(args)
+    elif args.workload == "slabs":
+        run_slabs(args)
     else:
         run_gb300(args)
 

@@ -784,12 +784,24 @@ mhd_status mhd_slab_exchange(mhd_lattice* lower, mhd_lattice* upper, int all_pla
     CK(cudaEventRecord(upper->xev, upper->stream), "exchange event");
     const size_t es = lower->L.esize, row = (size_t)lower->nx * es;
     // from `from`'s interior row `src_row` into `to`'s row `dst_row` (-1 or
-    // ny: a ghost row), the planes whose c_y equals `cy` (all with all_planes)
+    // ny: a ghost row), the planes whose c_y equals `cy` (all with all_planes):
+    // on one device one copy kernel for all of them (whole padded rows: the
+    // row pitch is a multiple of 128 bytes), across devices one copy each
     auto copy = [&](mhd_lattice* from, int src_row, mhd_lattice* to, int dst_row, int cy) -> mhd_status {
         CK(cudaSetDevice(to->dev), "cudaSetDevice");
         CK(cudaStreamWaitEvent(to->stream, from->xev, 0), "exchange wait");
         const char* sb = static_cast<const char*>(from->buf[from->cur]);
         char* db = static_cast<char*>(to->buf[to->cur]);
+        if (from->dev == to->dev) {
+            mhd::HaloPlanes hp{};
+            for (int p = 0; p < mhd::kStatePlanes; ++p)
+                if (all_planes || mhd::pcy(p) == cy) hp.p[hp.n++] = p;
+            const long long pb = (long long)from->L.pitch * (long long)es;
+            CK(mhd::launch_halo_rows(sb, db, from->L.plane * (long long)es, to->L.plane * (long long)es,
+                                     (long long)src_row * pb, (long long)dst_row * pb, pb, hp, to->stream),
+               "halo copy kernel");
+            return MHD_OK;
+        }
         for (int p = 0; p < mhd::kStatePlanes; ++p) {
             if (!all_planes && mhd::pcy(p) != cy) continue;
             const char* src = sb + ((long long)p * from->L.plane + (long long)src_row * from->L.pitch) * (long long)es;

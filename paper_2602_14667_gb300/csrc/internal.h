@@ -51,6 +51,16 @@ cudaError_t launch_fields(const Layout& L, int prec, const void* buf, double rho
                           double* ux, double* uy, double* bx, double* by, cudaStream_t st);
 cudaError_t launch_fields(const Layout& L, int prec, const void* buf, double rho0, float* rho, float* ux,
                           float* uy, float* bx, float* by, cudaStream_t st);
+// planes of one slab exchange (up to all 19)
+struct HaloPlanes {
+    int p[kStatePlanes];
+    int n;
+};
+// one launch for the row copies of a slab exchange on one device (see
+// halo_rows_kernel); cudaErrorInvalidValue unless every size, offset and
+// base address is a multiple of 16 bytes
+cudaError_t launch_halo_rows(const void* src, void* dst, long long src_plane, long long dst_plane, long long src_off,
+                             long long dst_off, long long bytes, const HaloPlanes& hp, cudaStream_t st);
 // stored state whose pull-gather reproduces the packed FP32 pre-collision
 // state F (periodic axes)
 cudaError_t launch_unstream(const Layout& L, int prec, void* buf, const float* F, cudaStream_t st);

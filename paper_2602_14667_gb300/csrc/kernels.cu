@@ -318,6 +318,34 @@ cudaError_t launch_fields(const Layout& L, int prec, const void* buf, double rho
     return launch_fields_t(L, prec, buf, rho0, rho, ux, uy, bx, by, st);
 }
 
+// The row copies of a slab exchange on one device: for each listed plane p,
+// `bytes` from src + p * src_plane + src_off to dst + p * dst_plane +
+// dst_off, in 16-byte pieces (every address and size a multiple of 16).
+__global__ void halo_rows_kernel(const char* __restrict__ src, char* __restrict__ dst, long long src_plane,
+                                 long long dst_plane, long long src_off, long long dst_off, long long bytes,
+                                 HaloPlanes hp) {
+    const long long n16 = bytes / 16;
+    for (int j = blockIdx.y; j < hp.n; j += gridDim.y) {
+        const long long p = hp.p[j];
+        const uint4* s = reinterpret_cast<const uint4*>(src + p * src_plane + src_off);
+        uint4* d = reinterpret_cast<uint4*>(dst + p * dst_plane + dst_off);
+        for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n16;
+             k += (long long)gridDim.x * blockDim.x)
+            d[k] = s[k];
+    }
+}
+
+cudaError_t launch_halo_rows(const void* src, void* dst, long long src_plane, long long dst_plane, long long src_off,
+                             long long dst_off, long long bytes, const HaloPlanes& hp, cudaStream_t st) {
+    if (hp.n < 1 || hp.n > kStatePlanes || bytes % 16 || src_plane % 16 || dst_plane % 16 || src_off % 16 ||
+        dst_off % 16 || reinterpret_cast<uintptr_t>(src) % 16 || reinterpret_cast<uintptr_t>(dst) % 16)
+        return cudaErrorInvalidValue;
+    const long long bx = std::max(1LL, std::min((bytes / 16 + 255) / 256, 64LL));
+    halo_rows_kernel<<<dim3((unsigned)bx, (unsigned)hp.n), 256, 0, st>>>(
+        static_cast<const char*>(src), static_cast<char*>(dst), src_plane, dst_plane, src_off, dst_off, bytes, hp);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_unstream(const Layout& L, int prec, void* buf, const float* F, cudaStream_t st) {
     MHD_DISPATCH(prec, unstream_kernel, flat_grid((long long)L.nx * L.ny), 256, st, L, buf, F);
     return cudaGetLastError();
