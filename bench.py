@@ -94,9 +94,9 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-# The device code of the step kernels: kernels.cu and the device headers it
+# The device code of the step kernels: step.cu and the device headers it
 # includes (internal.h holds only host declarations).
-STEP_KERNEL_SOURCES = ("f32x2.cuh", "kernels.cu", "lbm_device.cuh", "step_row.cuh")
+STEP_KERNEL_SOURCES = ("f32x2.cuh", "lbm_device.cuh", "step.cu", "step_row.cuh")
 DIAG_KERNEL_SOURCES = ("diag.cu", "f32x2.cuh", "lbm_device.cuh", "step_row.cuh")
 
 
@@ -300,7 +300,14 @@ def extra_rows(fp32_mlups, peak):
                 Orszag-Tang vortex at tau = 0.51 after 1000 steps against
                 an FP64 run of the same lattice (relative L2 of u and b);
       ensemble  the 512-lattice random-spectrum ensemble (39 M nodes) in one
-                persistent launch per step (100 steps)."""
+                persistent launch per step (100 steps);
+      diagnostics, closure_step, closure
+                the --workload lines of the global totals (4096^2 FP32,
+                100 calls), of the closure step's cost (512^2, 512 steps) and
+                of the learned-closure study (2048^2 -> 512^2, the closure
+                against plain 512^2, the untrained control and the plain
+                grid of equal GPU time, the MLP on every 1st / 4th / 8th
+                step), the last in compact form."""
     import numpy as np
     import torch
 
@@ -359,6 +366,26 @@ def extra_rows(fp32_mlups, peak):
                        "kernel_config": list(bshape),
                        "roofline": {"bound": "hbm", "achieved": gbsb, "peak": peak, "unit": "GB/s",
                                     "frac": gbsb / peak, "bytes_per_node": 152}}
+    d = diagnostics_line(4096, "fp32", 100, 3)
+    out["diagnostics"] = {k: d[k] for k in ("metric", "value", "unit", "ms_per_call", "config", "roofline")}
+    c = closure_step_line(512, 512, 64)
+    out["closure_step"] = {k: c[k] for k in ("metric", "value", "unit", "ms_per_step", "config", "roofline")}
+    cl = closure_line()
+    et = cl["equal_gpu_time"]
+    grid = et["plain_grid"]
+    out["closure"] = {
+        "metric": cl["metric"], "workload": cl["config"]["workload"], "checkpoints": cl["config"]["checkpoints"],
+        "closure_arm": cl["closure_arm"], "amplitude": cl["config"]["amplitude"],
+        "errors": "per checkpoint: [energy-spectrum error, current-density error]",
+        "closure_512": et["errors"]["closure_512"], "plain_512": et["errors"]["plain_512"],
+        "untrained_control_512": et["errors"]["untrained_512"],
+        "equal_gpu_time": {"plain_grid": grid, "errors": et["errors"]["plain_grid"], "gpu_s": et["gpu_s"],
+                           "plain_grid_gpu_s": et["plain_grid_gpu_s"]},
+        "closure_interval": {k: {"cost_vs_plain_512": v["cost_vs_plain_512"], "amplitude": v["amplitude"],
+                                 "errors": v["errors"], "equal_time_plain_grid": v["equal_time_plain_grid"],
+                                 "equal_time_plain_errors": v["equal_time_plain_errors"]}
+                             for k, v in cl["closure_interval"].items()},
+        "training": cl["training"], "wall_s": cl["wall_s"]}
     return out
 
 
@@ -604,6 +631,10 @@ def training_rate(res):
 
 
 def run_closure(args):
+    print(json.dumps(closure_line()), flush=True)
+
+
+def closure_line():
     """The learned-closure workload: 2048^2 fine runs (random-spectrum fields,
     rms 0.03) filtered 4x onto 512^2; MLP trained on the GPU on ~2 M samples
     from two seeds, amplitude calibrated on one of them, coarse closure and
@@ -674,10 +705,14 @@ def run_closure(args):
                                  for k, v in res["intervals"].items()},
            "training": training_rate(res),
            "wall_s": wall}
-    print(json.dumps(out), flush=True)
+    return out
 
 
 def run_closure_step(args):
+    print(json.dumps(closure_step_line(args.n if args.n != 4096 else 512, args.steps, args.warmup)), flush=True)
+
+
+def closure_step_line(n, steps, warmup):
     """Cost of the closure step alone: an n^2 FP32 lattice (512^2 unless --n
     names another size; random-spectrum fields, tau 0.505) advanced with the plain step and with the closure step
     (an untrained network: the MLP cost does not depend on the weights),
@@ -687,7 +722,6 @@ def run_closure_step(args):
     import mhd_inputs
     from paper_2602_14667_gb300 import Lattice, _abi
     torch.cuda.set_device(0)
-    n = args.n if args.n != 4096 else 512
     stream = torch.cuda.Stream()
     fields = mhd_inputs.random_spectrum(n, n, 7, 0.03, 0.03)
     out = {}
@@ -702,15 +736,15 @@ def run_closure_step(args):
                 _abi.set_closure_kernel(lat, _abi.MHD_CLOSURE_TCGEN05 if name == "closure_tcgen05"
                                         else _abi.MHD_CLOSURE_WARP_MMA)
             lat.set_fields(*fields)
-            lat.advance(args.warmup)
+            lat.advance(warmup)
             stream.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            lat.advance(args.steps)
+            lat.advance(steps)
             e1.record(stream)
             e1.synchronize()
-            out[name] = e0.elapsed_time(e1) / args.steps
+            out[name] = e0.elapsed_time(e1) / steps
     mlp.close()
     # Dominant kernel: step_closure.  Its algorithmic work is the MLP,
     # 24x64 + 64x64 + 64x3 multiply-adds = 11,648 flop per node (BF16 tensor
@@ -728,11 +762,11 @@ def run_closure_step(args):
            "config": {"workload": f"closure_step_{n}x{n}_fp32", "tau": 0.505,
                       "closure_kernel": "warp_mma" if best_kind == "closure" else "tcgen05"},
            "data": "synthetic",
-           "steps": args.steps, "warmup": args.warmup,
+           "steps": steps, "warmup": warmup,
            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                         "frac": achieved / peak, "peak_source": "measured bf16 dense (burst)",
                         "flops_per_node": flops // (n * n), "traffic": None}}
-    print(json.dumps(res), flush=True)
+    return res
 
 
 def run_training(args):
@@ -785,6 +819,10 @@ def run_training(args):
 
 
 def run_diagnostics(args):
+    print(json.dumps(diagnostics_line(args.n, args.precision, args.steps, args.warmup)), flush=True)
+
+
+def diagnostics_line(n, prec, steps, warmup):
     """Cost of the global diagnostics (mass, momentum, energies, cross
     helicity, sum b, div b rms / max, current-density and vorticity maxima):
     the Orszag-Tang lattice (4096^2 FP32 by default) after `warmup` steps,
@@ -800,23 +838,22 @@ def run_diagnostics(args):
     import mhd_inputs
     from paper_2602_14667_gb300 import Lattice
     torch.cuda.set_device(0)
-    n, prec = args.n, args.precision
     stream = torch.cuda.Stream()
     nodes = n * n
     with Lattice(n, n, 0.50006, 0.50006, precision=prec, stream=stream.cuda_stream) as lat:
         lat.set_fields(*mhd_inputs.orszag_tang(n, 0.04, 0.04))
-        lat.advance(max(args.warmup, 1))
+        lat.advance(max(warmup, 1))
         for _ in range(3):
             lat.get_totals()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         with ClockSampler(0) as clk:
             e0.record(stream)
-            for _ in range(args.steps):
+            for _ in range(steps):
                 tot = lat.get_totals()
             e1.record(stream)
             e1.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
+        ms = e0.elapsed_time(e1) / steps
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
         peak = float(json.load(fh)["hbm_gbs"])
     per_node = 19 * ESIZE[prec]
@@ -828,13 +865,13 @@ def run_diagnostics(args):
                 "traffic": None if dram is None else dram * nodes,
                 "note": "per call, including the final reduction, the D2H copy and the host wait"}
     out = {"metric": "global diagnostics rate", "value": nodes / (ms * 1e-3) / 1e6, "unit": "Mnodes/s",
-           "ms_per_call": ms, "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "dtype": DTYPE[prec] + " (f64 sums)", "data": "synthetic",
+           "ms_per_call": ms, "higher_is_better": True, "n_gpus": 1, "steps": steps,
+           "warmup": warmup, "dtype": DTYPE[prec] + " (f64 sums)", "data": "synthetic",
            "config": {"workload": f"diagnostics_orszag_tang_{n}x{n}_{prec}", "nx": n, "ny": n,
-                      "calls": args.steps, "l2": "no flush: the state is far above the 129 MB L2"},
+                      "calls": steps, "l2": "no flush: the state is far above the 129 MB L2"},
            "totals_sample": {"mass": tot["mass"], "divb_max": tot["divb_max"], "jz_max": tot["jz_max"]},
-           "clocks": clk.summary(), "gpu_launches": 2 * args.steps, "roofline": roofline}
-    print(json.dumps(out), flush=True)
+           "clocks": clk.summary(), "gpu_launches": 2 * steps, "roofline": roofline}
+    return out
 
 
 def run_slabs(args):
