@@ -74,6 +74,31 @@ def combine_totals(parts, nx: int, wall_x: bool = False) -> dict:
     return out
 
 
+def allreduce_totals(totals: dict, rows: int, nx: int, wall_x: bool = False, group=None) -> dict:
+    """The whole lattice's totals when each rank of a torch.distributed
+    group holds one slab (its own totals and row count): combine_totals as
+    two FP64 all-reduces, one SUM (the sums, the node-weighted means, the
+    weighted squares of the rms of div b and the node counts) and one MAX
+    (the maxima)."""
+    import torch
+    import torch.distributed as dist
+    nodes = nx * rows
+    nvalid = (nx - 2 if wall_x else nx) * rows
+    s = torch.tensor([float(totals[k]) for k in SUMS] + [totals[k] * nodes for k in MEANS]
+                     + [totals["divb_rms"] ** 2 * nvalid, float(nodes), float(nvalid)], dtype=torch.float64)
+    m = torch.tensor([float(totals[k]) for k in MAXIMA], dtype=torch.float64)
+    dist.all_reduce(s, op=dist.ReduceOp.SUM, group=group)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX, group=group)
+    s, m = s.tolist(), m.tolist()
+    ns, nm = len(SUMS), len(MEANS)
+    out = dict(zip(SUMS, s[:ns]))
+    out.update({k: s[ns + i] / s[-2] for i, k in enumerate(MEANS)})
+    out.update(zip(MAXIMA, m))
+    out["divb_rms"] = math.sqrt(s[ns + nm] / s[-1]) if s[-1] else 0.0
+    out["step"] = totals["step"]
+    return out
+
+
 class SlabGroup:
     """The slabs of one nx x ny lattice with a periodic y axis, all on the
     current device: every step advances each slab and then exchanges every

@@ -150,3 +150,49 @@ def test_two_gloo_ranks_reproduce_the_whole_lattice_bitwise(orc):
     f, g = orc.run(p, f, g, STEPS)
     whole = np.concatenate([f, g.reshape(10, NY, NX)])
     assert np.array_equal(np.concatenate(bands, axis=1), whole)
+
+
+_PARTS = (dict(mass=10.0, mom_x=1.0, mom_y=2.0, bsum_x=0.5, bsum_y=0.25, e_kin=1.0, e_mag=2.0, cross_hel=3.0,
+               divb_max=0.1, jz_max=0.2, omega_max=0.3, divb_rms=1.0, step=7),
+          dict(mass=30.0, mom_x=-1.0, mom_y=1.0, bsum_x=0.5, bsum_y=0.75, e_kin=3.0, e_mag=0.0, cross_hel=-1.0,
+               divb_max=0.4, jz_max=0.1, omega_max=0.2, divb_rms=2.0, step=7))
+_ROWS = (1, 3)
+
+
+def _totals_worker(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    from paper_2602_14667_gb300 import slabs
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    for wall_x in (False, True):
+        t = slabs.allreduce_totals(_PARTS[rank], _ROWS[rank], nx=4, wall_x=wall_x)
+        out[(rank, wall_x)] = t
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_allreduce_totals_on_two_gloo_ranks_equals_combine_totals():
+    """One slab per rank: the two FP64 all-reduces give every rank the
+    totals combine_totals forms from all the slabs' totals."""
+    from paper_2602_14667_gb300 import slabs
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        procs = [ctx.Process(target=_totals_worker, args=(r, world, port, out)) for r in range(world)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(180)
+            assert p.exitcode == 0
+        got = dict(out)
+    for wall_x in (False, True):
+        want = slabs.combine_totals(list(zip(_PARTS, _ROWS)), nx=4, wall_x=wall_x)
+        for r in range(world):
+            t = got[(r, wall_x)]
+            assert set(t) == set(want)
+            for k, v in want.items():
+                assert abs(t[k] - v) <= 1e-15 * max(1.0, abs(v)), (r, wall_x, k, t[k], v)
