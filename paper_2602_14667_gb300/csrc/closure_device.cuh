@@ -51,6 +51,14 @@ __device__ __forceinline__ uint32_t ld11(const bf16* lo, const bf16* hi) {
     return (uint32_t)__bfloat16_as_ushort(*lo) | ((uint32_t)__bfloat16_as_ushort(*hi) << 16);
 }
 
+// relu(lo), relu(hi) rounded to BF16 (nearest even) and packed: lo in the
+// low half, as the next layer's A fragment wants it.
+__device__ __forceinline__ uint32_t relu_pack2(float lo, float hi) {
+    uint32_t u;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;\n" : "=r"(u) : "f"(hi), "f"(lo));
+    return u;
+}
+
 // ---- feature stencils -------------------------------------------------------
 // s[q][r][c] holds q in (u_x, u_y, b_x, b_y) for a tile plus a one-node
 // halo; (r, c) = (ly + 1, lx + 1) is the node.
@@ -108,6 +116,25 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+
+// d_x, d_y (isotropic gradient), the 9-point Laplacian and d_xy of the four
+// fields (u_x, u_y, b_x, b_y) at the lane's node, from w[r][q] with slot 1
+// the node's row and slots 2 / 0 the rows on either side (sgn = +1 when
+// slot 2 is the row above, -1 when it is the row below); x neighbours come
+// from the neighbouring lanes.  Same stencils as stencil_features.
+__device__ __forceinline__ void stencil_rows(const float (&w)[3][4], float sgn, float* out16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float C = w[1][q], N = w[2][q], S = w[0][q];
+        const float E = __shfl_down_sync(kFull, C, 1), W = __shfl_up_sync(kFull, C, 1);
+        const float NE = __shfl_down_sync(kFull, N, 1), NW = __shfl_up_sync(kFull, N, 1);
+        const float SE = __shfl_down_sync(kFull, S, 1), SW = __shfl_up_sync(kFull, S, 1);
+        out16[4 * q + 0] = (1.0f / 3.0f) * (E - W) + (1.0f / 12.0f) * ((NE - NW) + (SE - SW));
+        out16[4 * q + 1] = sgn * ((1.0f / 3.0f) * (N - S) + (1.0f / 12.0f) * ((NE - SE) + (NW - SW)));
+        out16[4 * q + 2] = (4.0f * ((E + W) + (N + S)) + ((NE + NW) + (SE + SW)) - 20.0f * C) * (1.0f / 6.0f);
+        out16[4 * q + 3] = sgn * (0.25f * ((NE - NW) - (SE - SW)));
+    }
+}
 
 // Ring position h (0..83) of a tile: top row (34), bottom row (34), left
 // column (8), right column (8), as (column, row) of the 34 x 10 halo tile.

@@ -60,14 +60,6 @@ static_assert(offsetof(RowsShared, b1) % 8 == 0 && offsetof(RowsShared, b2) % 8 
                   offsetof(RowsShared, b3) % 8 == 0,
               "bias pairs are read as float2");
 
-// relu(lo), relu(hi) rounded to BF16 (nearest even) and packed: lo in the
-// low half, as the next layer's A fragment wants it.
-__device__ __forceinline__ uint32_t relu_pack2(float lo, float hi) {
-    uint32_t u;
-    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;\n" : "=r"(u) : "f"(hi), "f"(lo));
-    return u;
-}
-
 // MLP of the warp's 32 feature rows (two M tiles sharing every B fragment);
 // out_scale * y into da.
 __device__ __forceinline__ void mlp32(const RowsShared& sh, const bf16* feat, float (*da)[4], int lane) {
@@ -144,25 +136,6 @@ __device__ __forceinline__ void mlp32(const RowsShared& sh, const bf16* feat, fl
             da[16 * mt + g][2 * t + 1] = d[mt][1] * sh.out_scale[2 * t + 1];
             da[16 * mt + g + 8][2 * t + 1] = d[mt][3] * sh.out_scale[2 * t + 1];
         }
-    }
-}
-
-// d_x, d_y (isotropic gradient), the 9-point Laplacian and d_xy of the four
-// fields (u_x, u_y, b_x, b_y) at the lane's node, from w[r][q] with slot 1
-// the node's row and slots 2 / 0 the rows on either side (sgn = +1 when
-// slot 2 is the row above, -1 when it is the row below); x neighbours come
-// from the neighbouring lanes.  Same stencils as stencil_features.
-__device__ __forceinline__ void stencil_rows(const float (&w)[3][4], float sgn, float* out16) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float C = w[1][q], N = w[2][q], S = w[0][q];
-        const float E = __shfl_down_sync(kFull, C, 1), W = __shfl_up_sync(kFull, C, 1);
-        const float NE = __shfl_down_sync(kFull, N, 1), NW = __shfl_up_sync(kFull, N, 1);
-        const float SE = __shfl_down_sync(kFull, S, 1), SW = __shfl_up_sync(kFull, S, 1);
-        out16[4 * q + 0] = (1.0f / 3.0f) * (E - W) + (1.0f / 12.0f) * ((NE - NW) + (SE - SW));
-        out16[4 * q + 1] = sgn * ((1.0f / 3.0f) * (N - S) + (1.0f / 12.0f) * ((NE - SE) + (NW - SW)));
-        out16[4 * q + 2] = (4.0f * ((E + W) + (N + S)) + ((NE + NW) + (SE + SW)) - 20.0f * C) * (1.0f / 6.0f);
-        out16[4 * q + 3] = sgn * (0.25f * ((NE - NW) - (SE - SW)));
     }
 }
 

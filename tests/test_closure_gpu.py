@@ -321,6 +321,35 @@ def test_closure_step_matches_oracle(orc, kind):
 
 
 @KINDS
+def test_closure_step_matches_oracle_on_tall_ragged_tiles(orc, kind):
+    """A lattice whose tiles are several rows tall with a shorter last row
+    segment and a narrow last strip (968 x 200: on a 152-SM GPU 33 strips of
+    30 columns, the last of 8, and row segments of 3 rows, the last of 2;
+    the tensor-core kernel's last warpgroup then has a warp without a tile):
+    one closure step matches the oracle node by node."""
+    from oracle import closure as clo
+    from paper_2602_14667_gb300 import Lattice, _abi
+    nx, ny = 968, 200
+    p, f, g = _state(orc, nx, ny, 11, steps=2)
+    st = _packed(f, g)
+    f64, g64 = _unpacked(st, nx, ny)
+    Xo, _ = clo.features(p, f64, g64)
+    net = _random_net(clo, Xo, np.full((4, 3), 1.0), seed=7)
+    net.p["out_scale"][:] = 2e-5
+    with _abi.MLP(seed=0, max_batch=64) as m, Lattice(nx, ny, p.tau_f, p.tau_m, precision="fp32") as lat:
+        m.set_params(net.flat())
+        ref_net = clo.MLP.from_flat(m.get_params())
+        _abi.set_closure(lat, m)
+        _abi.set_closure_kernel(lat, kind)
+        _abi.set_precollision_state(lat, st)
+        lat.advance(1)
+        fg, gg = lat.get_populations()
+    da, _ = ref_net.forward(Xo, bf16_like_gpu=True)
+    fs, gs = orc.collide_da(p, f64, g64, da.reshape(ny, nx, 3))
+    assert np.abs(fg - fs).max() < 3e-6 and np.abs(gg - gs).max() < 2e-6, (np.abs(fg - fs).max(), np.abs(gg - gs).max())
+
+
+@KINDS
 def test_closure_keeps_mass_and_momentum(kind):
     import mhd_inputs
     from oracle import closure as clo
