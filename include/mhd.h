@@ -144,8 +144,11 @@ mhd_status mhd_create(int nx, int ny, const mhd_params* p, void* stream, mhd_lat
 /* Set the initial state: f = f_eq(rho, u, b) (Eq. feq_4th), g = g_eq(u, b),
  * i.e. zero non-equilibrium (a1^(2) = 0, so this is both the pre- and the
  * post-collision state at t = 0).  ux, uy, bx, by: host arrays of nx*ny;
- * rho may be NULL (rho = rho0).  Resets the step counter.  Non-finite input
- * -> MHD_EINVAL. */
+ * rho may be NULL (rho = rho0).  Resets the step counter.  Non-finite input,
+ * or rho <= 0 -> MHD_EINVAL and the state is left as it was.  The arrays
+ * are only read, and not after the call returns; pinned (page-locked)
+ * arrays of a two-buffer lattice are read in place by the device in one
+ * pass over the host link, other arrays through a device copy. */
 mhd_status mhd_set_fields(mhd_lattice* l, const double* ux, const double* uy, const double* bx,
                           const double* by, const double* rho);
 
@@ -155,7 +158,8 @@ mhd_status mhd_set_fields(mhd_lattice* l, const double* ux, const double* uy, co
 mhd_status mhd_advance(mhd_lattice* l, long long nsteps);
 
 /* Read the fields of the current state into host arrays of nx*ny (any of
- * them may be NULL).  Waits for the stream. */
+ * them may be NULL).  Waits for the stream.  Pinned (page-locked) arrays
+ * are written in place by the device, others through a device copy. */
 mhd_status mhd_get_fields(mhd_lattice* l, double* rho, double* ux, double* uy, double* bx,
                           double* by);
 

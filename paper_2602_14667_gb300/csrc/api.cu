@@ -356,14 +356,54 @@ mhd_status mhd_destroy(mhd_lattice* l) {
     return MHD_OK;
 }
 
+// Whether the device reads and writes host array p in place: pinned memory
+// mapped at the same address (a NULL optional array counts as mapped).
+static bool host_mapped(const void* p) {
+    if (!p) return true;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer == p;
+}
+
 // mhd_set_fields / mhd_set_fields_f32: T is the host (and device copy) type
-// of the fields, staged in the lattice's io buffer (5 x nx*ny doubles).
+// of the fields.  Pinned host arrays on a two-buffer lattice are read in
+// place by the initial-equilibrium kernel, which checks them on the way and
+// writes the other buffer (kept only if every value passed: one pass over
+// the host link); otherwise they are staged in the lattice's io buffer
+// (5 x nx*ny doubles), checked there, and then converted.
 extern "C++" {
 template <typename T>
 static mhd_status set_fields_t(mhd_lattice* l, const T* ux, const T* uy, const T* bx, const T* by, const T* rho) {
     if (!l || !ux || !uy || !bx || !by) return fail(MHD_EINVAL, "NULL argument");
     const long long n = l->n();
     CK(cudaSetDevice(l->dev), "cudaSetDevice");
+    if (!l->in_place && host_mapped(ux) && host_mapped(uy) && host_mapped(bx) && host_mapped(by) &&
+        host_mapped(rho)) {
+        int flags = 0;
+        CK(cudaMemsetAsync(l->flags_d, 0, sizeof(int), l->stream), "clear input flags");
+        CK(mhd::launch_init(l->L, l->p.precision, l->buf[l->cur ^ 1], rho, ux, uy, bx, by, l->p.rho0,
+                            l->p.eq_variant, l->stream, l->flags_d),
+           "init kernel");
+        CK(cudaMemcpyAsync(&flags, l->flags_d, sizeof(int), cudaMemcpyDeviceToHost, l->stream), "input flags");
+        CK(cudaStreamSynchronize(l->stream), "mhd_set_fields");
+        if (flags) {
+            // the state is unchanged, but the other buffer no longer holds
+            // the state the last step read
+            l->prev_valid = false;
+            return fail(MHD_EINVAL, (flags & 1) ? "non-finite input field" : "rho must be > 0");
+        }
+        l->cur ^= 1;
+        l->step = 0;
+        l->fields_set = true;
+        l->prev_valid = false;
+        l->closure_count = 0;  // the next closure step evaluates the MLP
+        l->state_is_eq = true;
+        l->aa_streamed = false;
+        return MHD_OK;
+    }
     mhd_status s = ensure_io(l);
     if (s != MHD_OK) return s;
     const size_t bytes = sizeof(T) * n;
@@ -493,6 +533,9 @@ mhd_status mhd_advance(mhd_lattice* l, long long nsteps) {
 }
 
 extern "C++" {
+// mhd_get_fields / mhd_get_fields_f32: pinned host arrays are written in
+// place by the fields kernel (one pass over the host link); others through
+// the io buffer and a copy.
 template <typename T>
 static mhd_status get_fields_t(mhd_lattice* l, T* rho, T* ux, T* uy, T* bx, T* by) {
     if (!l) return fail(MHD_EINVAL, "lattice is NULL");
@@ -502,6 +545,12 @@ static mhd_status get_fields_t(mhd_lattice* l, T* rho, T* ux, T* uy, T* bx, T* b
     {
         const mhd_status cs = closure_status(l);
         if (cs != MHD_OK) return cs;
+    }
+    if (host_mapped(rho) && host_mapped(ux) && host_mapped(uy) && host_mapped(bx) && host_mapped(by)) {
+        CK(mhd::launch_fields(l->L, l->p.precision, l->buf[l->cur], l->p.rho0, rho, ux, uy, bx, by, l->stream),
+           "fields kernel");
+        CK(cudaStreamSynchronize(l->stream), "mhd_get_fields");
+        return MHD_OK;
     }
     mhd_status s = ensure_io(l);
     if (s != MHD_OK) return s;

@@ -37,16 +37,18 @@ cudaError_t launch_step(const StepLaunch& s, cudaStream_t st);
 // is (V, BY) a legal launch shape for this lattice?
 bool step_shape_ok(const Layout& L, int prec, int wall_x, int V, int BY);
 
-// f = f_eq(rho, u, b), g = g_eq(u, b) from device FP64 (or FP32) fields
-// (rho may be null)
+// f = f_eq(rho, u, b), g = g_eq(u, b) from FP64 (or FP32) fields in device
+// memory or in mapped pinned host memory (rho may be null); with flags, the
+// input checks of mhd_set_fields OR-ed into *flags (the state is written
+// either way)
 cudaError_t launch_init(const Layout& L, int prec, void* buf, const double* rho, const double* ux,
                         const double* uy, const double* bx, const double* by, double rho0,
-                        int variant, cudaStream_t st);
+                        int variant, cudaStream_t st, int* flags = nullptr);
 cudaError_t launch_init(const Layout& L, int prec, void* buf, const float* rho, const float* ux,
                         const float* uy, const float* bx, const float* by, double rho0, int variant,
-                        cudaStream_t st);
+                        cudaStream_t st, int* flags = nullptr);
 // rho, u, b (FP64, or FP64 rounded to FP32; nx*ny each, any may be null)
-// of the stored state
+// of the stored state, into device memory or mapped pinned host memory
 cudaError_t launch_fields(const Layout& L, int prec, const void* buf, double rho0, double* rho,
                           double* ux, double* uy, double* bx, double* by, cudaStream_t st);
 cudaError_t launch_fields(const Layout& L, int prec, const void* buf, double rho0, float* rho, float* ux,

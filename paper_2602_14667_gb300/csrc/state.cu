@@ -24,23 +24,38 @@ __device__ __forceinline__ void encode_d(double v, __half& s) { s = __double2hal
 // compute type of the storage (FP64 for FP64, FP32 for FP32 and FP16S), as
 // the step evaluates its collision: on GB300 FP64 arithmetic would make
 // these memory-bound conversions bound by the FP64 units instead.
-// T: the type of the device field arrays (double, or float for the FP32
-// field calls: converted exactly to double or as the FP32 value).
+// T: the type of the field arrays (double, or float for the FP32 field
+// calls: converted exactly to double or as the FP32 value); they may live in
+// device memory or in pinned host memory mapped into the device's address
+// space (one pass over the host link).  flags (may be null): the input
+// checks of mhd_set_fields on the values read (bit 0 a non-finite field,
+// bit 1 rho <= 0 or non-finite); the state is written either way.
 template <int PREC, typename T>
 __global__ void init_kernel(Layout L, void* buf, const T* rho, const T* ux, const T* uy, const T* bx,
-                            const T* by, double rho0, int variant) {
+                            const T* by, double rho0, int variant, int* flags) {
     using S = typename Prec<PREC>::S;
     using C = typename Prec<PREC>::C;
     const long long n = (long long)L.nx * L.ny;
+    int fl = 0;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(k / L.nx), x = (int)(k % L.nx);
+        const T vx = ux[k], vy = uy[k], wx = bx[k], wy = by[k];
+        const double r = rho ? (double)rho[k] : rho0;
+        if (flags) {
+            if (!(isfinite(vx) && isfinite(vy) && isfinite(wx) && isfinite(wy))) fl |= 1;
+            if (rho) fl |= !isfinite(r) ? 1 : (r > 0 ? 0 : 2);
+        }
         C f[9], g[10];
-        equilibrium<C>(C(rho ? rho[k] : rho0), C(ux[k]), C(uy[k]), C(bx[k]), C(by[k]), C(rho0), variant, f, g);
+        equilibrium<C>(C(r), C(vx), C(vy), C(wx), C(wy), C(rho0), variant, f, g);
         S* b = static_cast<S*>(buf);
         const long long o = (long long)y * L.pitch + x;
         for (int i = 0; i < 9; ++i) encode(f[i], b[(long long)i * L.plane + o]);
         for (int q = 0; q < 10; ++q) encode(g[q], b[(long long)(9 + q) * L.plane + o]);
+    }
+    if (flags) {
+        fl = __reduce_or_sync(0xffffffffu, fl);
+        if ((threadIdx.x & 31) == 0 && fl) atomicOr(flags, fl);
     }
 }
 
@@ -154,9 +169,9 @@ static dim3 flat_grid(long long n) {
 
 template <typename T>
 static cudaError_t launch_init_t(const Layout& L, int prec, void* buf, const T* rho, const T* ux, const T* uy,
-                                 const T* bx, const T* by, double rho0, int variant, cudaStream_t st) {
+                                 const T* bx, const T* by, double rho0, int variant, cudaStream_t st, int* flags) {
     MHD_DISPATCH_T(prec, init_kernel, T, flat_grid((long long)L.nx * L.ny), 256, st, L, buf, rho, ux, uy, bx,
-                   by, rho0, variant);
+                   by, rho0, variant, flags);
     return cudaGetLastError();
 }
 
@@ -170,14 +185,14 @@ static cudaError_t launch_fields_t(const Layout& L, int prec, const void* buf, d
 
 cudaError_t launch_init(const Layout& L, int prec, void* buf, const double* rho, const double* ux,
                         const double* uy, const double* bx, const double* by, double rho0,
-                        int variant, cudaStream_t st) {
-    return launch_init_t(L, prec, buf, rho, ux, uy, bx, by, rho0, variant, st);
+                        int variant, cudaStream_t st, int* flags) {
+    return launch_init_t(L, prec, buf, rho, ux, uy, bx, by, rho0, variant, st, flags);
 }
 
 cudaError_t launch_init(const Layout& L, int prec, void* buf, const float* rho, const float* ux,
                         const float* uy, const float* bx, const float* by, double rho0, int variant,
-                        cudaStream_t st) {
-    return launch_init_t(L, prec, buf, rho, ux, uy, bx, by, rho0, variant, st);
+                        cudaStream_t st, int* flags) {
+    return launch_init_t(L, prec, buf, rho, ux, uy, bx, by, rho0, variant, st, flags);
 }
 
 cudaError_t launch_fields(const Layout& L, int prec, const void* buf, double rho0, double* rho,

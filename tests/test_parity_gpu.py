@@ -294,6 +294,50 @@ def test_fp32_field_calls_match_the_fp64_ones(prec):
         assert np.array_equal(a.get_fields(dtype=np.float32)["ux"], f32["ux"])  # state untouched
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16s"])
+def test_pinned_host_fields_are_read_and_written_in_place(prec):
+    """Pinned host arrays take the in-place path (the initial-equilibrium
+    kernel reads them over the host link, checks them and writes the spare
+    buffer; the fields kernel writes its output into them), pageable arrays
+    and in-place lattices the staging copy: the same state bit for bit and
+    the same fields, in float64 and float32.  A non-finite pinned input is
+    rejected with the state untouched, and the totals that follow are those
+    of that state (the spare buffer no longer holds the last step's input)."""
+    import torch
+
+    import mhd_inputs
+    from paper_2602_14667_gb300 import Lattice, MhdError
+    nx, ny = 96, 40
+    fields = list(mhd_inputs.random_spectrum(nx, ny, 5, 0.04, 0.04, kmax=6))
+    fields.append(1.0 + 0.25 * fields[0])
+    for tdt, ndt in ((torch.float64, np.float64), (torch.float32, np.float32)):
+        pin = [torch.empty((ny, nx), dtype=tdt).pin_memory() for _ in range(10)]
+        hp = [t.numpy() for t in pin]
+        for h, a in zip(hp, fields):
+            h[:] = a
+        hq = [np.ascontiguousarray(a, dtype=ndt) for a in fields]
+        with Lattice(nx, ny, 0.55, 0.6, precision=prec) as a, Lattice(nx, ny, 0.55, 0.6, precision=prec) as b, \
+                Lattice(nx, ny, 0.55, 0.6, precision=prec, in_place=True) as c:
+            a.set_fields(*hp[:4], rho=hp[4])
+            b.set_fields(*hq[:4], rho=hq[4])
+            c.set_fields(*hp[:4], rho=hp[4])
+            assert np.array_equal(a.get_state(), b.get_state()) and np.array_equal(a.get_state(), c.get_state())
+            a.advance(5)
+            b.advance(5)
+            fa = a.get_fields(out=hp[5:10])
+            fb = b.get_fields(dtype=ndt)
+            for k in fa:
+                assert np.array_equal(fa[k], fb[k]), k
+            s0 = a.get_state()
+            hp[2][3, 5] = np.nan
+            with pytest.raises(MhdError, match="EINVAL"):
+                a.set_fields(*hp[:4], rho=hp[4])
+            assert np.array_equal(a.get_state(), s0)
+            b.set_state(s0)  # the stored state alone, as a holds it now
+            assert a.get_totals() == b.get_totals()
+        del hp, pin
+
+
 def test_checkpoint_restart_is_bitwise():
     n = 64
     fields = _ot(n)
