@@ -68,7 +68,8 @@ def parse():
     ap.add_argument("--retune", action="store_true",
                     help="time every launch shape instead of using the autotuner's cache")
     ap.add_argument("--shape", default=None,
-                    help="fixed launch shape 'V,BY' (skips the autotuner; for profiling)")
+                    help="fixed launch shape 'V,BY' or 'V,BY,W' (W: resident warps per SM, the staging "
+                         "depth; skips the autotuner; for profiling)")
     ap.add_argument("--in-place", action="store_true",
                     help="ot4096 on one state buffer (in-place streaming) instead of two")
     ap.add_argument("--lattices", type=int, default=512,
@@ -125,8 +126,12 @@ def profiled(prec, shape, key, name=None, sources=STEP_KERNEL_SOURCES):
                 vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernel_source_sha") != kernel_source_hash(sources):
         return None
-    if shape is not None and vals.get("shape") != f"{shape[0]},{shape[1]}":
-        return None
+    if shape is not None:
+        # (nodes_per_thread, rows_per_block[, warps_per_sm]); a summary
+        # without a depth key was taken at the built-in depth (0)
+        depth = shape[2] if len(shape) > 2 else 0
+        if vals.get("shape") != f"{shape[0]},{shape[1]}" or vals.get("warps_per_sm", "0") != str(depth):
+            return None
     try:
         return float(vals[key])
     except (KeyError, ValueError):

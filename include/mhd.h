@@ -127,10 +127,18 @@ typedef struct {
  * updates with vector loads and stores: 1, 2 or 4 (at most 2 for MHD_FP64);
  * it must divide nx and must be 1 when the x axis has walls.
  * rows_per_block: warps per block, one row of 32*nodes_per_thread nodes
- * each: 1..16 (1..8 for MHD_FP64 and for MHD_FP16S with MHD_IN_PLACE). */
+ * each: 1..16 (1..8 for MHD_FP64 and for MHD_FP16S with MHD_IN_PLACE).
+ * warps_per_sm: the staging depth of the streamed neighbourhood -- how many
+ * row tiles (warps) the persistent grid keeps in flight per SM, and with
+ * them how many bytes of every plane are being loaded at once
+ * (warps_per_sm x 32 x nodes_per_thread elements): 0 for the built-in rule
+ * (about 4 KB of every plane per SM for FP32 and FP16S storage, every
+ * resident warp for FP64), else 1..64, rounded down to whole blocks and
+ * capped by what fits on an SM.  Ignored by the x-wall kernel. */
 typedef struct {
     int nodes_per_thread;
     int rows_per_block;
+    int warps_per_sm;
 } mhd_kernel_config;
 
 /* Create an nx x ny lattice on the current CUDA device.  The populations are
@@ -273,7 +281,10 @@ mhd_status mhd_get_kernel_config(const mhd_lattice* l, mhd_kernel_config* out);
 mhd_status mhd_set_kernel_config(mhd_lattice* l, const mhd_kernel_config* cfg);
 
 /* Autotune the launch shape: time every valid (nodes_per_thread,
- * rows_per_block) for this lattice with CUDA events and keep the fastest.
+ * rows_per_block) for this lattice with CUDA events at the built-in staging
+ * depth, then the fastest shape at other depths (warps_per_sm = 1/2, 3/4,
+ * 3/2 and 2 times the rule's), and keep the fastest (another depth only if
+ * it is at least 1 % faster).
  * The state is not advanced (candidates read the current buffer and write
  * the spare one).  Results are cached per (GPU, precision, nx, ny, bc) in
  * the JSON file named by $MHD_TUNE_CACHE (no caching when unset); a cached
@@ -307,8 +318,10 @@ mhd_status mhd_batch_get_fields(mhd_batch* b, int index, double* rho, double* ux
 mhd_status mhd_batch_get_totals(mhd_batch* b, int index, mhd_totals* out);
 /* total number of nodes over all lattices */
 mhd_status mhd_batch_nodes(const mhd_batch* b, long long* nodes);
-/* launch shape (nodes_per_thread must divide every nx); autotune times every
- * valid shape over the whole ensemble without advancing it */
+/* launch shape (nodes_per_thread must divide every nx; warps_per_sm 0 keeps
+ * every resident block, which the ensemble's many short rows want); autotune
+ * times every valid shape over the whole ensemble without advancing it,
+ * then the fastest at half and three quarters of the resident warps */
 mhd_status mhd_batch_get_kernel_config(const mhd_batch* b, mhd_kernel_config* out);
 mhd_status mhd_batch_set_kernel_config(mhd_batch* b, const mhd_kernel_config* cfg);
 mhd_status mhd_batch_autotune(mhd_batch* b, mhd_kernel_config* best);

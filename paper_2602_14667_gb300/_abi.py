@@ -42,7 +42,21 @@ class mhd_totals(ctypes.Structure):
 
 
 class mhd_kernel_config(ctypes.Structure):
-    _fields_ = [("nodes_per_thread", ctypes.c_int), ("rows_per_block", ctypes.c_int)]
+    _fields_ = [("nodes_per_thread", ctypes.c_int), ("rows_per_block", ctypes.c_int),
+                ("warps_per_sm", ctypes.c_int)]
+
+
+def _shape_in(v) -> "mhd_kernel_config":
+    """(nodes_per_thread, rows_per_block[, warps_per_sm]) -> the C struct;
+    a two-number shape keeps the built-in staging depth (warps_per_sm 0)."""
+    v = tuple(int(x) for x in v)
+    if len(v) not in (2, 3):
+        raise ValueError("a launch shape is (nodes_per_thread, rows_per_block[, warps_per_sm])")
+    return mhd_kernel_config(v[0], v[1], v[2] if len(v) == 3 else 0)
+
+
+def _shape_out(c: "mhd_kernel_config"):
+    return c.nodes_per_thread, c.rows_per_block, c.warps_per_sm
 
 
 class MhdError(RuntimeError):
@@ -268,17 +282,17 @@ class Lattice:
     def kernel_config(self):
         c = mhd_kernel_config()
         check(lib().mhd_get_kernel_config(self._h, ctypes.byref(c)), "mhd_get_kernel_config")
-        return c.nodes_per_thread, c.rows_per_block
+        return _shape_out(c)
 
     @kernel_config.setter
     def kernel_config(self, v):
-        c = mhd_kernel_config(int(v[0]), int(v[1]))
+        c = _shape_in(v)
         check(lib().mhd_set_kernel_config(self._h, ctypes.byref(c)), "mhd_set_kernel_config")
 
     def autotune(self):
         c = mhd_kernel_config()
         check(lib().mhd_autotune(self._h, ctypes.byref(c)), "mhd_autotune")
-        return c.nodes_per_thread, c.rows_per_block
+        return _shape_out(c)
 
 
 def slab_exchange(lower: "Lattice", upper: "Lattice", all_planes: bool = False) -> None:
@@ -379,17 +393,17 @@ class Batch:
     def kernel_config(self):
         c = mhd_kernel_config()
         check(lib().mhd_batch_get_kernel_config(self._h, ctypes.byref(c)), "mhd_batch_get_kernel_config")
-        return c.nodes_per_thread, c.rows_per_block
+        return _shape_out(c)
 
     @kernel_config.setter
     def kernel_config(self, v):
-        c = mhd_kernel_config(int(v[0]), int(v[1]))
+        c = _shape_in(v)
         check(lib().mhd_batch_set_kernel_config(self._h, ctypes.byref(c)), "mhd_batch_set_kernel_config")
 
     def autotune(self):
         c = mhd_kernel_config()
         check(lib().mhd_batch_autotune(self._h, ctypes.byref(c)), "mhd_batch_autotune")
-        return c.nodes_per_thread, c.rows_per_block
+        return _shape_out(c)
 
 
 MLP_PARAMS = 6006

@@ -128,6 +128,7 @@ mhd::StepLaunch step_launch(const mhd_lattice* l, int from) {
     s.wall_y = l->p.bc_y == MHD_WALL;
     s.V = l->cfg.nodes_per_thread;
     s.BY = l->cfg.rows_per_block;
+    s.W = l->cfg.warps_per_sm;
     if (l->halo) {
         // A slab steps as a periodic lattice of its ny + 2 rows: rows 0..ny-1
         // pull from the ghost rows, which hold the neighbours' edge rows; the
@@ -196,10 +197,12 @@ mhd_kernel_config default_config(const mhd::Layout& L, int prec, int wall_x) {
     while (V > 1 && !mhd::step_shape_ok(L, prec, wall_x, V, 4)) V >>= 1;
     c.nodes_per_thread = V;
     c.rows_per_block = V == 1 ? 8 : 4;
+    c.warps_per_sm = 0;
     return c;
 }
 
 bool config_ok(const mhd_lattice* l, const mhd_kernel_config& c) {
+    if (c.warps_per_sm < 0 || c.warps_per_sm > 64) return false;
     if (l->p.precision == 0 && c.rows_per_block > 8) return false;
     // the FP16S in-place phase A kernel takes blocks of at most 256 threads
     if (l->in_place && l->p.precision == MHD_FP16S && c.rows_per_block > 8) return false;
@@ -224,8 +227,12 @@ std::string cache_key(const mhd_lattice* l) {
     return buf;
 }
 
-std::map<std::string, std::pair<int, int>> read_cache(const char* path) {
-    std::map<std::string, std::pair<int, int>> m;
+// entries "key": [nodes_per_thread, rows_per_block, warps_per_sm] (a
+// two-number entry has the built-in staging depth, warps_per_sm = 0)
+using TuneCache = std::map<std::string, mhd_kernel_config>;
+
+TuneCache read_cache(const char* path) {
+    TuneCache m;
     FILE* fp = fopen(path, "r");
     if (!fp) return m;
     char line[512];
@@ -234,22 +241,23 @@ std::map<std::string, std::pair<int, int>> read_cache(const char* path) {
         if (!q1) continue;
         char* q2 = strchr(q1 + 1, '"');
         if (!q2) continue;
-        int v = 0, by = 0;
-        if (sscanf(q2 + 1, " : [%d , %d]", &v, &by) == 2) m[std::string(q1 + 1, q2)] = {v, by};
+        int v = 0, by = 0, w = 0;
+        const int got = sscanf(q2 + 1, " : [%d , %d , %d]", &v, &by, &w);
+        if (got >= 2) m[std::string(q1 + 1, q2)] = mhd_kernel_config{v, by, got == 3 ? w : 0};
     }
     fclose(fp);
     return m;
 }
 
-void write_cache(const char* path, const std::map<std::string, std::pair<int, int>>& m) {
+void write_cache(const char* path, const TuneCache& m) {
     std::string tmp = std::string(path) + ".tmp";
     FILE* fp = fopen(tmp.c_str(), "w");
     if (!fp) return;
     fprintf(fp, "{\n");
     size_t i = 0;
     for (auto& kv : m)
-        fprintf(fp, "  \"%s\": [%d, %d]%s\n", kv.first.c_str(), kv.second.first, kv.second.second,
-                ++i < m.size() ? "," : "");
+        fprintf(fp, "  \"%s\": [%d, %d, %d]%s\n", kv.first.c_str(), kv.second.nodes_per_thread,
+                kv.second.rows_per_block, kv.second.warps_per_sm, ++i < m.size() ? "," : "");
     fprintf(fp, "}\n");
     fclose(fp);
     rename(tmp.c_str(), path);
@@ -327,10 +335,7 @@ mhd_status mhd_create(int nx, int ny, const mhd_params* p, void* stream, mhd_lat
     if (const char* path = getenv("MHD_TUNE_CACHE")) {
         auto m = read_cache(path);
         auto it = m.find(cache_key(l));
-        if (it != m.end()) {
-            mhd_kernel_config c{it->second.first, it->second.second};
-            if (config_ok(l, c)) l->cfg = c;
-        }
+        if (it != m.end() && config_ok(l, it->second)) l->cfg = it->second;
     }
     *out = l;
     return MHD_OK;
@@ -918,7 +923,8 @@ mhd_status mhd_get_kernel_config(const mhd_lattice* l, mhd_kernel_config* out) {
 mhd_status mhd_set_kernel_config(mhd_lattice* l, const mhd_kernel_config* cfg) {
     if (!l || !cfg) return fail(MHD_EINVAL, "NULL argument");
     if (!config_ok(l, *cfg)) return fail(MHD_EINVAL, "launch shape not valid for this lattice");
-    if (cfg->nodes_per_thread != l->cfg.nodes_per_thread || cfg->rows_per_block != l->cfg.rows_per_block) {
+    if (cfg->nodes_per_thread != l->cfg.nodes_per_thread || cfg->rows_per_block != l->cfg.rows_per_block ||
+        cfg->warps_per_sm != l->cfg.warps_per_sm) {
         CK(cudaStreamSynchronize(l->stream), "mhd_set_kernel_config");
         drop_graphs(l);
         l->cfg = *cfg;
@@ -972,13 +978,10 @@ mhd_status mhd_autotune(mhd_lattice* l, mhd_kernel_config* best) {
     if (path) {
         auto m = read_cache(path);
         auto it = m.find(key);
-        if (it != m.end()) {
-            mhd_kernel_config c{it->second.first, it->second.second};
-            if (config_ok(l, c)) {
-                mhd_status s = mhd_set_kernel_config(l, &c);
-                if (best) *best = l->cfg;
-                return s;
-            }
+        if (it != m.end() && config_ok(l, it->second)) {
+            mhd_status s = mhd_set_kernel_config(l, &it->second);
+            if (best) *best = l->cfg;
+            return s;
         }
     }
     CK(cudaStreamSynchronize(l->stream), "mhd_autotune");
@@ -1001,37 +1004,61 @@ mhd_status mhd_autotune(mhd_lattice* l, mhd_kernel_config* best) {
     float best_ms = 1e30f;
     const mhd_kernel_config saved = l->cfg;
     const int iters = 20;
+    // time one candidate shape (ms for `iters` steps after 4 untimed ones)
+    auto time_config = [&](const mhd_kernel_config& c, float* ms) -> cudaError_t {
+        l->cfg = c;
+        mhd::StepLaunch s = step_launch(l, l->cur);  // reads cur, writes the spare buffer
+        auto one = [&](int k) {
+            return l->in_place ? launch_inplace_step(l, scratch, k & 1, l->stream) : mhd::launch_step(s, l->stream);
+        };
+        cudaError_t err = cudaSuccess;
+        for (int k = 0; k < 4 && err == cudaSuccess; ++k) err = one(k);
+        if (err == cudaSuccess) err = cudaEventRecord(e0, l->stream);
+        for (int k = 0; k < iters && err == cudaSuccess; ++k) err = one(k);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, l->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        if (err == cudaSuccess) err = cudaEventElapsedTime(ms, e0, e1);
+        if (err == cudaSuccess && getenv("MHD_TUNE_VERBOSE"))
+            fprintf(stderr, "mhd_autotune %dx%d p%d V=%d BY=%d W=%d: %.4f ms/step\n", l->nx, l->ny, l->p.precision,
+                    c.nodes_per_thread, c.rows_per_block, c.warps_per_sm, *ms / iters);
+        return err;
+    };
+    auto give_up = [&](cudaError_t err) {
+        l->cfg = saved;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (scratch) cudaFree(scratch);
+        return cuda_fail(err, "autotune candidate");
+    };
+    // every shape at the built-in staging depth ...
     for (int V : {1, 2, 4}) {
         for (int BY : {1, 2, 4, 8, 16}) {
-            mhd_kernel_config c{V, BY};
+            mhd_kernel_config c{V, BY, 0};
             if (!config_ok(l, c)) continue;
-            l->cfg = c;
-            mhd::StepLaunch s = step_launch(l, l->cur);  // reads cur, writes the spare buffer
-            auto one = [&](int k) {
-                return l->in_place ? launch_inplace_step(l, scratch, k & 1, l->stream)
-                                   : mhd::launch_step(s, l->stream);
-            };
-            cudaError_t err = cudaSuccess;
-            for (int k = 0; k < 4 && err == cudaSuccess; ++k) err = one(k);
-            if (err == cudaSuccess) err = cudaEventRecord(e0, l->stream);
-            for (int k = 0; k < iters && err == cudaSuccess; ++k) err = one(k);
-            if (err == cudaSuccess) err = cudaEventRecord(e1, l->stream);
-            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
             float ms = 0;
-            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-            if (err != cudaSuccess) {
-                l->cfg = saved;
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                if (scratch) cudaFree(scratch);
-                return cuda_fail(err, "autotune candidate");
-            }
-            if (getenv("MHD_TUNE_VERBOSE"))
-                fprintf(stderr, "mhd_autotune %dx%d p%d V=%d BY=%d: %.4f ms/step\n", l->nx, l->ny,
-                        l->p.precision, V, BY, ms / iters);
+            const cudaError_t err = time_config(c, &ms);
+            if (err != cudaSuccess) return give_up(err);
             if (ms < best_ms) {
                 best_ms = ms;
                 chosen = c;
+            }
+        }
+    }
+    // ... then the fastest one at other depths (the x-wall kernel has none)
+    if (l->p.bc_x != MHD_WALL) {
+        const int rule = mhd::step_rule_warps(l->p.precision, chosen.nodes_per_thread);
+        const mhd_kernel_config shape = chosen;
+        float depth_ms = best_ms;
+        for (int num : {2, 3, 6, 8}) {  // quarters of the rule's depth
+            const int W = std::min(64, std::max(shape.rows_per_block, rule * num / 4));
+            if (W / shape.rows_per_block == rule / shape.rows_per_block) continue;  // the same grid
+            mhd_kernel_config c{shape.nodes_per_thread, shape.rows_per_block, W};
+            float ms = 0;
+            const cudaError_t err = time_config(c, &ms);
+            if (err != cudaSuccess) return give_up(err);
+            if (ms < depth_ms) {
+                depth_ms = ms;
+                if (ms < 0.99f * best_ms) chosen = c;
             }
         }
     }
@@ -1047,7 +1074,7 @@ mhd_status mhd_autotune(mhd_lattice* l, mhd_kernel_config* best) {
     if (s != MHD_OK) return s;
     if (path) {
         auto m = read_cache(path);
-        m[key] = {chosen.nodes_per_thread, chosen.rows_per_block};
+        m[key] = chosen;
         write_cache(path, m);
     }
     if (best) *best = l->cfg;

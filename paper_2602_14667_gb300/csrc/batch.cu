@@ -115,6 +115,7 @@ void batch_drop_graphs(mhd_batch* b) {
 
 bool batch_shape_ok(const mhd_batch* b, const mhd_kernel_config& c) {
     if (c.rows_per_block < 1 || c.rows_per_block > 16) return false;
+    if (c.warps_per_sm < 0 || c.warps_per_sm > 64) return false;
     if (c.nodes_per_thread != 1 && c.nodes_per_thread != 2 && c.nodes_per_thread != 4) return false;
     for (auto& L : b->layouts)
         if (L.nx % c.nodes_per_thread) return false;
@@ -164,7 +165,10 @@ mhd_status batch_configure(mhd_batch* b, const mhd_kernel_config& c) {
                                                       threads, 0),
         "occupancy");
     BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev), "SM count");
-    b->grid = std::max(1, std::min(b->ntiles, std::max(1, per_sm) * sms));
+    per_sm = std::max(1, per_sm);
+    // staging depth: every resident block unless the shape caps the warps per SM
+    if (c.warps_per_sm > 0) per_sm = std::min(per_sm, std::max(1, c.warps_per_sm / rows));
+    b->grid = std::max(1, std::min(b->ntiles, per_sm * sms));
     batch_drop_graphs(b);
     b->cfg = c;
     return MHD_OK;
@@ -449,37 +453,58 @@ mhd_status mhd_batch_autotune(mhd_batch* b, mhd_kernel_config* best) {
     BCK(cudaEventCreate(&e1), "event");
     mhd_kernel_config chosen = b->cfg;
     float best_ms = 1e30f;
+    // one candidate: configure, two untimed and five timed steps
+    auto time_config = [&](const mhd_kernel_config& c, float* ms) -> mhd_status {
+        mhd_status s = batch_configure(b, c);
+        if (s != MHD_OK) return s;
+        const int V = c.nodes_per_thread;
+        cudaError_t err = cudaSuccess;
+        for (int k = 0; k < 2 && err == cudaSuccess; ++k) err = launch_batch(b, b->cur, V, b->stream);
+        if (err == cudaSuccess) err = cudaEventRecord(e0, b->stream);
+        for (int k = 0; k < 5 && err == cudaSuccess; ++k) err = launch_batch(b, b->cur, V, b->stream);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, b->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        if (err == cudaSuccess) err = cudaEventElapsedTime(ms, e0, e1);
+        if (err != cudaSuccess) return bcuda(err, "batch autotune candidate");
+        if (getenv("MHD_TUNE_VERBOSE"))
+            fprintf(stderr, "mhd_batch_autotune V=%d BY=%d W=%d grid=%d tiles=%d: %.4f ms/step\n", V,
+                    c.rows_per_block, c.warps_per_sm, b->grid, b->ntiles, *ms / 5);
+        return MHD_OK;
+    };
+    auto done = [&](mhd_status s) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return s;
+    };
     for (int V : {1, 2, 4})
         for (int BY : {1, 2, 4, 8, 16}) {
-            mhd_kernel_config c{V, BY};
+            mhd_kernel_config c{V, BY, 0};
             if (!batch_shape_ok(b, c)) continue;
-            mhd_status s = batch_configure(b, c);
-            if (s != MHD_OK) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return s;
-            }
-            cudaError_t err = cudaSuccess;
-            for (int k = 0; k < 2 && err == cudaSuccess; ++k) err = launch_batch(b, b->cur, V, b->stream);
-            if (err == cudaSuccess) err = cudaEventRecord(e0, b->stream);
-            for (int k = 0; k < 5 && err == cudaSuccess; ++k) err = launch_batch(b, b->cur, V, b->stream);
-            if (err == cudaSuccess) err = cudaEventRecord(e1, b->stream);
-            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
             float ms = 0;
-            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-            if (err != cudaSuccess) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return bcuda(err, "batch autotune candidate");
-            }
-            if (getenv("MHD_TUNE_VERBOSE"))
-                fprintf(stderr, "mhd_batch_autotune V=%d BY=%d grid=%d tiles=%d: %.4f ms/step\n", V, BY,
-                        b->grid, b->ntiles, ms / 5);
+            const mhd_status s = time_config(c, &ms);
+            if (s != MHD_OK) return done(s);
             if (ms < best_ms) {
                 best_ms = ms;
                 chosen = c;
             }
         }
+    // the fastest shape with fewer warps in flight per SM than fit (kept
+    // only if at least 1 % faster)
+    {
+        const mhd_kernel_config shape = chosen;
+        float depth_ms = best_ms;
+        for (int W : {8, 16, 32}) {
+            if (W < shape.rows_per_block) continue;
+            mhd_kernel_config c{shape.nodes_per_thread, shape.rows_per_block, W};
+            float ms = 0;
+            const mhd_status s = time_config(c, &ms);
+            if (s != MHD_OK) return done(s);
+            if (ms < depth_ms) {
+                depth_ms = ms;
+                if (ms < 0.99f * best_ms) chosen = c;
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     std::fill(b->prev_valid.begin(), b->prev_valid.end(), 0);  // the spare buffer was overwritten

@@ -102,10 +102,9 @@ static cudaError_t launch_aa_t(const StepLaunch& s, int phase, cudaStream_t st) 
     const int nxb = (s.L.nx + 32 * s.V - 1) / (32 * s.V);
     const int ntiles = nxb * ((s.L.ny + s.BY - 1) / s.BY);
     // persistent grid: as many blocks as are resident at once, with the
-    // resident warps capped as for the pull step (about 4 KB of every plane
-    // in flight per SM; FP64 uncapped)
-    using S = typename Prec<PREC>::S;
-    const int max_warps = PREC == 0 ? 64 : std::max(1, 4096 / (32 * s.V * (int)sizeof(S)));
+    // resident warps capped as for the pull step (by default about 4 KB of
+    // every plane in flight per SM; FP64 uncapped; s.W sets another depth)
+    const int max_warps = s.W > 0 ? s.W : step_rule_warps(PREC, s.V);
     const int warp_cap = std::max(1, max_warps / s.BY);
     auto go = [&](auto kernel) -> cudaError_t {
         int per_sm = 0, sms = 0, dev = 0;

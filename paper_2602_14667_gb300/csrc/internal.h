@@ -28,14 +28,19 @@ struct StepLaunch {
     void* dst;
     double omega, omega_m, rho0;
     int variant, collision, mag_collision, wall_x, wall_y;
-    int V;   // nodes per thread along x
-    int BY;  // warps (rows) per block
+    int V;      // nodes per thread along x
+    int BY;     // warps (rows) per block
+    int W = 0;  // resident warps per SM of the persistent grid (0: step_rule_warps)
 };
 
 // fused stream + collide (one time step)
 cudaError_t launch_step(const StepLaunch& s, cudaStream_t st);
 // is (V, BY) a legal launch shape for this lattice?
 bool step_shape_ok(const Layout& L, int prec, int wall_x, int V, int BY);
+// The built-in staging depth of the row kernels: resident warps per SM that
+// keep about 4 KB of every plane in flight (warps x 32 lanes x V elements);
+// FP64, bound by its arithmetic, keeps every resident warp (64).
+int step_rule_warps(int prec, int V);
 
 // f = f_eq(rho, u, b), g = g_eq(u, b) from FP64 (or FP32) fields in device
 // memory or in mapped pinned host memory (rho may be null); with flags, the

@@ -86,13 +86,14 @@ static cudaError_t launch_step_t(const StepLaunch& s, cudaStream_t st) {
         return cudaGetLastError();
     }
     const int nxb = grid.x, ntiles = grid.x * grid.y;
-    // Resident warps per SM: the DRAM throughput of the storage-bound
-    // kernels peaks with about 4 KB of every plane in flight per SM (warps x
-    // 32 lanes x V elements); more concurrent row streams lose bandwidth
-    // (FP32: 8 warps at V = 4 or 16 at V = 2; FP16S: 16 at V = 4).  FP64 is
-    // bound by its arithmetic and keeps every resident block.
-    using S = typename Prec<PREC>::S;
-    const int max_warps = PREC == 0 ? 64 : std::max(1, 4096 / (32 * s.V * (int)sizeof(S)));
+    // Resident warps per SM (the staging depth: how many row tiles, and
+    // bytes of every plane, are in flight): the DRAM throughput of the
+    // storage-bound kernels peaks with about 4 KB of every plane in flight
+    // per SM (warps x 32 lanes x V elements); more concurrent row streams
+    // lose bandwidth (FP32: 8 warps at V = 4 or 16 at V = 2; FP16S: 16 at
+    // V = 4).  FP64 is bound by its arithmetic and keeps every resident
+    // block.  The launch shape may set another depth (s.W).
+    const int max_warps = s.W > 0 ? s.W : step_rule_warps(PREC, s.V);
     const int warp_cap = std::max(1, max_warps / s.BY);
     auto go = [&](auto kernel) -> cudaError_t {
         int per_sm = 0, sms = 0, dev = 0;
@@ -121,6 +122,11 @@ static cudaError_t launch_step_t(const StepLaunch& s, cudaStream_t st) {
         return cudaErrorInvalidValue;
     }
     return cudaErrorInvalidValue;
+}
+
+int step_rule_warps(int prec, int V) {
+    const int esize = prec == 0 ? 8 : (prec == 1 ? 4 : 2);
+    return prec == 0 ? 64 : std::max(1, 4096 / (32 * V * esize));
 }
 
 bool step_shape_ok(const Layout& L, int prec, int wall_x, int V, int BY) {

@@ -136,12 +136,17 @@ def test_tune_cache_holds_only_valid_launch_shapes():
     """The autotuner's committed cache (read by mhd_create / mhd_autotune and
     by the benchmark) may only name shapes the library accepts: 1, 2 or 4
     nodes per thread dividing nx (at most 2 for FP64), 1..16 rows per block
-    (at most 8 for FP64 and for FP16S in place)."""
+    (at most 8 for FP64 and for FP16S in place), and a staging depth of 0
+    (the built-in rule) or 1..64 resident warps per SM."""
     import json
     with open(os.path.join(ROOT, "paper_2602_14667_gb300", "tune_cache.json")) as fh:
         cache = json.load(fh)
     assert cache
-    for key, (V, BY) in cache.items():
+    for key, shape in cache.items():
+        assert len(shape) in (2, 3), key
+        V, BY = shape[:2]
+        W = shape[2] if len(shape) == 3 else 0
+        assert W == 0 or 1 <= W <= 64, key
         gpu, prec, size, bc, *rest = key.split("|")
         nx = int(size.split("x")[0])
         p = int(prec[1:])

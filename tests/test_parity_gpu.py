@@ -377,13 +377,55 @@ def test_autotune_keeps_state_and_returns_valid_shape(tmp_path, monkeypatch):
         a.advance(10)
         before = a.get_populations()
         shape = a.autotune()
-        assert shape in [(v, by) for v in (1, 2, 4) for by in (1, 2, 4, 8, 16)]
+        assert shape[:2] in [(v, by) for v in (1, 2, 4) for by in (1, 2, 4, 8, 16)]
+        assert shape[2] == 0 or 1 <= shape[2] <= 64
         after = a.get_populations()
         np.testing.assert_array_equal(before[0], after[0])
         assert a.kernel_config == shape
     assert (tmp_path / "tune.json").exists()
     with _lat(n, n, "fp32") as b:       # a new lattice picks the cached shape
         assert b.kernel_config == shape
+
+
+@pytest.mark.parametrize("prec,in_place", [("fp32", False), ("fp16s", False), ("fp32", True)])
+def test_staging_depth_changes_no_bits(prec, in_place):
+    """The staging depth (resident warps per SM of the persistent grid) only
+    changes how many row tiles are in flight: every depth gives the state of
+    the built-in one bit for bit; depths outside 0..64 are rejected."""
+    from paper_2602_14667_gb300 import MhdError
+    import mhd_inputs
+    nx, ny = 264, 40
+    fields = mhd_inputs.random_spectrum(nx, ny, 3, 0.04, 0.04, kmax=6)
+    states = []
+    for W in (0, 1, 4, 16, 64):
+        with _lat(nx, ny, prec, in_place=in_place) as lat:
+            lat.kernel_config = (4, 1, W)
+            assert lat.kernel_config == (4, 1, W)
+            lat.set_fields(*fields)
+            lat.advance(70)  # one 64-step graph and single steps
+            states.append(lat.get_state())
+    assert all(np.array_equal(st, states[0]) for st in states[1:])
+    with _lat(nx, ny, prec, in_place=in_place) as lat:
+        for W in (-1, 65):
+            with pytest.raises(MhdError, match="EINVAL"):
+                lat.kernel_config = (4, 1, W)
+
+
+def test_batch_staging_depth_changes_no_bits():
+    import mhd_inputs
+    from paper_2602_14667_gb300 import Batch
+    sizes = [(64, 64), (96, 48), (128, 128)]
+    taus = [(0.53, 0.56), (0.6, 0.52), (0.55, 0.55)]
+    out = []
+    for W in (0, 4, 32):
+        with Batch(sizes, taus) as b:
+            b.kernel_config = (2, 4, W)
+            for i, (nx, ny) in enumerate(sizes):
+                b.set_fields(i, *mhd_inputs.random_spectrum(nx, ny, 10 + i, 0.03, 0.03))
+            b.advance(40)
+            out.append([b.get_fields(i)["ux"] for i in range(len(sizes))])
+    for o in out[1:]:
+        assert all(np.array_equal(x, y) for x, y in zip(o, out[0]))
 
 
 def test_conservation_over_many_steps():
