@@ -385,6 +385,12 @@ def test_autotune_keeps_state_and_returns_valid_shape(tmp_path, monkeypatch):
     assert (tmp_path / "tune.json").exists()
     with _lat(n, n, "fp32") as b:       # a new lattice picks the cached shape
         assert b.kernel_config == shape
+    # an entry of two numbers (shape without a depth) reads as depth 0
+    text = (tmp_path / "tune.json").read_text()
+    key = [ln for ln in text.splitlines() if "128x128" in ln][0].split('"')[1]
+    (tmp_path / "tune.json").write_text('{\n  "%s": [2, 8]\n}\n' % key)
+    with _lat(n, n, "fp32") as c:
+        assert c.kernel_config == (2, 8, 0)
 
 
 @pytest.mark.parametrize("prec,in_place", [("fp32", False), ("fp16s", False), ("fp32", True)])
