@@ -311,7 +311,7 @@ def extra_rows(fp32_mlups, peak):
                 100 calls), of the closure step's cost (512^2, 512 steps) and
                 of the learned-closure study (2048^2 -> 512^2, the closure
                 against plain 512^2, the untrained control and the plain
-                grid of equal GPU time, the MLP on every 1st / 4th / 8th
+                grid of equal GPU time, the MLP on every 1st / 2nd / 4th / 8th
                 step), the last in compact form."""
     import numpy as np
     import torch
@@ -652,7 +652,7 @@ def closure_line():
     scheme on the finest grid whose run is predicted to take no more GPU
     time than the closure run (equal GPU time; its fields box-filtered onto
     the 512^2 grid like the fine run's).  And the closure with its MLP
-    evaluated on every 4th and every 8th step only (the stored correction
+    evaluated on every 2nd, 4th and 8th step only (the stored correction
     reused between), each calibrated, judged, timed and compared with its
     own equal-time plain grid."""
     import torch
@@ -663,7 +663,7 @@ def closure_line():
                          sample_stride=1500, samples_per_seed=4,
                          eval_coarse_steps=(500, 1000, 1500, 2000), epochs=20, batch=8192)
     t0 = time.perf_counter()
-    res = cs.run(cfg, control=True, equal_time=True, intervals=(4, 8))
+    res = cs.run(cfg, control=True, equal_time=True, intervals=(2, 4, 8))
     wall = time.perf_counter() - t0
     steps = cfg.eval_coarse_steps
     last = steps[-1]
