@@ -883,11 +883,14 @@ def run_slabs(args):
     """Cost of the row-slab decomposition of one lattice on one GPU: the
     Orszag-Tang lattice (4096^2 FP32 by default) advanced whole and as S = 2
     and 4 slabs of equal rows (bc_y = MHD_HALO), every slab on the same
-    stream: each step is the fused step of every slab, then the exchange of
-    the boundary-crossing rows of every boundary (mhd_slab_exchange: one
-    copy kernel per direction).  CUDA events around `steps` steps; the
-    exchanges alone are timed the same way.  The slabs' populations equal
-    the whole lattice's bit for bit (tests/test_slabs_gpu.py)."""
+    stream.  Each step is the fused step of every slab, then the exchange of
+    the boundary-crossing rows of every boundary: through the slab group
+    (mhd_slab_group_advance: one exchange kernel per step, 64-step CUDA
+    graphs; the whole lattice also runs its 64-step graphs), and stepwise
+    (one mhd_advance per slab and one mhd_slab_exchange per boundary and
+    step, two copy kernels each).  CUDA events around `steps` steps.  The
+    slabs' populations equal the whole lattice's bit for bit
+    (tests/test_slabs_gpu.py)."""
     import torch
 
     import mhd_inputs
@@ -898,7 +901,8 @@ def run_slabs(args):
     stream = torch.cuda.Stream()
     fields = mhd_inputs.orszag_tang(n, 0.04, 0.04)
 
-    def timed(fn, reps):
+    def timed(fn, reps, steps):
+        fn()  # untimed: graphs captured, kernels loaded
         stream.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -907,32 +911,32 @@ def run_slabs(args):
             fn()
         e1.record(stream)
         e1.synchronize()
-        return e0.elapsed_time(e1) / reps
+        return e0.elapsed_time(e1) / steps
 
     out = {}
     with Lattice(n, n, tau, tau, precision=prec, stream=stream.cuda_stream) as lat:
         lat.set_fields(*fields)
         shape = lat.kernel_config
-        lat.advance(args.warmup)
-        # single launches, as the slabs step (no 64-step graphs)
-        out["whole"] = {"ms_per_step": timed(lambda: lat.advance(1), args.steps)}
+        out["whole"] = {"ms_per_step": timed(lambda: lat.advance(args.steps), 1, args.steps)}
     with ClockSampler(0) as clk:
         for S in (2, 4):
             with SlabGroup(n, n, S, tau, tau, precision=prec, stream=stream.cuda_stream) as sg:
                 sg.kernel_config = shape
                 sg.set_fields(*fields)
-                sg.advance(args.warmup)
-                ms = timed(lambda: sg.advance(1), args.steps)
-                ex = timed(sg.exchange, args.steps)
-            out[f"slabs_{S}"] = {"ms_per_step": ms, "exchange_us_per_step": ex * 1e3,
-                                 "overhead_vs_whole": ms / out["whole"]["ms_per_step"] - 1}
+                ms = timed(lambda: sg.advance(args.steps), 1, args.steps)
+                msw = timed(lambda: sg.advance(1, stepwise=True), args.steps, args.steps)
+                ex = timed(sg.exchange, args.steps, args.steps)
+            w = out["whole"]["ms_per_step"]
+            out[f"slabs_{S}"] = {"ms_per_step": ms, "overhead_vs_whole": ms / w - 1,
+                                 "stepwise_ms_per_step": msw, "stepwise_overhead_vs_whole": msw / w - 1,
+                                 "exchange_call_us": ex * 1e3}
     for v in out.values():
         v["mlups"] = n * n / (v["ms_per_step"] * 1e-3) / 1e6
     res = {"metric": f"row-slab decomposition on one GPU ({n}^2 {prec})", "value": out["slabs_2"]["mlups"],
            "unit": "MLUPS (2 slabs)", "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "dtype": DTYPE[prec], "data": "synthetic",
            "config": {"workload": f"slabs_orszag_tang_{n}x{n}_{prec}", "kernel_config": list(shape),
-                      "stream": "all slabs on one stream; single step launches"},
+                      "stream": "all slabs on one stream"},
            "runs": out, "clocks": clk.summary()}
     print(json.dumps(res), flush=True)
 

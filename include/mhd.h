@@ -238,6 +238,26 @@ mhd_status mhd_set_state(mhd_lattice* l, const void* host, size_t bytes);
  * ghost rows it had (zeros after mhd_create). */
 mhd_status mhd_slab_exchange(mhd_lattice* lower, mhd_lattice* upper, int all_planes);
 
+/* The slabs of one row-decomposed periodic lattice stepped together on one
+ * device: mhd_slab_group_advance(g, n) does what n rounds of (mhd_advance of
+ * every slab by one step, then mhd_slab_exchange of every boundary) do, with
+ * every round's exchanges in one kernel and runs of 64 rounds in one CUDA
+ * graph (captured on first use).  slabs[0..n-1] in order along y (slab i
+ * just below slab i+1, the last just below the first); every slab
+ * bc_y = MHD_HALO, the same nx, precision and bc_x, on the current device,
+ * created with the same stream.  The group only borrows
+ * the lattices (they must outlive it; the caller still destroys them) and
+ * holds a small device table of its copies.  MHD_EINVAL for NULL or
+ * mismatched slabs; advance: MHD_ESTATE unless every slab has its fields set
+ * and all have taken the same number of steps modulo 2 (as they do when
+ * stepped through the group).
+ * Exchange after setting the fields (mhd_slab_exchange of every boundary)
+ * before the first advance, as for slabs stepped one by one. */
+typedef struct mhd_slab_group mhd_slab_group;
+mhd_status mhd_slab_group_create(mhd_lattice* const* slabs, int n, mhd_slab_group** out);
+mhd_status mhd_slab_group_advance(mhd_slab_group* g, long long nsteps);
+mhd_status mhd_slab_group_destroy(mhd_slab_group* g);
+
 /* Allocation-free global diagnostics (the paper has no counterpart to this
  * call; it is a service for callers that cannot allocate device memory
  * when they need the totals -- e.g. a host framework that has reserved the

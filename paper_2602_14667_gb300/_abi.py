@@ -86,6 +86,9 @@ _SIGNATURES = {
     "mhd_destroy": [_P],
     "mhd_state_bytes": [_P, ctypes.POINTER(ctypes.c_size_t)],
     "mhd_slab_exchange": [_P, _P, ctypes.c_int],
+    "mhd_slab_group_create": [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)],
+    "mhd_slab_group_advance": [_P, ctypes.c_longlong],
+    "mhd_slab_group_destroy": [_P],
     "mhd_totals_noalloc": [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(mhd_params), _P,
                            ctypes.POINTER(mhd_totals)],
     "mhd_batch_create": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -299,6 +302,26 @@ def slab_exchange(lower: "Lattice", upper: "Lattice", all_planes: bool = False) 
     """mhd_slab_exchange: fill the ghost rows across the boundary between two
     neighbouring slabs (lower: the rows just below upper)."""
     check(lib().mhd_slab_exchange(lower.handle, upper.handle, int(all_planes)), "mhd_slab_exchange")
+
+
+class SlabSteps:
+    """mhd_slab_group_*: the slabs of one lattice (in order along y, on one
+    device and one stream) stepped together, every round's exchanges in one
+    kernel and runs of 64 rounds in one CUDA graph.  Borrows the lattices."""
+
+    def __init__(self, lattices):
+        self.lattices = list(lattices)
+        arr = (_P * len(self.lattices))(*[l.handle for l in self.lattices])
+        self._h = _P()
+        check(lib().mhd_slab_group_create(arr, len(self.lattices), ctypes.byref(self._h)), "mhd_slab_group_create")
+
+    def advance(self, nsteps: int):
+        check(lib().mhd_slab_group_advance(self._h, int(nsteps)), "mhd_slab_group_advance")
+
+    def close(self):
+        if self._h:
+            check(lib().mhd_slab_group_destroy(self._h), "mhd_slab_group_destroy")
+            self._h = _P()
 
 
 def totals_noalloc(state_ptr: int, nx: int, ny: int, params: "mhd_params", prev_ptr=None,

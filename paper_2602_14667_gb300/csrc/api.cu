@@ -869,6 +869,162 @@ mhd_status mhd_slab_exchange(mhd_lattice* lower, mhd_lattice* upper, int all_pla
     return s;
 }
 
+// ---- slab groups ------------------------------------------------------------
+struct mhd_slab_group {
+    std::vector<mhd_lattice*> slabs;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;              // capture stream of the group's graphs
+    mhd::HaloJob* jobs[2] = {nullptr, nullptr};  // per buffer parity: 2 copies per boundary
+    int njobs = 0;
+    long long row_bytes = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // kGraphSteps rounds from parity 0 / 1
+    std::vector<mhd_kernel_config> graph_cfg;       // the slabs' launch shapes at capture
+};
+
+static void group_drop_graphs(mhd_slab_group* g) {
+    for (auto& x : g->graph)
+        if (x) {
+            cudaGraphExecDestroy(x);
+            x = nullptr;
+        }
+}
+
+mhd_status mhd_slab_group_create(mhd_lattice* const* slabs, int n, mhd_slab_group** out) {
+    if (!out) return fail(MHD_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!slabs || n < 1) return fail(MHD_EINVAL, "need at least one slab");
+    const mhd_lattice* a = slabs[0];
+    for (int i = 0; i < n; ++i) {
+        const mhd_lattice* l = slabs[i];
+        if (!l) return fail(MHD_EINVAL, "slab is NULL");
+        if (!l->halo) return fail(MHD_EINVAL, "a slab group needs bc_y = MHD_HALO lattices");
+        if (l->nx != a->nx || l->p.precision != a->p.precision || l->p.bc_x != a->p.bc_x)
+            return fail(MHD_EINVAL, "the slabs of one lattice share nx, precision and bc_x");
+        if (l->dev != a->dev || l->stream != a->stream)
+            return fail(MHD_EINVAL, "the slabs of a group share one device and one stream");
+        if (l->closure_buf) return fail(MHD_EINVAL, "a slab group steps slabs without a closure");
+    }
+    CK(cudaSetDevice(a->dev), "cudaSetDevice");
+    auto* g = new mhd_slab_group;
+    g->slabs.assign(slabs, slabs + n);
+    g->stream = a->stream;
+    g->row_bytes = (long long)a->L.pitch * a->L.esize;  // a multiple of 128 bytes
+    g->njobs = 2 * n;
+    std::vector<mhd::HaloJob> host(g->njobs);
+    cudaError_t e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
+    for (int par = 0; par < 2 && e == cudaSuccess; ++par) {
+        for (int i = 0; i < n; ++i) {
+            mhd_lattice* lo = slabs[i];
+            mhd_lattice* up = slabs[(i + 1) % n];
+            const char* lb = static_cast<const char*>(lo->buf[par]);
+            const char* ub = static_cast<const char*>(up->buf[par]);
+            const long long lp = lo->L.plane * (long long)lo->L.esize, upl = up->L.plane * (long long)up->L.esize;
+            // the top row of `lo` into the ghost row below `up` (c_y = +1) ...
+            mhd::HaloJob& j0 = host[2 * i];
+            j0.src = lb + (long long)(lo->ny - 1) * g->row_bytes;
+            j0.dst = const_cast<char*>(ub) - g->row_bytes;
+            j0.src_plane = lp;
+            j0.dst_plane = upl;
+            // ... and the bottom row of `up` into the ghost row above `lo` (c_y = -1)
+            mhd::HaloJob& j1 = host[2 * i + 1];
+            j1.src = ub;
+            j1.dst = const_cast<char*>(lb) + (long long)lo->ny * g->row_bytes;
+            j1.src_plane = upl;
+            j1.dst_plane = lp;
+            int k0 = 0, k1 = 0;
+            for (int p = 0; p < mhd::kStatePlanes; ++p) {
+                if (mhd::pcy(p) > 0) j0.planes[k0++] = p;
+                if (mhd::pcy(p) < 0) j1.planes[k1++] = p;
+            }
+        }
+        e = cudaMalloc(&g->jobs[par], sizeof(mhd::HaloJob) * g->njobs);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g->jobs[par], host.data(), sizeof(mhd::HaloJob) * g->njobs, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        mhd_slab_group_destroy(g);
+        return cuda_fail(e, "mhd_slab_group_create");
+    }
+    *out = g;
+    return MHD_OK;
+}
+
+// One round from buffer parity `par` on stream st: every slab's step, then
+// the exchanges of every boundary into the buffers the steps wrote.
+static cudaError_t group_round(const mhd_slab_group* g, int par, cudaStream_t st) {
+    for (const mhd_lattice* l : g->slabs) {
+        const cudaError_t e = launch_lattice_step(l, par, st);
+        if (e != cudaSuccess) return e;
+    }
+    return mhd::launch_halo_jobs(g->jobs[par ^ 1], g->njobs, g->row_bytes, st);
+}
+
+mhd_status mhd_slab_group_advance(mhd_slab_group* g, long long nsteps) {
+    if (!g) return fail(MHD_EINVAL, "group is NULL");
+    if (nsteps < 0) return fail(MHD_EINVAL, "nsteps must be >= 0");
+    const int par0 = g->slabs[0]->cur;
+    for (const mhd_lattice* l : g->slabs) {
+        if (!l->fields_set) return fail(MHD_ESTATE, "set the fields of every slab first");
+        if (l->cur != par0) return fail(MHD_ESTATE, "the slabs have taken different numbers of steps");
+        if (l->closure_buf) return fail(MHD_EINVAL, "a slab group steps slabs without a closure");
+    }
+    if (nsteps == 0) return MHD_OK;
+    CK(cudaSetDevice(g->slabs[0]->dev), "cudaSetDevice");
+    // graphs captured with other launch shapes are stale
+    std::vector<mhd_kernel_config> cfg;
+    for (const mhd_lattice* l : g->slabs) cfg.push_back(l->cfg);
+    if (cfg.size() != g->graph_cfg.size() ||
+        !std::equal(cfg.begin(), cfg.end(), g->graph_cfg.begin(), [](const mhd_kernel_config& x, const mhd_kernel_config& y) {
+            return x.nodes_per_thread == y.nodes_per_thread && x.rows_per_block == y.rows_per_block &&
+                   x.warps_per_sm == y.warps_per_sm;
+        })) {
+        CK(cudaStreamSynchronize(g->stream), "mhd_slab_group_advance");
+        group_drop_graphs(g);
+        g->graph_cfg = cfg;
+    }
+    int par = par0;
+    long long done = 0;
+    while (nsteps - done >= kGraphSteps) {
+        if (!g->graph[par]) {
+            cudaGraph_t gr = nullptr;
+            CK(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+            cudaError_t le = cudaSuccess;
+            for (int k = 0, c = par; k < kGraphSteps && le == cudaSuccess; ++k, c ^= 1) le = group_round(g, c, g->cap);
+            const cudaError_t ee = cudaStreamEndCapture(g->cap, &gr);
+            if (le != cudaSuccess) {
+                if (gr) cudaGraphDestroy(gr);
+                return cuda_fail(le, "slab group capture");
+            }
+            if (ee != cudaSuccess) return cuda_fail(ee, "end capture");
+            const cudaError_t ie = cudaGraphInstantiate(&g->graph[par], gr, 0);
+            cudaGraphDestroy(gr);
+            if (ie != cudaSuccess) return cuda_fail(ie, "graph instantiate");
+        }
+        CK(cudaGraphLaunch(g->graph[par], g->stream), "graph launch");
+        done += kGraphSteps;  // kGraphSteps is even: the parity is unchanged
+    }
+    for (; done < nsteps; ++done, par ^= 1) CK(group_round(g, par, g->stream), "slab group round");
+    for (mhd_lattice* l : g->slabs) {
+        l->cur = par;
+        l->step += nsteps;
+        l->prev_valid = true;
+        l->state_is_eq = false;
+    }
+    return MHD_OK;
+}
+
+mhd_status mhd_slab_group_destroy(mhd_slab_group* g) {
+    if (!g) return MHD_OK;
+    cudaSetDevice(g->slabs[0]->dev);
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    group_drop_graphs(g);
+    for (auto& j : g->jobs)
+        if (j) cudaFree(j);
+    if (g->cap) cudaStreamDestroy(g->cap);
+    delete g;
+    return MHD_OK;
+}
+
 mhd_status mhd_get_state(mhd_lattice* l, void* host, size_t bytes) {
     size_t need = 0;
     if (!host || mhd_state_bytes(l, &need) != MHD_OK) return fail(MHD_EINVAL, "NULL argument");

@@ -68,6 +68,17 @@ struct HaloPlanes {
 // base address is a multiple of 16 bytes
 cudaError_t launch_halo_rows(const void* src, void* dst, long long src_plane, long long dst_plane, long long src_off,
                              long long dst_off, long long bytes, const HaloPlanes& hp, cudaStream_t st);
+// one copy of a slab group's exchange: the 5 crossing planes of one padded
+// row, src and dst already at the row (plane 0), plane strides in bytes
+struct HaloJob {
+    const char* src;
+    char* dst;
+    long long src_plane, dst_plane;
+    int planes[5];
+};
+// every job of a device job table in one launch (row_bytes a multiple of
+// 16; cudaErrorInvalidValue otherwise)
+cudaError_t launch_halo_jobs(const HaloJob* jobs, int njobs, long long row_bytes, cudaStream_t st);
 // stored state whose pull-gather reproduces the packed FP32 pre-collision
 // state F (periodic axes)
 cudaError_t launch_unstream(const Layout& L, int prec, void* buf, const float* F, cudaStream_t st);

@@ -233,6 +233,26 @@ cudaError_t launch_halo_rows(const void* src, void* dst, long long src_plane, lo
     return cudaGetLastError();
 }
 
+// The exchanges of a whole slab group in one launch: block (x, job, k)
+// copies a share of plane planes[k] of job's row, in 16-byte pieces.
+__global__ void halo_jobs_kernel(const HaloJob* __restrict__ jobs, long long n16) {
+    const HaloJob& j = jobs[blockIdx.y];
+    const long long p = j.planes[blockIdx.z];
+    const uint4* s = reinterpret_cast<const uint4*>(j.src + p * j.src_plane);
+    uint4* d = reinterpret_cast<uint4*>(j.dst + p * j.dst_plane);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n16; k += (long long)gridDim.x * blockDim.x)
+        d[k] = s[k];
+}
+
+cudaError_t launch_halo_jobs(const HaloJob* jobs, int njobs, long long row_bytes, cudaStream_t st) {
+    if (njobs < 1 || njobs > 65535 || row_bytes % 16 || reinterpret_cast<uintptr_t>(jobs) % alignof(HaloJob))
+        return cudaErrorInvalidValue;
+    const long long n16 = row_bytes / 16;
+    const long long bx = std::max(1LL, std::min((n16 + 255) / 256, 16LL));
+    halo_jobs_kernel<<<dim3((unsigned)bx, (unsigned)njobs, 5), 256, 0, st>>>(jobs, n16);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_unstream(const Layout& L, int prec, void* buf, const float* F, cudaStream_t st) {
     MHD_DISPATCH(prec, unstream_kernel, flat_grid((long long)L.nx * L.ny), 256, st, L, buf, F);
     return cudaGetLastError();

@@ -22,7 +22,7 @@ import math
 
 import numpy as np
 
-from ._abi import Lattice, slab_exchange
+from ._abi import Lattice, SlabSteps, slab_exchange
 
 # c_y of the 19 populations: D2Q9 (the paper's order) and D2Q5 (each twice)
 _CY_F = (0, 1, 0, -1, -1, -1, 0, 1, 1)
@@ -101,9 +101,12 @@ def allreduce_totals(totals: dict, rows: int, nx: int, wall_x: bool = False, gro
 
 class SlabGroup:
     """The slabs of one nx x ny lattice with a periodic y axis, all on the
-    current device: every step advances each slab and then exchanges every
-    boundary (mhd_slab_exchange).  Fields, populations and totals are those
-    of the whole lattice."""
+    current device and one stream: every step advances each slab and then
+    exchanges every boundary -- through the library's slab group
+    (mhd_slab_group_advance: one exchange kernel per round, 64-round CUDA
+    graphs), or, with stepwise=True, one mhd_advance per slab and one
+    mhd_slab_exchange per boundary and step.  Fields, populations and totals
+    are those of the whole lattice."""
 
     def __init__(self, nx, ny, nslabs, tau_f, tau_m, precision="fp32", rows=None, stream=None, **kw):
         self.nx, self.ny = int(nx), int(ny)
@@ -115,8 +118,12 @@ class SlabGroup:
         self.slabs = [Lattice(nx, y1 - y0, tau_f, tau_m, precision=precision, halo_y=True, stream=stream, **kw)
                       for y0, y1 in self.rows]
         self.schedule = exchange_schedule(len(self.slabs))
+        self._steps = None
 
     def close(self):
+        if self._steps is not None:
+            self._steps.close()
+            self._steps = None
         for s in self.slabs:
             s.close()
 
@@ -150,11 +157,16 @@ class SlabGroup:
             s.set_populations(np.ascontiguousarray(f[:, y0:y1]), np.ascontiguousarray(g[:, :, y0:y1]))
         self.exchange()
 
-    def advance(self, nsteps: int):
-        for _ in range(int(nsteps)):
-            for s in self.slabs:
-                s.advance(1)
-            self.exchange()
+    def advance(self, nsteps: int, stepwise: bool = False):
+        if stepwise:
+            for _ in range(int(nsteps)):
+                for s in self.slabs:
+                    s.advance(1)
+                self.exchange()
+            return
+        if self._steps is None:
+            self._steps = SlabSteps(self.slabs)
+        self._steps.advance(nsteps)
 
     def get_fields(self) -> dict:
         parts = [s.get_fields() for s in self.slabs]

@@ -87,3 +87,63 @@ def test_exchange_rejects_mismatched_lattices():
             _abi.slab_exchange(a, c)
     with pytest.raises(MhdError, match="EINVAL"):
         Lattice(32, 8, 0.6, 0.6, halo_y=True, in_place=True)
+
+
+@pytest.mark.parametrize("prec,nslabs", [("fp32", 2), ("fp16s", 3), ("fp64", 2)])
+def test_slab_group_matches_stepwise_slabs_and_the_whole_lattice(prec, nslabs):
+    """mhd_slab_group_advance (every round's exchanges in one kernel, runs of
+    64 rounds in a CUDA graph) gives the bits of the slabs stepped one by one
+    with one exchange call per boundary, and of the whole lattice: over 130
+    steps (two graphs and two single rounds), again after a change of launch
+    shape (the group's graphs are captured anew), and the step counters
+    advance as for single slabs."""
+    from paper_2602_14667_gb300 import Lattice
+    from paper_2602_14667_gb300.slabs import SlabGroup
+    nx, ny = 96, 64
+    fields = _fields(nx, ny, 6)
+    with Lattice(nx, ny, 0.55, 0.6, precision=prec) as whole, \
+            SlabGroup(nx, ny, nslabs, 0.55, 0.6, precision=prec) as a, \
+            SlabGroup(nx, ny, nslabs, 0.55, 0.6, precision=prec) as b:
+        for lat in (whole, a, b):
+            lat.kernel_config = (2, 4)
+            lat.set_fields(*fields)
+        whole.advance(130)
+        a.advance(130)
+        b.advance(130, stepwise=True)
+        pw, pa, pb = whole.get_populations(), a.get_populations(), b.get_populations()
+        assert all(np.array_equal(x, y) for x, y in zip(pa, pb)) and all(np.array_equal(x, y) for x, y in zip(pa, pw))
+        for lat in (whole, a):
+            lat.kernel_config = (1, 8)
+        whole.advance(65)
+        a.advance(65)
+        assert all(np.array_equal(x, y) for x, y in zip(a.get_populations(), whole.get_populations()))
+        assert all(s.get_totals()["step"] == 195 for s in a.slabs)
+
+
+def test_slab_group_rejects_what_it_cannot_step():
+    import torch
+
+    from paper_2602_14667_gb300 import Lattice, MhdError, _abi
+    nx = 32
+    s1 = torch.cuda.Stream()
+    with Lattice(nx, 8, 0.6, 0.6, halo_y=True) as a, Lattice(nx, 8, 0.6, 0.6, halo_y=True) as b, \
+            Lattice(nx, 8, 0.6, 0.6) as c, Lattice(48, 8, 0.6, 0.6, halo_y=True) as d, \
+            Lattice(nx, 8, 0.6, 0.6, halo_y=True, stream=s1.cuda_stream) as e:
+        for bad in ([a, c], [a, d], [a, e]):
+            with pytest.raises(MhdError, match="EINVAL"):
+                _abi.SlabSteps(bad)
+        g = _abi.SlabSteps([a, b])
+        try:
+            with pytest.raises(MhdError, match="ESTATE"):  # no fields yet
+                g.advance(1)
+            f = _fields(nx, 16, 2)
+            a.set_fields(*(np.ascontiguousarray(x[:8]) for x in f))
+            b.set_fields(*(np.ascontiguousarray(x[8:]) for x in f))
+            a.advance(1)  # one slab a step ahead
+            with pytest.raises(MhdError, match="ESTATE"):
+                g.advance(1)
+            b.advance(1)
+            g.advance(3)
+            assert a.get_totals()["step"] == b.get_totals()["step"] == 4
+        finally:
+            g.close()
