@@ -306,6 +306,8 @@ def extra_rows(fp32_mlups, peak):
                 an FP64 run of the same lattice (relative L2 of u and b);
       ensemble  the 512-lattice random-spectrum ensemble (39 M nodes) in one
                 persistent launch per step (100 steps);
+      cost_scaling  time per step of the RR and BGK collisions at 1024^2,
+                2048^2 and 4096^2 (the paper's runtime-scaling figure);
       diagnostics, closure_step, closure
                 the --workload lines of the global totals (4096^2 FP32,
                 100 calls), of the closure step's cost (512^2, 512 steps) and
@@ -371,6 +373,22 @@ def extra_rows(fp32_mlups, peak):
                        "kernel_config": list(bshape),
                        "roofline": {"bound": "hbm", "achieved": gbsb, "peak": peak, "unit": "GB/s",
                                     "frac": gbsb / peak, "bytes_per_node": 152}}
+    # The paper's only cost result (Fig. runtime_scaling): runtime linear in
+    # N^2 with the RR collision above BGK.  Here: FP32, tau 0.51 (where BGK
+    # is stable too), 200 graph-launched steps per lattice.
+    from paper_2602_14667_gb300 import MHD_BGK, MHD_RR
+    cost = {}
+    for name, coll in (("rr", MHD_RR), ("bgk", MHD_BGK)):
+        cost[name] = {}
+        for m in (1024, 2048, 4096):
+            with Lattice(m, m, 0.51, 0.51, precision="fp32", collision=coll, stream=stream.cuda_stream) as lat:
+                lat.set_fields(*mhd_inputs.orszag_tang(m, 0.04, 0.04))
+                ms = timed(lat, 200)
+            cost[name][str(m)] = {"ms_per_step": ms, "ns_per_node": ms * 1e6 / (m * m)}
+    out["cost_scaling"] = {"collisions": cost, "rr_over_bgk_time_4096": cost["rr"]["4096"]["ms_per_step"]
+                           / cost["bgk"]["4096"]["ms_per_step"],
+                           "note": "the paper's Fig. runtime_scaling: runtime linear in N^2, RR slower than BGK "
+                                   "(C++/Kokkos, hardware unstated, no absolute values)"}
     d = diagnostics_line(4096, "fp32", 100, 3)
     out["diagnostics"] = {k: d[k] for k in ("metric", "value", "unit", "ms_per_call", "config", "roofline")}
     c = closure_step_line(512, 512, 64)
