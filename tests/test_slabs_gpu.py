@@ -89,7 +89,7 @@ def test_exchange_rejects_mismatched_lattices():
         Lattice(32, 8, 0.6, 0.6, halo_y=True, in_place=True)
 
 
-@pytest.mark.parametrize("prec,nslabs", [("fp32", 2), ("fp16s", 3), ("fp64", 2)])
+@pytest.mark.parametrize("prec,nslabs", [("fp32", 2), ("fp16s", 3), ("fp64", 2), ("fp32", 1), ("fp32", 4)])
 def test_slab_group_matches_stepwise_slabs_and_the_whole_lattice(prec, nslabs):
     """mhd_slab_group_advance (every round's exchanges in one kernel, runs of
     64 rounds in a CUDA graph) gives the bits of the slabs stepped one by one
