@@ -184,3 +184,15 @@ def test_bench_reads_profile_keys_only_for_matching_sources_and_shapes():
     finally:
         os.remove(tmp)
     assert bench.profiled("nonexistent", (4, 1), "dram_bytes_per_node") is None
+
+
+def test_launch_shapes_take_two_or_three_numbers():
+    """A launch shape is (nodes_per_thread, rows_per_block[, warps_per_sm]);
+    two numbers keep the built-in staging depth (warps_per_sm = 0)."""
+    from paper_2602_14667_gb300 import _abi
+    c = _abi._shape_in((4, 1))
+    assert (c.nodes_per_thread, c.rows_per_block, c.warps_per_sm) == (4, 1, 0)
+    assert _abi._shape_out(_abi._shape_in([2, 8, 16])) == (2, 8, 16)
+    for bad in ((4,), (1, 2, 3, 4)):
+        with pytest.raises(ValueError):
+            _abi._shape_in(bad)
