@@ -350,6 +350,36 @@ def test_closure_step_matches_oracle_on_tall_ragged_tiles(orc, kind):
 
 
 @KINDS
+def test_closure_step_matches_oracle_at_the_coarse_workload_size(orc, kind):
+    """The closure step's timed workload: a 512 x 512 coarse lattice at
+    tau = 0.505, in the launch configuration the closure-step benchmark uses
+    (the library's own tiling: 18 strips of 30 columns, the last of 2, and
+    row segments of 4 rows); one step matches the oracle node by node."""
+    from oracle import closure as clo
+    from paper_2602_14667_gb300 import Lattice, _abi
+    nx = ny = 512
+    p, f, g = _state(orc, nx, ny, 13, steps=2, tau=(0.505, 0.505))
+    st = _packed(f, g)
+    f64, g64 = _unpacked(st, nx, ny)
+    Xo, _ = clo.features(p, f64, g64)
+    net = _random_net(clo, Xo, np.full((4, 3), 1.0), seed=11)
+    net.p["out_scale"][:] = 2e-5
+    with _abi.MLP(seed=0, max_batch=64) as m, Lattice(nx, ny, p.tau_f, p.tau_m, precision="fp32") as lat:
+        m.set_params(net.flat())
+        ref_net = clo.MLP.from_flat(m.get_params())
+        _abi.set_closure(lat, m)
+        _abi.set_closure_kernel(lat, kind)
+        _abi.set_precollision_state(lat, st)
+        lat.advance(1)
+        fg, gg = lat.get_populations()
+    da, _ = ref_net.forward(Xo, bf16_like_gpu=True)
+    fs, gs = orc.collide_da(p, f64, g64, da.reshape(ny, nx, 3))
+    fp, _ = orc.collide(p, f64, g64)
+    assert np.abs(fs - fp).max() > 1e-6
+    assert np.abs(fg - fs).max() < 3e-6 and np.abs(gg - gs).max() < 2e-6, (np.abs(fg - fs).max(), np.abs(gg - gs).max())
+
+
+@KINDS
 def test_closure_keeps_mass_and_momentum(kind):
     import mhd_inputs
     from oracle import closure as clo

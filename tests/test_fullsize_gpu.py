@@ -8,7 +8,8 @@ oracle collides that node, and the GPU's post-step populations at the node
 must agree (FP32: 2e-6; FP16S: the half-rounding bound of the one-step
 test).  Samples cover random interior nodes plus every warp / vector-lane /
 tile edge column and the first and last rows.  Conservation over the bench's
-600 steps is checked on the whole lattice.
+600 steps, and the global diagnostics against the oracle's, are checked on
+the whole lattice.
 """
 import json
 import os
@@ -76,6 +77,29 @@ def test_orszag_tang_4096_sampled_nodes(orc, prec, code):
     xs, ys = _samples(n, n, rng)
     worst = _check_nodes(orc, p, Pf, Pg, Qf, Qg, xs, ys, tol)
     print(f"{prec} 4096^2: {len(xs)} nodes, worst |GPU - oracle| = {worst:.2e} (tol {tol:.1e})")
+
+
+@pytest.mark.parametrize("prec,code", [("fp32", 1), ("fp16s", 2)])
+def test_orszag_tang_4096_totals_against_oracle(orc, prec, code):
+    """The diagnostics of the timed 4096^2 workload, whole: the totals of the
+    pre-collision state the last step gathered against the oracle's totals
+    of the stream of the state that step read (the bounds of the
+    diagnostics tests; the fields are smooth, so div b stays at the FP32
+    rounding floor of the moments)."""
+    import mhd_inputs
+    from test_diag_gpu import _check
+    from paper_2602_14667_gb300 import Lattice
+    n, tau = 4096, 0.50006
+    p = orc.Params(n, n, tau, tau)
+    with Lattice(n, n, tau, tau, precision=prec) as lat:
+        lat.kernel_config = _bench_shape(code, n)
+        lat.set_fields(*mhd_inputs.orszag_tang(n, 0.04, 0.04))
+        lat.advance(23)
+        Pf, Pg = lat.get_populations()
+        lat.advance(1)
+        got = lat.get_totals()
+    ref = orc.totals(p, *orc.stream(p, Pf, Pg))
+    _check(got, ref, n * n, False)
 
 
 def test_orszag_tang_4096_conservation_over_bench_steps():
