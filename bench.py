@@ -98,7 +98,7 @@ def measured_peaks():
 # The device code of the step kernels: step.cu and the device headers it
 # includes (internal.h holds only host declarations).
 STEP_KERNEL_SOURCES = ("f32x2.cuh", "lbm_device.cuh", "step.cu", "step_row.cuh")
-DIAG_KERNEL_SOURCES = ("diag.cu", "f32x2.cuh", "lbm_device.cuh", "step_row.cuh")
+DIAG_KERNEL_SOURCES = ("diag.cu", "diag_device.cuh", "f32x2.cuh", "lbm_device.cuh", "step_row.cuh")
 
 
 def kernel_source_hash(sources=STEP_KERNEL_SOURCES):
@@ -390,7 +390,8 @@ def extra_rows(fp32_mlups, peak):
                            "note": "the paper's Fig. runtime_scaling: runtime linear in N^2, RR slower than BGK "
                                    "(C++/Kokkos, hardware unstated, no absolute values)"}
     d = diagnostics_line(4096, "fp32", 100, 3)
-    out["diagnostics"] = {k: d[k] for k in ("metric", "value", "unit", "ms_per_call", "config", "roofline")}
+    out["diagnostics"] = {k: d[k] for k in ("metric", "value", "unit", "ms_per_call", "config", "roofline",
+                                            "sample_step")}
     c = closure_step_line(512, 512, 64)
     out["closure_step"] = {k: c[k] for k in ("metric", "value", "unit", "ms_per_step", "config", "roofline")}
     cl = closure_line()
@@ -877,6 +878,31 @@ def diagnostics_line(n, prec, steps, warmup):
             e1.record(stream)
             e1.synchronize()
         ms = e0.elapsed_time(e1) / steps
+
+        # A sample step three ways, one step per call: the plain step alone;
+        # the step then the diagnostics pass (mhd_advance + mhd_get_totals);
+        # the fused step that reduces the point totals (mhd_advance_totals).
+        def per_call(fn):
+            for _ in range(3):
+                fn()
+            stream.synchronize()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(steps):
+                fn()
+            a1.record(stream)
+            a1.synchronize()
+            return a0.elapsed_time(a1) / steps
+
+        ms_plain = per_call(lambda: lat.advance(1))
+        ms_pass = per_call(lambda: (lat.advance(1), lat.get_totals()))
+        ms_fused = per_call(lambda: lat.advance_totals(1))
+        sample = {"ms_plain_step": ms_plain, "ms_step_then_totals_pass": ms_pass, "ms_fused_step": ms_fused,
+                  "extra_ms_totals_pass": ms_pass - ms_plain, "extra_ms_fused": ms_fused - ms_plain,
+                  "note": "one step per call; the pass and the fused step include the copy of the totals "
+                          "to the host and the host's wait; the fused step gives the point totals (mass, "
+                          "momentum, energies, cross helicity, sum b, max |j_z|), the pass every total"}
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
         peak = float(json.load(fh)["hbm_gbs"])
     per_node = 19 * ESIZE[prec]
@@ -893,7 +919,8 @@ def diagnostics_line(n, prec, steps, warmup):
            "config": {"workload": f"diagnostics_orszag_tang_{n}x{n}_{prec}", "nx": n, "ny": n,
                       "calls": steps, "l2": "no flush: the state is far above the 129 MB L2"},
            "totals_sample": {"mass": tot["mass"], "divb_max": tot["divb_max"], "jz_max": tot["jz_max"]},
-           "clocks": clk.summary(), "gpu_launches": 2 * steps, "roofline": roofline}
+           "clocks": clk.summary(), "gpu_launches": 2 * steps, "roofline": roofline,
+           "sample_step": sample}
     return out
 
 

@@ -192,6 +192,23 @@ mhd_status mhd_get_fields_f32(mhd_lattice* l, float* rho, float* ux, float* uy, 
  * when tau_m = 1, where that inverse does not exist). */
 mhd_status mhd_get_totals(mhd_lattice* l, mhd_totals* out);
 
+/* Advance nsteps >= 1 steps (as mhd_advance) and return the point totals of
+ * the pre-collision state the last step gathered -- the quantities of
+ * mhd_totals that need no neighbour of a node: mass, momentum, e_kin, e_mag,
+ * cross_hel, bsum and jz_max, with the definitions and arithmetic of
+ * mhd_get_totals (the task 1 moments, Eq. current, the energies of the
+ * Orszag-Tang section; FP64 only in the reductions).  The last step forms
+ * them from the populations it holds for its collision, so this sample step
+ * costs about what a plain step does (one read and one write of the state,
+ * no diagnostics pass).  divb_max, divb_rms and omega_max need the 3 x 3
+ * neighbourhood and are set to NaN here (mhd_get_totals gives them).  The
+ * populations written are those of mhd_advance, bit for bit.  Two-buffer
+ * lattices with a periodic x axis, no closure and no ghost rows; for other
+ * lattices the call is mhd_advance followed by mhd_get_totals (all fields
+ * filled).  Waits for the stream.  nsteps < 1 -> MHD_EINVAL; a non-finite
+ * point total -> MHD_EUNSTABLE (with *out filled). */
+mhd_status mhd_advance_totals(mhd_lattice* l, long long nsteps, mhd_totals* out);
+
 /* Checkpoint: the stored post-collision populations as unshifted FP64 values.
  * f: 9*nx*ny doubles, plane i at f + i*nx*ny (i in the paper's D2Q9 order);
  * g: 10*nx*ny doubles, component a of g_j at g + (2*j + a)*nx*ny.

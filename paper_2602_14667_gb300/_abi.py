@@ -78,6 +78,7 @@ _SIGNATURES = {
     "mhd_set_fields_f32": [_P, _F, _F, _F, _F, _F],
     "mhd_get_fields_f32": [_P, _F, _F, _F, _F, _F],
     "mhd_get_totals": [_P, ctypes.POINTER(mhd_totals)],
+    "mhd_advance_totals": [_P, ctypes.c_longlong, ctypes.POINTER(mhd_totals)],
     "mhd_get_populations": [_P, _D, _D],
     "mhd_set_populations": [_P, _D, _D],
     "mhd_get_kernel_config": [_P, ctypes.POINTER(mhd_kernel_config)],
@@ -254,6 +255,17 @@ class Lattice:
         st = lib().mhd_get_totals(self._h, ctypes.byref(t))
         if st != MHD_EUNSTABLE or check_stable:
             check(st, "mhd_get_totals")
+        d = {n: getattr(t, n) for n in TOTAL_FIELDS}
+        d["step"] = t.step
+        return d
+
+    def advance_totals(self, nsteps: int, check_stable: bool = True) -> dict:
+        """mhd_advance_totals: advance, the last step reducing the point
+        totals (divb_max, divb_rms, omega_max are NaN on the fused path)."""
+        t = mhd_totals()
+        st = lib().mhd_advance_totals(self._h, int(nsteps), ctypes.byref(t))
+        if st != MHD_EUNSTABLE or check_stable:
+            check(st, "mhd_advance_totals")
         d = {n: getattr(t, n) for n in TOTAL_FIELDS}
         d["step"] = t.step
         return d

@@ -14,6 +14,7 @@
 #include <climits>
 #include <cstdint>
 
+#include "diag_device.cuh"
 #include "internal.h"
 #include "lbm_device.cuh"
 #include "step_row.cuh"
@@ -68,97 +69,6 @@ template <typename C> struct DiagArgs {
     int rows;          // output rows per tile (H)
     int ntiles;
 };
-
-// ---- accumulation helpers -------------------------------------------------
-template <typename C> struct LaneSum {
-    double s = 0.0;
-    __device__ __forceinline__ void add(double x) { s += x; }
-    __device__ __forceinline__ double take() {
-        const double v = s;
-        s = 0.0;
-        return v;
-    }
-};
-template <> struct LaneSum<float> {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float x) {
-        const float t = s + x;
-        const float bv = t - s;
-        const float e = (s - (t - bv)) + (x - bv);
-        s = t;
-        c += e;
-    }
-    __device__ __forceinline__ double take() {
-        const double v = (double)s + (double)c;
-        s = c = 0.f;
-        return v;
-    }
-};
-
-template <typename C> struct AbsBits;
-template <> struct AbsBits<double> {
-    using T = unsigned long long;
-    __device__ __forceinline__ static T of(double v) {
-        return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
-    }
-    __device__ __forceinline__ static double value(T b) { return __longlong_as_double((long long)b); }
-};
-template <> struct AbsBits<float> {
-    using T = unsigned int;
-    __device__ __forceinline__ static T of(float v) { return __float_as_uint(v) & 0x7fffffffu; }
-    __device__ __forceinline__ static double value(T b) { return (double)__uint_as_float(b); }
-};
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-    return v;
-}
-__device__ __forceinline__ unsigned long long warp_max_bits(unsigned long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long w = __shfl_down_sync(kFull, v, o);
-        v = w > v ? w : v;
-    }
-    return v;
-}
-__device__ __forceinline__ unsigned long long dbits(double v) {
-    return (unsigned long long)__double_as_longlong(fabs(v));
-}
-__device__ __forceinline__ unsigned long long max_bits(unsigned long long a, unsigned long long b) {
-    return a > b ? a : b;
-}
-
-// ---- one node's moments -----------------------------------------------------
-template <typename C> struct NodeMom {
-    C drho, mx, my, bx, by, ux, uy;
-    C dg;  // (g_3y - g_1y) - (g_4x - g_2x): the e-weighted antisymmetric part entering j_z
-};
-
-// From populations in `unit`s of the deviation (FP16S storage units: 2^-12).
-template <typename C>
-__device__ __forceinline__ NodeMom<C> node_moments(const C (&f)[9], const C (&g)[10], C unit, C rho0) {
-    Moments<C> m;
-    moment_sums(f, g, m);
-    NodeMom<C> n;
-    n.drho = m.drho * unit;
-    n.mx = m.mx * unit;
-    n.my = m.my * unit;
-    n.bx = m.bx * unit;
-    n.by = m.by * unit;
-    const C inv = C(1) / (rho0 + n.drho);
-    n.ux = n.mx * inv;
-    n.uy = n.my * inv;
-    n.dg = ((g[7] - g[3]) - (g[8] - g[4])) * unit;
-    return n;
-}
-
-// Eq. current with g_eq of the node substituted: for D2Q5,
-// sum_j (e_jx g_neq_jy - e_jy g_neq_jx) = dg - 2 (u_x b_y - u_y b_x).
-template <typename C>
-__device__ __forceinline__ C node_current(const NodeMom<C>& n, C omega_m, C neq_scale) {
-    return -C(3) * omega_m * neq_scale * (n.dg - C(2) * (n.ux * n.by - n.uy * n.bx));
-}
 
 // u, b of one node (x, y) inside the lattice, one population at a time:
 // mode 0 gathers the pre-collision state, mode 1 reads the stored one.
@@ -290,14 +200,7 @@ __global__ void __launch_bounds__(kDWarps * 32, PREC == 0 ? 1 : 2) diag_kernel(c
                         for (int k = 0; k < V; ++k) {
                             if (xl + k < a.nx) {
                                 const NodeMom<C>& n = nm[k];
-                                ps[0] += n.drho;
-                                ps[1] += n.mx;
-                                ps[2] += n.my;
-                                ps[3] += C(0.5) * (n.ux * n.ux + n.uy * n.uy);
-                                ps[4] += C(0.5) * (n.bx * n.bx + n.by * n.by);
-                                ps[5] += n.ux * n.bx + n.uy * n.by;
-                                ps[6] += n.bx;
-                                ps[7] += n.by;
+                                add_point_sums(n, ps);
                                 mjz = max(mjz, MB::of(node_current(n, a.omega_m, a.neq_scale)));
                             }
                         }
@@ -494,7 +397,13 @@ cudaError_t launch_diag(const DiagLaunch& d, double* partials, int capacity, dou
     default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
-    diag_final<<<1, 256, 0, st>>>(partials, nblocks, d.rho0 * (double)d.L.nx * (double)d.L.ny, totals);
+    return launch_diag_final(partials, nblocks, d.rho0 * (double)d.L.nx * (double)d.L.ny, totals, st);
+}
+
+cudaError_t launch_diag_final(const double* partials, int nblocks, double mass_base, double* totals,
+                              cudaStream_t st) {
+    if (nblocks < 1) return cudaErrorInvalidValue;
+    diag_final<<<1, 256, 0, st>>>(partials, nblocks, mass_base, totals);
     return cudaGetLastError();
 }
 

@@ -108,6 +108,19 @@ struct DiagLaunch {
 };
 int diag_blocks(const Layout& L);
 cudaError_t launch_diag(const DiagLaunch& d, double* partials, int capacity, double* totals, cudaStream_t st);
+// The fixed-order reduction of `nblocks` per-block partials into `totals`
+// (slot 0 plus mass_base: the mass).
+cudaError_t launch_diag_final(const double* partials, int nblocks, double mass_base, double* totals,
+                              cudaStream_t st);
+
+// One step (as launch_step, two buffers, periodic x; s.V nodes per lane)
+// that also reduces the point totals of the pre-collision state it gathers
+// into `totals` (kDiagSlots doubles, the diagnostics' slots; the slots of
+// the gradient quantities, 8, 9, 10 and 12, are zero) through at most
+// `capacity` per-block partials.  The populations it writes are those of
+// launch_step.  cudaErrorInvalidValue for x walls.
+cudaError_t launch_step_totals(const StepLaunch& s, double* partials, int capacity, double* totals,
+                               cudaStream_t st);
 
 Layout make_layout(int nx, int ny, int prec);
 
