@@ -353,6 +353,13 @@ mhd_status mhd_batch_advance(mhd_batch* b, long long nsteps);
 mhd_status mhd_batch_get_fields(mhd_batch* b, int index, double* rho, double* ux, double* uy,
                                 double* bx, double* by);
 mhd_status mhd_batch_get_totals(mhd_batch* b, int index, mhd_totals* out);
+/* The totals of every lattice of the batch (as mhd_batch_get_totals of each
+ * index, bit for bit) into out[0 .. count-1]: the diagnostics of all the
+ * lattices are queued back to back and copied back once, with one wait for
+ * the stream instead of one per lattice.  A lattice whose fields were not
+ * set -> MHD_ESTATE (nothing written); a non-finite total in any lattice ->
+ * MHD_EUNSTABLE, with every entry filled. */
+mhd_status mhd_batch_get_all_totals(mhd_batch* b, mhd_totals* out);
 /* total number of nodes over all lattices */
 mhd_status mhd_batch_nodes(const mhd_batch* b, long long* nodes);
 /* launch shape (nodes_per_thread must divide every nx; warps_per_sm 0 keeps

@@ -251,8 +251,9 @@ mhd_status mhd_batch_create(int count, const int* nx, const int* ny, const mhd_p
     int maxblocks = 0;
     for (auto& L : b->layouts) maxblocks = std::max(maxblocks, mhd::diag_blocks(L));
     if (e == cudaSuccess) e = cudaMalloc(&b->partials, sizeof(double) * mhd::kDiagSlots * maxblocks);
-    if (e == cudaSuccess) e = cudaMalloc(&b->totals_d, sizeof(double) * mhd::kDiagSlots);
-    if (e == cudaSuccess) e = cudaMallocHost(&b->totals_h, sizeof(double) * mhd::kDiagSlots);
+    // one slot set of totals per lattice (mhd_batch_get_all_totals)
+    if (e == cudaSuccess) e = cudaMalloc(&b->totals_d, sizeof(double) * mhd::kDiagSlots * b->count);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->totals_h, sizeof(double) * mhd::kDiagSlots * b->count);
     if (e != cudaSuccess) {
         cudaGetLastError();
         mhd_batch_destroy(b);
@@ -392,12 +393,8 @@ mhd_status mhd_batch_get_fields(mhd_batch* b, int index, double* rho, double* ux
     return MHD_OK;
 }
 
-mhd_status mhd_batch_get_totals(mhd_batch* b, int index, mhd_totals* out) {
-    mhd_status s = batch_index(b, index);
-    if (s != MHD_OK) return s;
-    if (!out) return bfail(MHD_EINVAL, "out is NULL");
-    if (!b->set[index]) return bfail(MHD_ESTATE, "fields of this lattice were not set");
-    BCK(cudaSetDevice(b->dev), "cudaSetDevice");
+// The diagnostics pass of lattice `index` into slot set `slot` of totals_d.
+static cudaError_t batch_diag(mhd_batch* b, int index, int slot) {
     const mhd::Layout& L = b->layouts[index];
     mhd::DiagLaunch d;
     d.L = L;
@@ -410,12 +407,12 @@ mhd_status mhd_batch_get_totals(mhd_batch* b, int index, mhd_totals* out) {
     const double om1 = 1.0 - d.omega_m;
     d.neq_scale = d.mode == 0 ? 1.0 : ((b->is_eq[index] || std::fabs(om1) < 1e-12) ? 0.0 : 1.0 / om1);
     d.wall_x = d.wall_y = 0;
-    BCK(mhd::launch_diag(d, b->partials, mhd::diag_blocks(L), b->totals_d, b->stream), "diagnostics kernel");
-    BCK(cudaMemcpyAsync(b->totals_h, b->totals_d, sizeof(double) * mhd::kDiagSlots, cudaMemcpyDeviceToHost,
-                        b->stream),
-        "D2H totals");
-    BCK(cudaStreamSynchronize(b->stream), "mhd_batch_get_totals");
-    const double* t = b->totals_h;
+    return mhd::launch_diag(d, b->partials, mhd::diag_blocks(L), b->totals_d + (long long)mhd::kDiagSlots * slot,
+                            b->stream);
+}
+
+static bool batch_totals_out(const mhd_batch* b, int index, const double* t, mhd_totals* out) {
+    const mhd::Layout& L = b->layouts[index];
     const double n = (double)L.nx * L.ny;
     out->mass = t[0]; out->mom_x = t[1]; out->mom_y = t[2];
     out->e_kin = t[3] / n; out->e_mag = t[4] / n; out->cross_hel = t[5] / n;
@@ -424,7 +421,43 @@ mhd_status mhd_batch_get_totals(mhd_batch* b, int index, mhd_totals* out) {
     out->divb_max = t[10]; out->jz_max = t[11]; out->omega_max = t[12];
     out->step = b->step;
     for (int k = 0; k < mhd::kDiagSlots; ++k)
-        if (!std::isfinite(t[k])) return bfail(MHD_EUNSTABLE, "non-finite diagnostics: the run blew up");
+        if (!std::isfinite(t[k])) return false;
+    return true;
+}
+
+mhd_status mhd_batch_get_totals(mhd_batch* b, int index, mhd_totals* out) {
+    mhd_status s = batch_index(b, index);
+    if (s != MHD_OK) return s;
+    if (!out) return bfail(MHD_EINVAL, "out is NULL");
+    if (!b->set[index]) return bfail(MHD_ESTATE, "fields of this lattice were not set");
+    BCK(cudaSetDevice(b->dev), "cudaSetDevice");
+    BCK(batch_diag(b, index, 0), "diagnostics kernel");
+    BCK(cudaMemcpyAsync(b->totals_h, b->totals_d, sizeof(double) * mhd::kDiagSlots, cudaMemcpyDeviceToHost,
+                        b->stream),
+        "D2H totals");
+    BCK(cudaStreamSynchronize(b->stream), "mhd_batch_get_totals");
+    if (!batch_totals_out(b, index, b->totals_h, out))
+        return bfail(MHD_EUNSTABLE, "non-finite diagnostics: the run blew up");
+    return MHD_OK;
+}
+
+mhd_status mhd_batch_get_all_totals(mhd_batch* b, mhd_totals* out) {
+    if (!b || !out) return bfail(MHD_EINVAL, "NULL argument");
+    for (int i = 0; i < b->count; ++i)
+        if (!b->set[i]) return bfail(MHD_ESTATE, "the fields of every lattice must be set");
+    BCK(cudaSetDevice(b->dev), "cudaSetDevice");
+    // every lattice's pass queued back to back (the partials are reused in
+    // stream order), one copy of all the totals, one wait
+    for (int i = 0; i < b->count; ++i) BCK(batch_diag(b, i, i), "diagnostics kernel");
+    BCK(cudaMemcpyAsync(b->totals_h, b->totals_d, sizeof(double) * mhd::kDiagSlots * b->count,
+                        cudaMemcpyDeviceToHost, b->stream),
+        "D2H totals");
+    BCK(cudaStreamSynchronize(b->stream), "mhd_batch_get_all_totals");
+    int bad = -1;
+    for (int i = 0; i < b->count; ++i)
+        if (!batch_totals_out(b, i, b->totals_h + (long long)mhd::kDiagSlots * i, out + i) && bad < 0) bad = i;
+    if (bad >= 0)
+        return bfail(MHD_EUNSTABLE, "non-finite diagnostics in lattice " + std::to_string(bad) + ": the run blew up");
     return MHD_OK;
 }
 

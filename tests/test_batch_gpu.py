@@ -90,3 +90,21 @@ def test_batch_errors():
         assert _abi.lib().mhd_batch_get_fields(b.handle, 2, None, None, None, None, None) == _abi.MHD_EINVAL
         with pytest.raises(MhdError, match="EINVAL"):
             b.kernel_config = (3, 4)
+
+
+def test_all_totals_equal_the_per_lattice_totals():
+    """mhd_batch_get_all_totals against mhd_batch_get_totals of each index,
+    bit for bit: after 30 steps (the gathered state) and right after the
+    fields are set (the stored equilibrium); unset lattices are refused."""
+    from paper_2602_14667_gb300 import Batch, MhdError
+    with Batch(SIZES, TAUS) as b:
+        with pytest.raises(MhdError, match="ESTATE"):
+            b.get_all_totals()
+        for i, (nx, ny) in enumerate(SIZES):
+            b.set_fields(i, *_fields(i, nx, ny))
+        for steps in (0, 30):
+            b.advance(steps)
+            every = b.get_all_totals()
+            assert len(every) == len(SIZES)
+            for i in range(len(SIZES)):
+                assert every[i] == b.get_totals(i), i
