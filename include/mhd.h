@@ -353,10 +353,14 @@ mhd_status mhd_batch_advance(mhd_batch* b, long long nsteps);
 mhd_status mhd_batch_get_fields(mhd_batch* b, int index, double* rho, double* ux, double* uy,
                                 double* bx, double* by);
 mhd_status mhd_batch_get_totals(mhd_batch* b, int index, mhd_totals* out);
-/* The totals of every lattice of the batch (as mhd_batch_get_totals of each
- * index, bit for bit) into out[0 .. count-1]: the diagnostics of all the
- * lattices are queued back to back and copied back once, with one wait for
- * the stream instead of one per lattice.  A lattice whose fields were not
+/* The totals of every lattice of the batch into out[0 .. count-1]: one
+ * diagnostics launch walks the tiles of all the lattices (each tile's sums
+ * into a partial of its own, then each lattice's partials added in tile
+ * order), one copy back, one wait for the stream.  The values are those of
+ * mhd_batch_get_totals of each index up to the order of the FP64 sums (the
+ * maxima exactly); where a lattice's rows do not allow the kernel's
+ * two-node vector loads, every lattice's own pass is queued instead (then
+ * bit for bit those values).  A lattice whose fields were not
  * set -> MHD_ESTATE (nothing written); a non-finite total in any lattice ->
  * MHD_EUNSTABLE, with every entry filled. */
 mhd_status mhd_batch_get_all_totals(mhd_batch* b, mhd_totals* out);

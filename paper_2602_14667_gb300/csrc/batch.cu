@@ -101,6 +101,7 @@ struct mhd_batch {
     double* partials = nullptr;
     double* totals_d = nullptr;
     double* totals_h = nullptr;
+    mhd::DiagEnsemble diag;  // the all-lattice diagnostics tables (built on first use)
 };
 
 namespace {
@@ -284,6 +285,7 @@ mhd_status mhd_batch_destroy(mhd_batch* b) {
     if (b->partials) cudaFree(b->partials);
     if (b->totals_d) cudaFree(b->totals_d);
     if (b->totals_h) cudaFreeHost(b->totals_h);
+    mhd::diag_ensemble_destroy(b->diag);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
     return MHD_OK;
@@ -446,9 +448,31 @@ mhd_status mhd_batch_get_all_totals(mhd_batch* b, mhd_totals* out) {
     for (int i = 0; i < b->count; ++i)
         if (!b->set[i]) return bfail(MHD_ESTATE, "the fields of every lattice must be set");
     BCK(cudaSetDevice(b->dev), "cudaSetDevice");
-    // every lattice's pass queued back to back (the partials are reused in
-    // stream order), one copy of all the totals, one wait
-    for (int i = 0; i < b->count; ++i) BCK(batch_diag(b, i, i), "diagnostics kernel");
+    // one launch over the tiles of every lattice; where a lattice's rows do
+    // not allow its vector loads, every lattice's pass queued back to back
+    // (the partials are reused in stream order); then one copy, one wait
+    if (!b->diag.d_args) {
+        std::vector<double> rho0(b->count);
+        for (int i = 0; i < b->count; ++i) rho0[i] = b->params[i].rho0;
+        BCK(mhd::diag_ensemble_create(b->diag, b->layouts.data(), rho0.data(), b->count), "ensemble diagnostics tables");
+    }
+    std::vector<mhd::DiagLatticeState> st(b->count);
+    for (int i = 0; i < b->count; ++i) {
+        mhd::DiagLatticeState& d = st[i];
+        d.prev = b->buf[b->cur ^ 1] + b->offsets[i];
+        d.cur = b->buf[b->cur] + b->offsets[i];
+        d.mode = b->prev_valid[i] ? 0 : 1;
+        d.omega_m = 1.0 / b->params[i].tau_m;
+        d.rho0 = b->params[i].rho0;
+        const double om1 = 1.0 - d.omega_m;
+        d.neq_scale = d.mode == 0 ? 1.0 : ((b->is_eq[i] || std::fabs(om1) < 1e-12) ? 0.0 : 1.0 / om1);
+    }
+    const cudaError_t le = mhd::diag_ensemble_launch(b->diag, b->layouts.data(), st.data(), b->totals_d, b->stream);
+    if (le == cudaErrorNotSupported) {
+        for (int i = 0; i < b->count; ++i) BCK(batch_diag(b, i, i), "diagnostics kernel");
+    } else {
+        BCK(le, "ensemble diagnostics kernel");
+    }
     BCK(cudaMemcpyAsync(b->totals_h, b->totals_d, sizeof(double) * mhd::kDiagSlots * b->count,
                         cudaMemcpyDeviceToHost, b->stream),
         "D2H totals");

@@ -113,6 +113,35 @@ cudaError_t launch_diag(const DiagLaunch& d, double* partials, int capacity, dou
 cudaError_t launch_diag_final(const double* partials, int nblocks, double mass_base, double* totals,
                               cudaStream_t st);
 
+// The diagnostics of a whole ensemble (FP32 storage, periodic lattices) in
+// one launch over a list of (lattice, tile) pairs, then one block per
+// lattice adding its tiles' partials in order.  DiagEnsemble holds the
+// device tables, built once for the ensemble's layouts.
+struct DiagEnsemble {
+    int count = 0, ntiles = 0;
+    void* d_args = nullptr;   // per-lattice kernel arguments, refreshed by every launch
+    void* h_args = nullptr;   // their pinned host staging
+    void* d_tiles = nullptr;  // (lattice, tile) pairs
+    int* d_first = nullptr;   // first tile of each lattice (count + 1)
+    double* d_mass = nullptr;  // rho0 * nodes of each lattice
+    double* d_partials = nullptr;  // kDiagSlots per tile
+};
+// What one lattice of the ensemble reduces now: the buffer the last step
+// read (mode 0, gathered) or the stored state (mode 1, with neq_scale).
+struct DiagLatticeState {
+    const void* prev;
+    const void* cur;
+    int mode;
+    double omega_m, rho0, neq_scale;
+};
+cudaError_t diag_ensemble_create(DiagEnsemble& e, const Layout* layouts, const double* rho0, int count);
+void diag_ensemble_destroy(DiagEnsemble& e);
+// cudaErrorNotSupported when a lattice does not allow the two-node vector
+// loads (odd nx, or rows not 8-byte aligned): take launch_diag per lattice.
+// totals: kDiagSlots doubles per lattice.
+cudaError_t diag_ensemble_launch(DiagEnsemble& e, const Layout* layouts, const DiagLatticeState* states,
+                                 double* totals, cudaStream_t st);
+
 // One step (as launch_step, two buffers, periodic x; s.V nodes per lane)
 // that also reduces the point totals of the pre-collision state it gathers
 // into `totals` (kDiagSlots doubles, the diagnostics' slots; the slots of
