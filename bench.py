@@ -319,7 +319,7 @@ def extra_rows(fp32_mlups, peak):
     import torch
 
     import mhd_inputs
-    from paper_2602_14667_gb300 import Batch, Lattice
+    from paper_2602_14667_gb300 import Batch, Lattice, MhdError
     out = {}
     stream = torch.cuda.Stream()
 
@@ -368,14 +368,19 @@ def extra_rows(fp32_mlups, peak):
         msb = timed(b, 100)
         nodes = b.nodes
         # the totals of all 512 lattices: one call per lattice, and one call
-        b.get_all_totals()
-        t0 = time.perf_counter()
-        for i in range(len(draws)):
-            b.get_totals(i)
-        loop_ms = (time.perf_counter() - t0) * 1e3
-        t0 = time.perf_counter()
-        b.get_all_totals()
-        all_ms = (time.perf_counter() - t0) * 1e3
+        # (not timed if a lattice has gone non-finite)
+        loop_ms = all_ms = None
+        try:
+            b.get_all_totals()
+            t0 = time.perf_counter()
+            for i in range(len(draws)):
+                b.get_totals(i)
+            loop_ms = (time.perf_counter() - t0) * 1e3
+            t0 = time.perf_counter()
+            b.get_all_totals()
+            all_ms = (time.perf_counter() - t0) * 1e3
+        except MhdError:
+            pass
     gbsb = 152 * nodes / (msb * 1e-3) / 1e9
     out["ensemble"] = {"value": nodes / (msb * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": msb, "steps": 100,
                        "workload": "ensemble_512_random_spectrum_fp32", "lattices": len(draws), "nodes": nodes,
