@@ -94,17 +94,6 @@ __device__ __forceinline__ NodeMom<typename Prec<PREC>::C> scalar_node(
     return node_moments(f, g, C(1), a.rho0);
 }
 
-// ---- the tile kernel --------------------------------------------------------
-// V: nodes per lane (vector loads; V = 1 also for lattices whose nx is not
-// a multiple of the vector width).  GEN: x walls, one node per lane, every
-// node gathered one population at a time (nodes outside the lattice are
-// left at zero and never enter a valid stencil).  WALLY: y walls in the
-// vector gather of mode 0.
-// Launch bounds: FP32 and FP16S keep two blocks per SM (at most 128
-// registers, twice the rows in flight), FP16S with four nodes per lane
-// (8-byte loads; its register cap spills a little: 0.23 against 0.29 ms per
-// totals call at 4096^2 with one block per SM), FP32 with two (at four:
-// 0.29 against 0.26 ms).  FP64 is bound by its arithmetic.
 // The accumulators of one warp: the lane sums of slots 0..8, the count of
 // gradient nodes and the three maxima (as bit patterns).
 template <typename C> struct DiagAcc {
@@ -123,6 +112,12 @@ template <typename C> struct DiagAcc {
     }
 };
 
+// ---- the tile kernel --------------------------------------------------------
+// V: nodes per lane (vector loads; V = 1 also for lattices whose nx is not
+// a multiple of the vector width).  GEN: x walls, one node per lane, every
+// node gathered one population at a time (nodes outside the lattice are
+// left at zero and never enter a valid stencil).  WALLY: y walls in the
+// vector gather of mode 0.
 // One tile t of lattice a into the warp's accumulators.
 template <int PREC, int V, int MODE, bool WALLY, bool GEN>
 __device__ __forceinline__ void diag_tile(const DiagArgs<typename Prec<PREC>::C>& a, int t, int lane,
@@ -278,6 +273,12 @@ __device__ __forceinline__ void diag_tile(const DiagArgs<typename Prec<PREC>::C>
     }
 }
 
+// The tile kernel: a persistent grid whose warps walk tiles t, t + warps, ...
+// Launch bounds: FP32 and FP16S keep two blocks per SM (at most 128
+// registers, twice the rows in flight), FP16S with four nodes per lane
+// (8-byte loads; its register cap spills a little: 0.23 against 0.29 ms per
+// totals call at 4096^2 with one block per SM), FP32 with two (at four:
+// 0.29 against 0.26 ms).  FP64 is bound by its arithmetic.
 template <int PREC, int V, int MODE, bool WALLY, bool GEN>
 __global__ void __launch_bounds__(kDWarps * 32, PREC == 0 ? 1 : 2) diag_kernel(const DiagArgs<typename Prec<PREC>::C> a,
                                                             double* __restrict__ partials) {
