@@ -381,13 +381,33 @@ def extra_rows(fp32_mlups, peak):
             all_ms = (time.perf_counter() - t0) * 1e3
         except MhdError:
             pass
+        # a sample step of the ensemble three ways, one step per call
+        sample = None
+        try:
+            def per_call(fn, reps=20):
+                fn()
+                stream.synchronize()
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                for _ in range(reps):
+                    fn()
+                a1.record(stream)
+                a1.synchronize()
+                return a0.elapsed_time(a1) / reps
+            sample = {"ms_plain_step": per_call(lambda: b.advance(1)),
+                      "ms_step_then_all_totals": per_call(lambda: (b.advance(1), b.get_all_totals())),
+                      "ms_fused_step": per_call(lambda: b.advance_totals(1))}
+        except MhdError:
+            pass
     gbsb = 152 * nodes / (msb * 1e-3) / 1e9
     out["ensemble"] = {"value": nodes / (msb * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": msb, "steps": 100,
                        "workload": "ensemble_512_random_spectrum_fp32", "lattices": len(draws), "nodes": nodes,
                        "kernel_config": list(bshape),
                        "roofline": {"bound": "hbm", "achieved": gbsb, "peak": peak, "unit": "GB/s",
                                     "frac": gbsb / peak, "bytes_per_node": 152},
-                       "totals_ms": {"per_lattice_calls": loop_ms, "all_lattices_call": all_ms}}
+                       "totals_ms": {"per_lattice_calls": loop_ms, "all_lattices_call": all_ms},
+                       "sample_step": sample}
     # The paper's only cost result (Fig. runtime_scaling): runtime linear in
     # N^2 with the RR collision above BGK.  Here: FP32, tau 0.51 (where BGK
     # is stable too), 200 graph-launched steps per lattice.

@@ -350,6 +350,17 @@ mhd_status mhd_batch_set_fields(mhd_batch* b, int index, const double* ux, const
                                 const double* bx, const double* by, const double* rho);
 /* every lattice must have its fields set (MHD_ESTATE otherwise) */
 mhd_status mhd_batch_advance(mhd_batch* b, long long nsteps);
+/* Advance nsteps >= 1 steps (as mhd_batch_advance) and return the point
+ * totals of every lattice's pre-collision state of the last step into
+ * out[0 .. count-1]: mass, momentum, e_kin, e_mag, cross_hel, bsum and
+ * jz_max (the definitions and arithmetic of mhd_totals), formed by that
+ * step from the populations it collides, so the sample step reads and
+ * writes the ensemble once; divb_max, divb_rms and omega_max are NaN (they
+ * need the neighbourhood: mhd_batch_get_all_totals).  The populations are
+ * those of mhd_batch_advance, bit for bit.  Waits for the stream.
+ * nsteps < 1 -> MHD_EINVAL; a non-finite point total in any lattice ->
+ * MHD_EUNSTABLE, with every entry filled. */
+mhd_status mhd_batch_advance_totals(mhd_batch* b, long long nsteps, mhd_totals* out);
 mhd_status mhd_batch_get_fields(mhd_batch* b, int index, double* rho, double* ux, double* uy,
                                 double* bx, double* by);
 mhd_status mhd_batch_get_totals(mhd_batch* b, int index, mhd_totals* out);

@@ -99,6 +99,7 @@ _SIGNATURES = {
     "mhd_batch_get_fields": [_P, ctypes.c_int, _D, _D, _D, _D, _D],
     "mhd_batch_get_totals": [_P, ctypes.c_int, ctypes.POINTER(mhd_totals)],
     "mhd_batch_get_all_totals": [_P, ctypes.POINTER(mhd_totals)],
+    "mhd_batch_advance_totals": [_P, ctypes.c_longlong, ctypes.POINTER(mhd_totals)],
     "mhd_batch_nodes": [_P, ctypes.POINTER(ctypes.c_longlong)],
     "mhd_batch_get_kernel_config": [_P, ctypes.POINTER(mhd_kernel_config)],
     "mhd_batch_set_kernel_config": [_P, ctypes.POINTER(mhd_kernel_config)],
@@ -424,6 +425,13 @@ class Batch:
         t = mhd_totals()
         check(lib().mhd_batch_get_totals(self._h, int(i), ctypes.byref(t)), "mhd_batch_get_totals")
         return _totals_dict(t)
+
+    def advance_totals(self, nsteps: int) -> list:
+        """mhd_batch_advance_totals: advance, the last step reducing every
+        lattice's point totals (divb_max, divb_rms, omega_max are NaN)."""
+        ts = (mhd_totals * len(self.sizes))()
+        check(lib().mhd_batch_advance_totals(self._h, int(nsteps), ts), "mhd_batch_advance_totals")
+        return [_totals_dict(t) for t in ts]
 
     def get_all_totals(self) -> list:
         """mhd_batch_get_all_totals: the totals of every lattice, one wait."""

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "../../include/mhd.h"
+#include "diag_device.cuh"
 #include "internal.h"
 #include "step_row.cuh"
 
@@ -50,6 +51,98 @@ __global__ void __launch_bounds__(512) batch_step(const BatchLattice* __restrict
             step_row<1, V, false, Off>(src + L.offset, dst + L.offset, L.nx, L.ny, L.pitch, L.plane,
                                        L.np, tile.xblock, y, threadIdx.x);
     }
+}
+
+// A sample step of the ensemble: batch_step that also reduces the point
+// totals of every lattice's pre-collision state (mass, momentum, energies,
+// cross helicity, sum b, max |j_z|; the arithmetic of the diagnostics,
+// diag_device.cuh) from the populations each warp collides.  Each block
+// takes a contiguous run of the tile list (the tiles come lattice by
+// lattice), adds its rows into compensated FP32 lane sums and, when the
+// lattice changes and at the end, reduces them in FP64 into the partial of
+// the first tile of that lattice's run; the block's other tiles get zero
+// partials (kDiagSlots doubles per tile; the gradient slots 8, 9, 10, 12
+// zero), which launch_diag_batch_final reduces per lattice in tile order.
+// The populations are batch_step's.
+template <int V, typename Off>
+__global__ void __launch_bounds__(512) batch_step_totals(const BatchLattice* __restrict__ lats,
+                                                         const BatchTile* __restrict__ tiles, int ntiles,
+                                                         const float* __restrict__ src, float* __restrict__ dst,
+                                                         double* __restrict__ tile_partials) {
+    using MB = AbsBits<float>;
+    __shared__ double red[16][kDiagSlots];
+    const int lane = threadIdx.x, warp = threadIdx.y, tid = threadIdx.y * 32 + lane;
+    const int chunk = (ntiles + gridDim.x - 1) / gridDim.x;
+    const int t0 = blockIdx.x * chunk, t1 = min(ntiles, t0 + chunk);
+    LaneSum<float> ls[8];
+    MB::T mjz = 0;
+    // the block's sums so far into the partial of tile `slot` (block-uniform)
+    auto flush = [&](int slot) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const double w = warp_sum(ls[q].take());
+            if (lane == 0) red[warp][q] = w;
+        }
+        const unsigned long long m = warp_max_bits(dbits(MB::value(mjz)));
+        mjz = 0;
+        if (lane == 0) {
+            red[warp][8] = red[warp][9] = red[warp][10] = red[warp][12] = 0.0;
+            red[warp][11] = __longlong_as_double((long long)m);
+        }
+        __syncthreads();
+        if (tid < kDiagSlots) {
+            double a = red[0][tid];
+            for (int w = 1; w < (int)blockDim.y; ++w)
+                a = tid < 10 ? a + red[w][tid] : __longlong_as_double((long long)max_bits(dbits(a), dbits(red[w][tid])));
+            tile_partials[(long long)slot * kDiagSlots + tid] = a;
+        }
+        __syncthreads();  // red is rewritten by the next flush
+    };
+    int cur = -1, first = t0;
+    for (int t = t0; t < t1; ++t) {
+        const BatchTile tile = tiles[t];
+        if (tile.lat != cur) {  // uniform over the block
+            if (cur >= 0) flush(first);
+            cur = tile.lat;
+            first = t;
+        } else if (tid < kDiagSlots) {
+            tile_partials[(long long)t * kDiagSlots + tid] = 0.0;
+        }
+        const BatchLattice L = lats[tile.lat];
+        const int y = tile.y0 + threadIdx.y;
+        if (y < L.ny) {  // uniform over the warp
+            float v[kPlanes][V];
+            if (gather_row<1, V, false, Off>(src + L.offset, L.nx, L.ny, L.pitch, L.plane, tile.xblock, y, lane, v)) {
+                float ps[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) ps[q] = 0.f;
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    float f[9], g[10];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) f[i] = v[i][k];
+#pragma unroll
+                    for (int q = 0; q < 10; ++q) g[q] = v[9 + q][k];
+                    const NodeMom<float> n = node_moments(f, g, 1.f, L.np.rho0);
+                    add_point_sums(n, ps);
+                    mjz = max(mjz, MB::of(node_current(n, L.np.omega_m, 1.f)));
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) ls[q].add(ps[q]);
+                collide_nodes<float, V, false, kNative>(v, L.np);
+                const int x0 = (tile.xblock * 32 + lane) * V;
+                const Off o_0 = (Off)y * (Off)L.pitch, pl = (Off)L.plane;
+                float* d = dst + L.offset;
+#pragma unroll
+                for (int p = 0; p < kPlanes; ++p) {
+                    float r[V];
+                    StepCodec<float, V>::to_storage(v[p], r);
+                    VecIO<float, V>::store(d + ((Off)p * pl + o_0 + x0), r);
+                }
+            }
+        }
+    }
+    if (cur >= 0) flush(first);
 }
 
 }  // namespace mhd
@@ -102,6 +195,10 @@ struct mhd_batch {
     double* totals_d = nullptr;
     double* totals_h = nullptr;
     mhd::DiagEnsemble diag;  // the all-lattice diagnostics tables (built on first use)
+    // the sample step's per-tile partials and each lattice's first tile
+    double* tile_partials = nullptr;
+    int* d_tile_first = nullptr;
+    double* d_mass = nullptr;  // rho0 * nodes of each lattice
 };
 
 namespace {
@@ -134,6 +231,18 @@ BatchKernel batch_kernel(bool wide, int V) {
     return nullptr;
 }
 
+using BatchTotalsKernel = void (*)(const mhd::BatchLattice*, const mhd::BatchTile*, int, const float*, float*,
+                                  double*);
+
+BatchTotalsKernel batch_totals_kernel(bool wide, int V) {
+    switch (V) {
+    case 1: return wide ? mhd::batch_step_totals<1, long long> : mhd::batch_step_totals<1, int>;
+    case 2: return wide ? mhd::batch_step_totals<2, long long> : mhd::batch_step_totals<2, int>;
+    case 4: return wide ? mhd::batch_step_totals<4, long long> : mhd::batch_step_totals<4, int>;
+    }
+    return nullptr;
+}
+
 cudaError_t launch_batch(const mhd_batch* b, int from, int V, cudaStream_t st) {
     dim3 block(32, b->cfg.rows_per_block);
     const float* src = b->buf[from];
@@ -160,6 +269,25 @@ mhd_status batch_configure(mhd_batch* b, const mhd_kernel_config& c) {
                    cudaMemcpyHostToDevice),
         "H2D tiles");
     b->ntiles = (int)tiles.size();
+    // the tiles of lattice l are [first[l], first[l + 1]) (they come lattice by lattice)
+    std::vector<int> first(b->count + 1, 0);
+    for (size_t k = tiles.size(); k-- > 0;) first[tiles[k].lat] = (int)k;
+    first[b->count] = b->ntiles;
+    if (b->tile_partials) cudaFree(b->tile_partials);
+    if (b->d_tile_first) cudaFree(b->d_tile_first);
+    b->tile_partials = nullptr;
+    b->d_tile_first = nullptr;
+    BCK(cudaMalloc(&b->tile_partials, sizeof(double) * mhd::kDiagSlots * tiles.size()), "cudaMalloc(tile partials)");
+    BCK(cudaMalloc(&b->d_tile_first, sizeof(int) * (b->count + 1)), "cudaMalloc(tile ranges)");
+    BCK(cudaMemcpy(b->d_tile_first, first.data(), sizeof(int) * (b->count + 1), cudaMemcpyHostToDevice),
+        "H2D tile ranges");
+    if (!b->d_mass) {
+        std::vector<double> mass(b->count);
+        for (int l = 0; l < b->count; ++l)
+            mass[l] = b->params[l].rho0 * (double)b->layouts[l].nx * (double)b->layouts[l].ny;
+        BCK(cudaMalloc(&b->d_mass, sizeof(double) * b->count), "cudaMalloc(mass)");
+        BCK(cudaMemcpy(b->d_mass, mass.data(), sizeof(double) * b->count, cudaMemcpyHostToDevice), "H2D mass");
+    }
     int per_sm = 0, sms = 0;
     const int threads = 32 * rows;
     BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(b->wide, c.nodes_per_thread),
@@ -286,6 +414,9 @@ mhd_status mhd_batch_destroy(mhd_batch* b) {
     if (b->totals_d) cudaFree(b->totals_d);
     if (b->totals_h) cudaFreeHost(b->totals_h);
     mhd::diag_ensemble_destroy(b->diag);
+    if (b->tile_partials) cudaFree(b->tile_partials);
+    if (b->d_tile_first) cudaFree(b->d_tile_first);
+    if (b->d_mass) cudaFree(b->d_mass);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
     return MHD_OK;
@@ -370,6 +501,53 @@ mhd_status mhd_batch_advance(mhd_batch* b, long long nsteps) {
     }
     std::fill(b->prev_valid.begin(), b->prev_valid.end(), 1);
     std::fill(b->is_eq.begin(), b->is_eq.end(), 0);
+    return MHD_OK;
+}
+
+mhd_status mhd_batch_advance_totals(mhd_batch* b, long long nsteps, mhd_totals* out) {
+    if (!b || !out) return bfail(MHD_EINVAL, "NULL argument");
+    if (nsteps < 1) return bfail(MHD_EINVAL, "nsteps must be >= 1");
+    mhd_status s = mhd_batch_advance(b, nsteps - 1);
+    if (s != MHD_OK) return s;
+    const BatchTotalsKernel k = batch_totals_kernel(b->wide, b->cfg.nodes_per_thread);
+    if (!k) return bfail(MHD_EINVAL, "launch shape");
+    const float* src = b->buf[b->cur];
+    float* dst = b->buf[b->cur ^ 1];
+    // one resident wave of this kernel (its blocks take contiguous runs of tiles)
+    const int threads = 32 * b->cfg.rows_per_block;
+    int per_sm = 0;
+    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0), "occupancy");
+    const int grid = std::max(1, std::min(b->ntiles, std::max(1, per_sm) * mhd::device_sms()));
+    k<<<grid, dim3(32, b->cfg.rows_per_block), 0, b->stream>>>(b->d_lats, b->d_tiles, b->ntiles, src, dst,
+                                                              b->tile_partials);
+    BCK(cudaGetLastError(), "ensemble step with totals");
+    b->cur ^= 1;
+    ++b->step;
+    std::fill(b->prev_valid.begin(), b->prev_valid.end(), 1);
+    std::fill(b->is_eq.begin(), b->is_eq.end(), 0);
+    BCK(mhd::launch_diag_batch_final(b->tile_partials, b->d_tile_first, b->d_mass, b->count, b->totals_d, b->stream),
+        "ensemble point totals");
+    BCK(cudaMemcpyAsync(b->totals_h, b->totals_d, sizeof(double) * mhd::kDiagSlots * b->count,
+                        cudaMemcpyDeviceToHost, b->stream),
+        "D2H totals");
+    BCK(cudaStreamSynchronize(b->stream), "mhd_batch_advance_totals");
+    int bad = -1;
+    for (int i = 0; i < b->count; ++i) {
+        const double* t = b->totals_h + (long long)mhd::kDiagSlots * i;
+        const mhd::Layout& L = b->layouts[i];
+        const double n = (double)L.nx * L.ny;
+        mhd_totals& o = out[i];
+        o.mass = t[0]; o.mom_x = t[1]; o.mom_y = t[2];
+        o.e_kin = t[3] / n; o.e_mag = t[4] / n; o.cross_hel = t[5] / n;
+        o.bsum_x = t[6]; o.bsum_y = t[7];
+        o.divb_rms = o.divb_max = o.omega_max = std::nan("");
+        o.jz_max = t[11];
+        o.step = b->step;
+        for (int q : {0, 1, 2, 3, 4, 5, 6, 7, 11})
+            if (!std::isfinite(t[q]) && bad < 0) bad = i;
+    }
+    if (bad >= 0)
+        return bfail(MHD_EUNSTABLE, "non-finite point totals in lattice " + std::to_string(bad) + ": the run blew up");
     return MHD_OK;
 }
 

@@ -366,19 +366,37 @@ __global__ void __launch_bounds__(kDWarps * 32, 2) diag_batch_kernel(const DiagA
     }
 }
 
-// One block per lattice: thread q adds slot q of the lattice's tiles
-// [first[l], first[l + 1]) in order; slot 0 plus mass_base[l] is the mass.
-__global__ void diag_batch_final(const double* __restrict__ tile_partials, const int* __restrict__ first,
-                                 const double* __restrict__ mass_base, double* __restrict__ totals) {
-    const int l = blockIdx.x, q = threadIdx.x;
-    if (q >= kDiagSlots) return;
+// One block of kFinalThreads per lattice: thread j adds the partials of the
+// lattice's tiles first[l] + j, + j + kFinalThreads, ... (in that order),
+// then thread q adds slot q of the threads' sums in thread order (a fixed
+// order: bitwise reproducible); slot 0 plus mass_base[l] is the mass.
+constexpr int kFinalThreads = 256;
+__global__ void __launch_bounds__(kFinalThreads) diag_batch_final(const double* __restrict__ tile_partials,
+                                                                  const int* __restrict__ first,
+                                                                  const double* __restrict__ mass_base,
+                                                                  double* __restrict__ totals) {
+    __shared__ double red[kFinalThreads][kDiagSlots];
+    const int l = blockIdx.x, j = threadIdx.x;
     const int t0 = first[l], t1 = first[l + 1];
-    double v = tile_partials[(long long)t0 * kDiagSlots + q];
-    for (int k = t0 + 1; k < t1; ++k) {
-        const double x = tile_partials[(long long)k * kDiagSlots + q];
-        v = q < 10 ? v + x : __longlong_as_double((long long)max_bits(dbits(v), dbits(x)));
+    double acc[kDiagSlots];
+#pragma unroll
+    for (int q = 0; q < kDiagSlots; ++q) acc[q] = 0.0;
+    for (int k = t0 + j; k < t1; k += kFinalThreads) {
+        const double* p = tile_partials + (long long)k * kDiagSlots;
+#pragma unroll
+        for (int q = 0; q < kDiagSlots; ++q)
+            acc[q] = q < 10 ? acc[q] + p[q] : __longlong_as_double((long long)max_bits(dbits(acc[q]), dbits(p[q])));
     }
-    totals[(long long)l * kDiagSlots + q] = q == 0 ? mass_base[l] + v : v;
+#pragma unroll
+    for (int q = 0; q < kDiagSlots; ++q) red[j][q] = acc[q];
+    __syncthreads();
+    if (j < kDiagSlots) {
+        const int q = j;
+        double v = red[0][q];
+        for (int w = 1; w < kFinalThreads; ++w)
+            v = q < 10 ? v + red[w][q] : __longlong_as_double((long long)max_bits(dbits(v), dbits(red[w][q])));
+        totals[(long long)l * kDiagSlots + q] = q == 0 ? mass_base[l] + v : v;
+    }
 }
 
 int diag_blocks(const Layout& L) {
@@ -544,7 +562,13 @@ cudaError_t diag_ensemble_launch(DiagEnsemble& e, const Layout* layouts, const D
                                                         static_cast<const int2*>(e.d_tiles), e.ntiles, e.d_partials);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    diag_batch_final<<<e.count, 32, 0, st>>>(e.d_partials, e.d_first, e.d_mass, totals);
+    return launch_diag_batch_final(e.d_partials, e.d_first, e.d_mass, e.count, totals, st);
+}
+
+cudaError_t launch_diag_batch_final(const double* tile_partials, const int* first, const double* mass_base,
+                                    int count, double* totals, cudaStream_t st) {
+    if (count < 1) return cudaErrorInvalidValue;
+    diag_batch_final<<<count, kFinalThreads, 0, st>>>(tile_partials, first, mass_base, totals);
     return cudaGetLastError();
 }
 

@@ -141,6 +141,11 @@ void diag_ensemble_destroy(DiagEnsemble& e);
 // totals: kDiagSlots doubles per lattice.
 cudaError_t diag_ensemble_launch(DiagEnsemble& e, const Layout* layouts, const DiagLatticeState* states,
                                  double* totals, cudaStream_t st);
+// Lattice l's totals (kDiagSlots doubles at totals + kDiagSlots l) from its
+// tiles' partials [first[l], first[l + 1]) added in order; slot 0 plus
+// mass_base[l] is the mass.
+cudaError_t launch_diag_batch_final(const double* tile_partials, const int* first, const double* mass_base,
+                                    int count, double* totals, cudaStream_t st);
 
 // One step (as launch_step, two buffers, periodic x; s.V nodes per lane)
 // that also reduces the point totals of the pre-collision state it gathers

@@ -118,3 +118,41 @@ def test_all_totals_equal_the_per_lattice_totals():
                     assert abs(every[i][k] - one[k]) <= 1e-12 * nx * ny, (i, k)
                 for k in ("e_kin", "e_mag", "cross_hel", "divb_rms"):
                     assert abs(every[i][k] - one[k]) <= 1e-12 * abs(one[k]) + 1e-300, (i, k)
+
+
+@pytest.mark.parametrize("shape", [(1, 4), (2, 2), (4, 16)])
+def test_sample_step_of_the_ensemble(shape):
+    """mhd_batch_advance_totals: the fields after it (and after 5 more plain
+    steps) equal the plain batch's bit for bit, and its point totals are
+    those of mhd_batch_get_all_totals of the same gathered state up to the
+    order of the sums (the maximum of |j_z| to the same bound)."""
+    import math
+    from paper_2602_14667_gb300 import Batch
+    runs = []
+    for fused in (False, True):
+        with Batch(SIZES, TAUS) as b:
+            b.kernel_config = shape
+            for i, (nx, ny) in enumerate(SIZES):
+                b.set_fields(i, *_fields(i, nx, ny))
+            if fused:
+                pt = b.advance_totals(13)
+            else:
+                b.advance(13)
+                pt = None
+            ref = b.get_all_totals()
+            f13 = [b.get_fields(i) for i in range(len(SIZES))]
+            b.advance(5)
+            f18 = [b.get_fields(i) for i in range(len(SIZES))]
+            runs.append((pt, ref, f13, f18))
+    for i in range(len(SIZES)):
+        for k in ("rho", "ux", "uy", "bx", "by"):
+            assert np.array_equal(runs[0][2][i][k], runs[1][2][i][k]), (i, k)
+            assert np.array_equal(runs[0][3][i][k], runs[1][3][i][k]), (i, k)
+    pt, ref = runs[1][0], runs[1][1]
+    for i, (nx, ny) in enumerate(SIZES):
+        assert pt[i]["step"] == ref[i]["step"] == 13
+        assert all(math.isnan(pt[i][k]) for k in ("divb_max", "divb_rms", "omega_max"))
+        for k in ("mass", "mom_x", "mom_y", "bsum_x", "bsum_y"):
+            assert abs(pt[i][k] - ref[i][k]) <= 5e-9 * nx * ny, (i, k)
+        for k in ("e_kin", "e_mag", "cross_hel", "jz_max"):
+            assert abs(pt[i][k] - ref[i][k]) <= 1e-6 * abs(ref[i][k]), (i, k)
