@@ -377,7 +377,7 @@ def extra_rows(fp32_mlups, peak):
                 b.get_totals(i)
             loop_ms = (time.perf_counter() - t0) * 1e3
             t0 = time.perf_counter()
-            b.get_all_totals()
+            b.get_all_totals(as_arrays=True)
             all_ms = (time.perf_counter() - t0) * 1e3
         except MhdError:
             pass
@@ -395,9 +395,11 @@ def extra_rows(fp32_mlups, peak):
                 a1.record(stream)
                 a1.synchronize()
                 return a0.elapsed_time(a1) / reps
+            # (the totals as one array per field: building 512 dicts in Python
+            # would take ~0.7 ms per call, during which the GPU idles)
             sample = {"ms_plain_step": per_call(lambda: b.advance(1)),
-                      "ms_step_then_all_totals": per_call(lambda: (b.advance(1), b.get_all_totals())),
-                      "ms_fused_step": per_call(lambda: b.advance_totals(1))}
+                      "ms_step_then_all_totals": per_call(lambda: (b.advance(1), b.get_all_totals(as_arrays=True))),
+                      "ms_fused_step": per_call(lambda: b.advance_totals(1, as_arrays=True))}
         except MhdError:
             pass
     gbsb = 152 * nodes / (msb * 1e-3) / 1e9
@@ -656,9 +658,9 @@ def run_ensemble(args):
     loop_ms = (time.perf_counter() - t0) * 1e3
     all_ms = None
     if finite == len(mine):
-        b.get_all_totals()
+        b.get_all_totals(as_arrays=True)
         t0 = time.perf_counter()
-        b.get_all_totals()
+        b.get_all_totals(as_arrays=True)
         all_ms = (time.perf_counter() - t0) * 1e3
     nodes = b.nodes
     if dist is not None:

@@ -350,6 +350,14 @@ def totals_noalloc(state_ptr: int, nx: int, ny: int, params: "mhd_params", prev_
     return _totals_dict(t)
 
 
+def _totals_arrays(ts) -> dict:
+    """A ctypes array of mhd_totals as one numpy array per field."""
+    dt = np.dtype([(n, np.float64 if t is ctypes.c_double else np.int64) for n, t in mhd_totals._fields_])
+    assert dt.itemsize == ctypes.sizeof(mhd_totals)
+    a = np.frombuffer(ts, dtype=dt)
+    return {n: a[n].copy() for n in TOTAL_FIELDS + ("step",)}
+
+
 def _totals_dict(t: "mhd_totals") -> dict:
     d = {n: getattr(t, n) for n in TOTAL_FIELDS}
     d["step"] = t.step
@@ -426,18 +434,20 @@ class Batch:
         check(lib().mhd_batch_get_totals(self._h, int(i), ctypes.byref(t)), "mhd_batch_get_totals")
         return _totals_dict(t)
 
-    def advance_totals(self, nsteps: int) -> list:
+    def advance_totals(self, nsteps: int, as_arrays: bool = False):
         """mhd_batch_advance_totals: advance, the last step reducing every
-        lattice's point totals (divb_max, divb_rms, omega_max are NaN)."""
+        lattice's point totals (divb_max, divb_rms, omega_max are NaN): a
+        list of dicts, or with as_arrays one array per field."""
         ts = (mhd_totals * len(self.sizes))()
         check(lib().mhd_batch_advance_totals(self._h, int(nsteps), ts), "mhd_batch_advance_totals")
-        return [_totals_dict(t) for t in ts]
+        return _totals_arrays(ts) if as_arrays else [_totals_dict(t) for t in ts]
 
-    def get_all_totals(self) -> list:
-        """mhd_batch_get_all_totals: the totals of every lattice, one wait."""
+    def get_all_totals(self, as_arrays: bool = False):
+        """mhd_batch_get_all_totals: the totals of every lattice, one wait;
+        a list of dicts, or with as_arrays one array per field."""
         ts = (mhd_totals * len(self.sizes))()
         check(lib().mhd_batch_get_all_totals(self._h, ts), "mhd_batch_get_all_totals")
-        return [_totals_dict(t) for t in ts]
+        return _totals_arrays(ts) if as_arrays else [_totals_dict(t) for t in ts]
 
     @property
     def kernel_config(self):

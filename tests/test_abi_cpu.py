@@ -196,3 +196,20 @@ def test_launch_shapes_take_two_or_three_numbers():
     for bad in ((4,), (1, 2, 3, 4)):
         with pytest.raises(ValueError):
             _abi._shape_in(bad)
+
+
+def test_totals_arrays_follow_the_struct_fields():
+    """The batch totals as one array per field read the ctypes records field
+    by field (no GPU: the records are filled here)."""
+    from paper_2602_14667_gb300 import _abi
+    ts = (_abi.mhd_totals * 5)()
+    for i in range(5):
+        for j, name in enumerate(_abi.TOTAL_FIELDS):
+            setattr(ts[i], name, 100.0 * i + j)
+        ts[i].step = 40 + i
+    a = _abi._totals_arrays(ts)
+    assert sorted(a) == sorted(_abi.TOTAL_FIELDS + ("step",))
+    for j, name in enumerate(_abi.TOTAL_FIELDS):
+        assert list(a[name]) == [100.0 * i + j for i in range(5)], name
+    assert list(a["step"]) == [40, 41, 42, 43, 44]
+    assert [_abi._totals_dict(t) for t in ts][3] == {k: v[3] for k, v in a.items()}

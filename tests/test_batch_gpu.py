@@ -109,6 +109,9 @@ def test_all_totals_equal_the_per_lattice_totals():
             b.advance(steps)
             every = b.get_all_totals()
             assert len(every) == len(SIZES)
+            arrays = b.get_all_totals(as_arrays=True)
+            for k, col in arrays.items():
+                assert [e[k] for e in every] == list(col), k
             for i, (nx, ny) in enumerate(SIZES):
                 one = b.get_totals(i)
                 assert every[i]["step"] == one["step"]
